@@ -1,0 +1,649 @@
+/*
+ * musta_oracle.c -- plain, slow, FP64 CPU oracle for the MUSTA-FORCE update of
+ * ideal relativistic hydrodynamics (Porter-Sobieraj et al., "A MUSTA-FORCE
+ * algorithm for solving partial differential equations of relativistic
+ * hydrodynamics").
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the CPU
+ * baseline leg of the benchmark may load this library.  It shares no code,
+ * header, table or constant generator with the CUDA path; it is written
+ * from the paper's equations and the readings listed below, in the paper's
+ * order, with no blocking, fusion or reordering.
+ *
+ * State per cell: U = (E, Mx, My, Mz) = T^{00}, T^{0i}  (Sec. 2.1, Eq. 4,
+ * without the charge R).  Arrays are field-major [4][nz][ny][nx], x fastest.
+ *
+ * Readings of points the paper leaves open (each is also a named item in the
+ * design notes):
+ *  R1  Lax-Wendroff flux (Eq. 10) uses (F_R - F_L) inside the argument, the
+ *      textbook FORCE form; the printed (U_R - U_L) is read as a typo.
+ *  R2  alpha = 1 for dimension-split sweeps (Eq. 10-11; "alpha = 3" refers to
+ *      the unsplit 3-D predictor of Eq. 13).  alpha is a parameter.
+ *  R3  MUSTA start states at interface i+1/2 are the Hancock-evolved right
+ *      face of cell i and left face of cell i+1 (Sec. 2.4, MUSCL-Hancock
+ *      step 3).
+ *  R4  k MUSTA stages = k FORCE evaluations and k-1 local Riemann predictor
+ *      updates (Eq. 8) with the global lambda = dt/dx.
+ *  R5  Limited slope written division-free: with a = U_i - U_{i-1},
+ *      b = U_{i+1} - U_i, slope = a * xi(b/a) (Eq. 15-17); by the symmetry
+ *      of Eq. 22 both faces use the same slope.  van Albada is the clipped
+ *      form (zero for r <= 0).  MC (not in the paper) is
+ *      xi = max(0, min(2r, (1+r)/2, 2)).
+ *  R6  Inside an RK stage of a sweep of length dt_s, lambda = dt_s/dx_d is
+ *      used by Hancock, MUSTA and the divergence.
+ *  R7  Dimension splitting is Strang: X(dt/2) Y(dt/2) Z(dt) Y(dt/2) X(dt/2)
+ *      over the axes with more than one cell; one CFL dt per full step.
+ *  R8  CFL signal speed: ideal-fluid characteristic speeds
+ *      lam = [v_d(1-c2) +- c sqrt((1-v^2)(1-v_d^2-(v^2-v_d^2)c2))]/(1-v^2 c2),
+ *      dt = cfl / max_{cells,d} (max|lam|/dx_d), clipped to t_end.
+ *  R9  Admissibility: cons->prim caps |M| at (1-delta)E; a cell whose two
+ *      Hancock face states are not both admissible (E > 0 and
+ *      |M| < (1-delta)E) uses its cell average on both faces.
+ *  R10 p = c2*e cons->prim solves Eq. 23 exactly: W = E + p is the positive
+ *      root of W^2 - (1+c2)E W + c2 M^2 = 0.
+ *  R11 Tabulated EOS: nodes uniform in ln e, p and c_s^2 interpolated
+ *      linearly in ln e; p = e/3 below the table, linear extrapolation with
+ *      the last c_s^2 above it.  Eq. 23 is solved by safeguarded Newton on
+ *      f(v) = v - |M|/(E + p(E - |M| v)) in the bracket [0, |M|/E].
+ *  R12 Jet source: S^{0mu} = dEdx (1, n) g(x - x0 - n t), g a normalised
+ *      3-D Gaussian; added once per step as U += dt S(t_n) before the sweeps.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ---------------------------------------------------------------- config */
+typedef struct {
+    int nx, ny, nz;
+    double dx, dy, dz;
+    double x0, y0, z0;         /* lower corner of the box */
+    int bc[3];                 /* 0 periodic, 1 outflow */
+    int limiter;               /* 0 none 1 minmod 2 mc 3 superbee 4 vanleer 5 vanalbada */
+    int stages;                /* MUSTA stages k >= 1 */
+    int rk_order;              /* 1 (forward Euler), 2 or 3 */
+    int hancock;               /* 1: MUSCL-Hancock half step on; 0: plain MUSCL faces */
+    double alpha;              /* FORCE alpha */
+    double cfl;
+    double fixed_dt;           /* > 0 overrides the CFL step */
+    double delta;              /* admissibility margin (R9) */
+    int eos_kind;              /* 0: p = cs2 e ; 1: table */
+    double cs2;
+    int tab_n;
+    double lne_min, lne_max;
+    const double *cs2_tab, *p_tab;
+    int seed_kind;             /* Newton seed: 0 zero, 1 conformal closed form, 2 MLP */
+    const double *mlp;         /* MLP parameters (layout in or_mlp_forward) */
+    int mlp_quantize;          /* 1: bf16 weights and layer-2 inputs */
+    double newton_tol;         /* |dv| tolerance */
+    int jet_on;
+    double jet[8];             /* x0,y0,z0, nx,ny,nz, dEdx, sigma */
+} or_config;
+
+/* diagnostics counters (reset by or_reset_counters) */
+static long g_newton_calls = 0, g_newton_iters = 0, g_newton_fail = 0;
+static long g_capped = 0, g_face_fallback = 0;
+
+void or_reset_counters(void) {
+    g_newton_calls = g_newton_iters = g_newton_fail = 0;
+    g_capped = g_face_fallback = 0;
+}
+void or_get_counters(long out[5]) {
+    out[0] = g_newton_calls; out[1] = g_newton_iters; out[2] = g_newton_fail;
+    out[3] = g_capped; out[4] = g_face_fallback;
+}
+
+/* ------------------------------------------------------- slope limiters */
+/* Sec. 2.5, Eq. 15-21 (R5): returns the limited slope a*xi(b/a). */
+double or_limiter(int kind, double a, double b) {
+    double ab = a * b;
+    double sa = (a > 0.0) ? 1.0 : -1.0;
+    switch (kind) {
+    case 0: /* no limiter: central slope, Eq. 14 */
+        return 0.5 * (a + b);
+    case 1: /* Minbee, Eq. 18 */
+        if (ab <= 0.0) return 0.0;
+        return sa * fmin(fabs(a), fabs(b));
+    case 2: /* monotonized central (van Leer 1977) */
+        if (ab <= 0.0) return 0.0;
+        return sa * fmin(fmin(2.0 * fabs(a), 2.0 * fabs(b)), 0.5 * fabs(a + b));
+    case 3: /* Superbee, Eq. 19 */
+        if (ab <= 0.0) return 0.0;
+        return sa * fmax(fmin(2.0 * fabs(a), fabs(b)), fmin(fabs(a), 2.0 * fabs(b)));
+    case 4: /* van Leer, Eq. 21 */
+        if (ab <= 0.0) return 0.0;
+        return 2.0 * ab / (a + b);
+    case 5: /* van Albada, Eq. 20 (clipped, R5) */
+        if (ab <= 0.0) return 0.0;
+        return ab * (a + b) / (a * a + b * b);
+    }
+    return 0.0;
+}
+
+/* ------------------------------------------------------------------ EOS */
+/* R11: pressure and squared sound speed from the table. */
+void or_eos_table(const or_config *c, double e, double *p, double *c2) {
+    int n = c->tab_n;
+    double lne = log(e);
+    if (!(e > 0.0) || lne < c->lne_min) {
+        *p = e / 3.0; *c2 = 1.0 / 3.0;
+        if (!(e > 0.0)) *p = 0.0;
+        return;
+    }
+    double h = (c->lne_max - c->lne_min) / (double)(n - 1);
+    double u = (lne - c->lne_min) / h;
+    if (u >= (double)(n - 1)) {
+        double emax = exp(c->lne_max);
+        *p = c->p_tab[n - 1] + c->cs2_tab[n - 1] * (e - emax);
+        *c2 = c->cs2_tab[n - 1];
+        return;
+    }
+    int i = (int)floor(u);
+    double f = u - (double)i;
+    *p = c->p_tab[i] + f * (c->p_tab[i + 1] - c->p_tab[i]);
+    *c2 = c->cs2_tab[i] + f * (c->cs2_tab[i + 1] - c->cs2_tab[i]);
+}
+
+double or_eos_p(const or_config *c, double e) {
+    if (c->eos_kind == 0) return c->cs2 * e;
+    double p, c2; or_eos_table(c, e, &p, &c2); return p;
+}
+double or_eos_cs2(const or_config *c, double e) {
+    if (c->eos_kind == 0) return c->cs2;
+    double p, c2; or_eos_table(c, e, &p, &c2); return c2;
+}
+
+/* ------------------------------------------------------------------ MLP */
+/*
+ * Newton seed network (not in the paper): inputs (ln E, |M|/E) standardised,
+ * two tanh hidden layers of 32, output r = sigmoid(z), seed v0 = (|M|/E) r.
+ * Parameter layout: W1[32][2] b1[32] W2[32][32] b2[32] W3[32] b3 mu0 s0 mu1 s1.
+ */
+#define MLP_H 32
+#define MLP_NPARAM (MLP_H * 2 + MLP_H + MLP_H * MLP_H + MLP_H + MLP_H + 1 + 4)
+
+int or_mlp_nparam(void) { return MLP_NPARAM; }
+
+/* round to the nearest bfloat16 (ties to even), via the float32 value */
+double or_round_bf16(double x) {
+    float f = (float)x;
+    unsigned int u; memcpy(&u, &f, 4);
+    if ((u & 0x7f800000u) == 0x7f800000u) return (double)f;
+    unsigned int lsb = (u >> 16) & 1u;
+    u += 0x7fffu + lsb;
+    u &= 0xffff0000u;
+    memcpy(&f, &u, 4);
+    return (double)f;
+}
+
+/* forward for one sample; cache (optional) receives h1[32], h2[32], r */
+static double mlp_forward1(const double *P, int q, double lnE, double x, double *cache) {
+    const double *W1 = P, *b1 = W1 + 2 * MLP_H, *W2 = b1 + MLP_H, *b2 = W2 + MLP_H * MLP_H;
+    const double *W3 = b2 + MLP_H, *b3 = W3 + MLP_H, *nrm = b3 + 1;
+    double in0 = (lnE - nrm[0]) / nrm[1];
+    double in1 = (x - nrm[2]) / nrm[3];
+    double h1[MLP_H], h2[MLP_H];
+    for (int j = 0; j < MLP_H; j++) {
+        double w0 = q ? or_round_bf16(W1[2 * j]) : W1[2 * j];
+        double w1 = q ? or_round_bf16(W1[2 * j + 1]) : W1[2 * j + 1];
+        h1[j] = tanh(w0 * in0 + w1 * in1 + b1[j]);
+        if (q) h1[j] = or_round_bf16(h1[j]);
+    }
+    for (int j = 0; j < MLP_H; j++) {
+        double s = b2[j];
+        for (int k = 0; k < MLP_H; k++) {
+            double w = q ? or_round_bf16(W2[j * MLP_H + k]) : W2[j * MLP_H + k];
+            s += w * h1[k];
+        }
+        h2[j] = tanh(s);
+    }
+    double z = b3[0];
+    for (int k = 0; k < MLP_H; k++) {
+        double w = q ? or_round_bf16(W3[k]) : W3[k];
+        z += w * h2[k];
+    }
+    double r = 1.0 / (1.0 + exp(-z));
+    if (cache) {
+        memcpy(cache, h1, sizeof h1);
+        memcpy(cache + MLP_H, h2, sizeof h2);
+        cache[2 * MLP_H] = r;
+        cache[2 * MLP_H + 1] = in0;
+        cache[2 * MLP_H + 2] = in1;
+    }
+    return x * r;
+}
+
+/* batch forward: X[n][2] = (ln E, |M|/E), out[n] = seed velocity */
+void or_mlp_forward(const double *P, int q, int n, const double *X, double *out) {
+    for (int i = 0; i < n; i++) out[i] = mlp_forward1(P, q, X[2 * i], X[2 * i + 1], NULL);
+}
+
+/*
+ * loss = mean_i (v0_i - Y_i)^2 and its gradient with respect to the
+ * parameters (normalisation entries get zero gradient).  With q = 1 the
+ * rounding to bf16 is passed straight through (its derivative taken as 1).
+ */
+double or_mlp_loss_grad(const double *P, int q, int n, const double *X, const double *Y,
+                        double *G) {
+    const double *W2 = P + 3 * MLP_H, *W3 = W2 + MLP_H * MLP_H + MLP_H;
+    double *gW1 = G, *gb1 = gW1 + 2 * MLP_H, *gW2 = gb1 + MLP_H, *gb2 = gW2 + MLP_H * MLP_H;
+    double *gW3 = gb2 + MLP_H, *gb3 = gW3 + MLP_H;
+    memset(G, 0, sizeof(double) * MLP_NPARAM);
+    double loss = 0.0;
+    double cache[2 * MLP_H + 3];
+    for (int i = 0; i < n; i++) {
+        double x = X[2 * i + 1];
+        double v0 = mlp_forward1(P, q, X[2 * i], x, cache);
+        const double *h1 = cache, *h2 = cache + MLP_H;
+        double r = cache[2 * MLP_H], in0 = cache[2 * MLP_H + 1], in1 = cache[2 * MLP_H + 2];
+        double d = v0 - Y[i];
+        loss += d * d;
+        double dv = 2.0 * d / (double)n;
+        double dz = dv * x * r * (1.0 - r);
+        gb3[0] += dz;
+        double da2[MLP_H];
+        for (int k = 0; k < MLP_H; k++) {
+            double w3 = q ? or_round_bf16(W3[k]) : W3[k];
+            gW3[k] += dz * h2[k];
+            da2[k] = dz * w3 * (1.0 - h2[k] * h2[k]);
+        }
+        for (int j = 0; j < MLP_H; j++) {
+            gb2[j] += da2[j];
+            for (int k = 0; k < MLP_H; k++) gW2[j * MLP_H + k] += da2[j] * h1[k];
+        }
+        for (int k = 0; k < MLP_H; k++) {
+            double dh1 = 0.0;
+            for (int j = 0; j < MLP_H; j++) {
+                double w = q ? or_round_bf16(W2[j * MLP_H + k]) : W2[j * MLP_H + k];
+                dh1 += w * da2[j];
+            }
+            /* tanh derivative at the unrounded activation value */
+            double a1 = h1[k];
+            double da1 = dh1 * (1.0 - a1 * a1);
+            gb1[k] += da1;
+            gW1[2 * k] += da1 * in0;
+            gW1[2 * k + 1] += da1 * in1;
+        }
+    }
+    return loss / (double)n;
+}
+
+/* ------------------------------------------------------- cons -> prim */
+/*
+ * Sec. 2.6, Eq. 23: from U = (E, M) find v (vector), p and e.  Returns 0 for
+ * an admissible state, 1 when |M| was capped, 2 for E <= 0 (vacuum: v = p = 0),
+ * 3 when the Newton solve hit its iteration cap.
+ */
+int or_cons2prim(const or_config *c, const double U[4], double *e_out, double v[3],
+                 double *p_out, int *iters) {
+    double E = U[0], Mx = U[1], My = U[2], Mz = U[3];
+    double M2 = Mx * Mx + My * My + Mz * Mz;
+    int status = 0;
+    if (iters) *iters = 0;
+    if (!(E > 0.0)) {
+        v[0] = v[1] = v[2] = 0.0;
+        *p_out = 0.0; *e_out = 0.0;
+        return 2;
+    }
+    double cap = (1.0 - c->delta) * E;
+    if (M2 > cap * cap) {               /* R9: cap |M| at (1-delta) E */
+        double s = cap / sqrt(M2);
+        Mx *= s; My *= s; Mz *= s;
+        M2 = Mx * Mx + My * My + Mz * Mz;
+        status = 1;
+        g_capped++;
+    }
+    double M = sqrt(M2);
+    if (c->eos_kind == 0) {
+        /* R10: W = E + p is the positive root of W^2 - (1+c2) E W + c2 M^2 = 0 */
+        double a = (1.0 + c->cs2) * E;
+        double disc = a * a - 4.0 * c->cs2 * M2;
+        if (disc < 0.0) disc = 0.0;
+        double W = 0.5 * (a + sqrt(disc));
+        v[0] = Mx / W; v[1] = My / W; v[2] = Mz / W;
+        *p_out = W - E;
+        *e_out = E - M2 / W;
+        return status;
+    }
+    /* R11: safeguarded Newton on f(v) = v - M/(E + p(E - M v)), v in [0, M/E] */
+    g_newton_calls++;
+    double lo = 0.0, hi = M / E;
+    double vv;
+    if (c->seed_kind == 1) {
+        double a = (4.0 / 3.0) * E, disc = a * a - (4.0 / 3.0) * M2;
+        if (disc < 0.0) disc = 0.0;
+        vv = M / (0.5 * (a + sqrt(disc)));
+    } else if (c->seed_kind == 2 && c->mlp) {
+        vv = mlp_forward1(c->mlp, c->mlp_quantize, log(E), M / E, NULL);
+    } else {
+        vv = 0.0;
+    }
+    if (vv < lo) vv = lo;
+    if (vv > hi) vv = hi;
+    double p = 0.0, c2 = 0.0;
+    int it, conv = 0;
+    if (M == 0.0) {
+        vv = 0.0; conv = 1; it = 0;
+    } else {
+        for (it = 1; it <= 50; it++) {
+            double e = E - M * vv;
+            or_eos_table(c, e, &p, &c2);
+            double W = E + p;
+            double f = vv - M / W;
+            if (f == 0.0) { conv = 1; break; }          /* vv is the root */
+            if (f > 0.0) hi = vv; else lo = vv;
+            double fp = 1.0 - c2 * M2 / (W * W);
+            double vn = vv - f / fp;
+            if (!(vn > lo && vn < hi)) vn = 0.5 * (lo + hi);
+            double dv = vn - vv;
+            vv = vn;
+            if (fabs(dv) <= c->newton_tol) { conv = 1; break; }
+        }
+        if (it > 50) it = 50;
+    }
+    g_newton_iters += it;
+    if (iters) *iters = it;
+    if (!conv) { g_newton_fail++; status = 3; }
+    double e = E - M * vv;
+    or_eos_table(c, e, &p, &c2);
+    double sc = (M > 0.0) ? vv / M : 0.0;
+    v[0] = Mx * sc; v[1] = My * sc; v[2] = Mz * sc;
+    *p_out = p;
+    *e_out = e;
+    return status;
+}
+
+/* ------------------------------------------------------- prim -> cons */
+/* Sec. 2.1, Eq. 4: E = (e+p) g^2 - p, M_i = (e+p) g^2 v_i. */
+void or_prim2cons(const or_config *c, double e, double vx, double vy, double vz, double U[4]) {
+    double p = or_eos_p(c, e);
+    double g2 = 1.0 / (1.0 - (vx * vx + vy * vy + vz * vz));
+    double w = (e + p) * g2;
+    U[0] = w - p;
+    U[1] = w * vx;
+    U[2] = w * vy;
+    U[3] = w * vz;
+}
+
+/* ----------------------------------------------------------------- flux */
+/* Sec. 2.1, Eq. 3: flux along axis d of U. */
+void or_flux(const or_config *c, int d, const double U[4], double F[4]) {
+    double e, v[3], p;
+    or_cons2prim(c, U, &e, v, &p, NULL);
+    F[0] = (U[0] + p) * v[d];
+    F[1] = U[1] * v[d];
+    F[2] = U[2] * v[d];
+    F[3] = U[3] * v[d];
+    F[1 + d] += p;
+}
+
+/* ---------------------------------------------------------- MUSTA-FORCE */
+/* Sec. 2.4, MUSTA steps 1-5 with the FORCE flux of Eq. 9-11 (R1, R2, R4). */
+void or_musta_force(const or_config *c, int d, double lam, const double UL0[4],
+                    const double UR0[4], double Fout[4]) {
+    double UL[4], UR[4], FL[4], FR[4], Ulw[4], Flw[4], Flf[4], Fc[4];
+    double al = c->alpha * lam;
+    memcpy(UL, UL0, sizeof UL);
+    memcpy(UR, UR0, sizeof UR);
+    for (int l = 0; l < c->stages; l++) {
+        or_flux(c, d, UL, FL);
+        or_flux(c, d, UR, FR);
+        for (int q = 0; q < 4; q++)
+            Ulw[q] = 0.5 * (UL[q] + UR[q]) - 0.5 * al * (FR[q] - FL[q]);
+        or_flux(c, d, Ulw, Flw);
+        for (int q = 0; q < 4; q++)
+            Flf[q] = 0.5 * (FL[q] + FR[q]) - (0.5 / al) * (UR[q] - UL[q]);
+        for (int q = 0; q < 4; q++) Fc[q] = 0.5 * (Flw[q] + Flf[q]);
+        if (l < c->stages - 1) {
+            for (int q = 0; q < 4; q++) {
+                UL[q] = UL[q] - lam * (Fc[q] - FL[q]);
+                UR[q] = UR[q] - lam * (FR[q] - Fc[q]);
+            }
+        }
+    }
+    memcpy(Fout, Fc, sizeof Fc);
+}
+
+static int admissible(const or_config *c, const double U[4]) {
+    double M2 = U[1] * U[1] + U[2] * U[2] + U[3] * U[3];
+    double cap = (1.0 - c->delta) * U[0];
+    return U[0] > 0.0 && M2 < cap * cap;
+}
+
+/*
+ * Sec. 2.4-2.5: MUSCL slopes (Eq. 15-17), faces, Hancock half step (Eq. 13,
+ * the term along the sweep axis), R9 fallback.  V holds cells -1..+1 around
+ * the cell; outputs the evolved faces.
+ */
+void or_hancock_faces(const or_config *c, int d, double lam, const double Vm[4],
+                      const double V0[4], const double Vp[4], double ULt[4], double URt[4]) {
+    double UL[4], UR[4], FL[4], FR[4];
+    for (int q = 0; q < 4; q++) {
+        double s = or_limiter(c->limiter, V0[q] - Vm[q], Vp[q] - V0[q]);
+        UL[q] = V0[q] - 0.5 * s;
+        UR[q] = V0[q] + 0.5 * s;
+    }
+    if (c->hancock) {
+        or_flux(c, d, UL, FL);
+        or_flux(c, d, UR, FR);
+        for (int q = 0; q < 4; q++) {
+            ULt[q] = UL[q] + 0.5 * lam * (FL[q] - FR[q]);
+            URt[q] = UR[q] + 0.5 * lam * (FL[q] - FR[q]);
+        }
+    } else {
+        memcpy(ULt, UL, sizeof UL);
+        memcpy(URt, UR, sizeof UR);
+    }
+    if (!admissible(c, ULt) || !admissible(c, URt)) {
+        memcpy(ULt, V0, 4 * sizeof(double));
+        memcpy(URt, V0, 4 * sizeof(double));
+        g_face_fallback++;
+    }
+}
+
+/* ------------------------------------------------------------- pencils */
+/* V[(N+4)][4]: cell i at V[i+2]; fill two ghost cells on each side. */
+static void fill_ghosts(double (*V)[4], int N, int bc) {
+    for (int g = 1; g <= 2; g++) {
+        int lo_dst = 2 - g, hi_dst = N + 1 + g;
+        int lo_src = (bc == 0) ? (N - g + 2) : 2;
+        int hi_src = (bc == 0) ? (g + 1) : (N + 1);
+        memcpy(V[lo_dst], V[lo_src], 4 * sizeof(double));
+        memcpy(V[hi_dst], V[hi_src], 4 * sizeof(double));
+    }
+}
+
+/* D[i] = F_{i+1/2} - F_{i-1/2} for cells 0..N-1 (the divergence, times dx) */
+static void pencil_L(const or_config *c, int d, double lam, double (*V)[4], int N, double (*D)[4],
+                     double (*ULt)[4], double (*URt)[4], double (*F)[4]) {
+    /* evolved faces of cells -1..N (index +1) */
+    for (int i = -1; i <= N; i++)
+        or_hancock_faces(c, d, lam, V[i + 1], V[i + 2], V[i + 3], ULt[i + 1], URt[i + 1]);
+    /* interface fluxes F_{i+1/2} for i = -1..N-1 (index +1) */
+    for (int i = -1; i < N; i++)
+        or_musta_force(c, d, lam, URt[i + 1], ULt[i + 2], F[i + 1]);
+    for (int i = 0; i < N; i++)
+        for (int q = 0; q < 4; q++) D[i][q] = F[i + 1][q] - F[i][q];
+}
+
+/* one Runge-Kutta sweep (Sec. 2.3, Eq. 6 or 7) of every pencil along axis d */
+void or_sweep(const or_config *c, double *U, int d, double dt) {
+    int n[3] = {c->nx, c->ny, c->nz};
+    double h[3] = {c->dx, c->dy, c->dz};
+    int N = n[d];
+    long cells = (long)c->nx * c->ny * c->nz;
+    long stride = (d == 0) ? 1 : (d == 1) ? c->nx : (long)c->nx * c->ny;
+    double lam = dt / h[d];
+    int a_ax = (d == 0) ? 1 : 0, b_ax = (d == 2) ? 1 : 2;
+    double (*V0)[4] = malloc(sizeof(double[4]) * (N + 4));
+    double (*V1)[4] = malloc(sizeof(double[4]) * (N + 4));
+    double (*V2)[4] = malloc(sizeof(double[4]) * (N + 4));
+    double (*D)[4] = malloc(sizeof(double[4]) * N);
+    double (*ULt)[4] = malloc(sizeof(double[4]) * (N + 2));
+    double (*URt)[4] = malloc(sizeof(double[4]) * (N + 2));
+    double (*F)[4] = malloc(sizeof(double[4]) * (N + 1));
+    for (int b = 0; b < n[b_ax]; b++) {
+        for (int a = 0; a < n[a_ax]; a++) {
+            int idx[3];
+            idx[d] = 0; idx[a_ax] = a; idx[b_ax] = b;
+            long base = idx[0] + (long)c->nx * (idx[1] + (long)c->ny * idx[2]);
+            for (int i = 0; i < N; i++)
+                for (int q = 0; q < 4; q++) V0[i + 2][q] = U[q * cells + base + i * stride];
+            fill_ghosts(V0, N, c->bc[d]);
+            /* stage 1: U1 = U + dt L(U) */
+            pencil_L(c, d, lam, V0, N, D, ULt, URt, F);
+            if (c->rk_order == 1) {
+                for (int i = 0; i < N; i++)
+                    for (int q = 0; q < 4; q++)
+                        U[q * cells + base + i * stride] = V0[i + 2][q] - lam * D[i][q];
+                continue;
+            }
+            for (int i = 0; i < N; i++)
+                for (int q = 0; q < 4; q++) V1[i + 2][q] = V0[i + 2][q] - lam * D[i][q];
+            fill_ghosts(V1, N, c->bc[d]);
+            pencil_L(c, d, lam, V1, N, D, ULt, URt, F);
+            if (c->rk_order == 3) {
+                /* U2 = 3/4 U + 1/4 U1 + 1/4 dt L(U1) */
+                for (int i = 0; i < N; i++)
+                    for (int q = 0; q < 4; q++)
+                        V2[i + 2][q] = 0.75 * V0[i + 2][q] + 0.25 * (V1[i + 2][q] - lam * D[i][q]);
+                fill_ghosts(V2, N, c->bc[d]);
+                pencil_L(c, d, lam, V2, N, D, ULt, URt, F);
+                /* U^{n+1} = 1/3 U + 2/3 U2 + 2/3 dt L(U2) */
+                for (int i = 0; i < N; i++)
+                    for (int q = 0; q < 4; q++)
+                        U[q * cells + base + i * stride] =
+                            V0[i + 2][q] / 3.0 + (2.0 / 3.0) * (V2[i + 2][q] - lam * D[i][q]);
+            } else {
+                /* U^{n+1} = 1/2 (U + U1 + dt L(U1)) */
+                for (int i = 0; i < N; i++)
+                    for (int q = 0; q < 4; q++)
+                        U[q * cells + base + i * stride] =
+                            0.5 * (V0[i + 2][q] + V1[i + 2][q] - lam * D[i][q]);
+            }
+        }
+    }
+    free(V0); free(V1); free(V2); free(D); free(ULt); free(URt); free(F);
+}
+
+/* ------------------------------------------------------------------ CFL */
+/* R8: largest characteristic speed magnitude of one cell along axis d */
+double or_signal_speed(const or_config *c, const double U[4], int d) {
+    double e, v[3], p;
+    or_cons2prim(c, U, &e, v, &p, NULL);
+    double c2 = or_eos_cs2(c, e);
+    double cs = sqrt(c2);
+    double v2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+    double vd = v[d];
+    double rad = (1.0 - v2) * (1.0 - vd * vd - (v2 - vd * vd) * c2);
+    if (rad < 0.0) rad = 0.0;
+    double den = 1.0 - v2 * c2;
+    double lp = (vd * (1.0 - c2) + cs * sqrt(rad)) / den;
+    double lm = (vd * (1.0 - c2) - cs * sqrt(rad)) / den;
+    return fmax(fabs(lp), fabs(lm));
+}
+
+/* max over cells and active axes of speed/dx, the inverse of the CFL dt */
+double or_max_rate(const or_config *c, const double *U) {
+    long cells = (long)c->nx * c->ny * c->nz;
+    int n[3] = {c->nx, c->ny, c->nz};
+    double h[3] = {c->dx, c->dy, c->dz};
+    double m = 0.0;
+    for (long i = 0; i < cells; i++) {
+        double u[4] = {U[i], U[cells + i], U[2 * cells + i], U[3 * cells + i]};
+        for (int d = 0; d < 3; d++) {
+            if (n[d] <= 1) continue;
+            double r = or_signal_speed(c, u, d) / h[d];
+            if (r > m) m = r;
+        }
+    }
+    return m;
+}
+
+/* ------------------------------------------------------------ jet source */
+/* R12: U += dt * S(t) */
+void or_jet_source(const or_config *c, double *U, double t, double dt) {
+    long cells = (long)c->nx * c->ny * c->nz;
+    const double *j = c->jet;
+    double sig = j[7];
+    double norm = 1.0 / (pow(2.0 * M_PI, 1.5) * sig * sig * sig);
+    double cx = j[0] + j[3] * t, cy = j[1] + j[4] * t, cz = j[2] + j[5] * t;
+    for (int z = 0; z < c->nz; z++)
+        for (int y = 0; y < c->ny; y++)
+            for (int x = 0; x < c->nx; x++) {
+                double px = c->x0 + (x + 0.5) * c->dx - cx;
+                double py = c->y0 + (y + 0.5) * c->dy - cy;
+                double pz = c->z0 + (z + 0.5) * c->dz - cz;
+                double g = norm * exp(-(px * px + py * py + pz * pz) / (2.0 * sig * sig));
+                long i = x + (long)c->nx * (y + (long)c->ny * z);
+                double s = dt * j[6] * g;
+                U[i] += s;
+                U[cells + i] += s * j[3];
+                U[2 * cells + i] += s * j[4];
+                U[3 * cells + i] += s * j[5];
+            }
+}
+
+/* ----------------------------------------------------------------- step */
+/* one full step: dt (R8), source (R12), Strang sweeps (R7).  Returns dt. */
+double or_step(const or_config *c, double *U, double t, double t_end) {
+    double dt;
+    if (c->fixed_dt > 0.0) dt = c->fixed_dt;
+    else dt = c->cfl / or_max_rate(c, U);
+    if (t_end > 0.0 && t + dt > t_end) dt = t_end - t;
+    if (!(dt > 0.0)) return 0.0;
+    if (c->jet_on) or_jet_source(c, U, t, dt);
+    int n[3] = {c->nx, c->ny, c->nz};
+    int act[3], na = 0;
+    for (int d = 0; d < 3; d++) if (n[d] > 1) act[na++] = d;
+    if (na == 0) return dt;
+    for (int k = 0; k < na - 1; k++) or_sweep(c, U, act[k], 0.5 * dt);
+    or_sweep(c, U, act[na - 1], dt);
+    for (int k = na - 2; k >= 0; k--) or_sweep(c, U, act[k], 0.5 * dt);
+    return dt;
+}
+
+/* advance up to nsteps steps (stopping at t_end when t_end > 0); returns steps taken */
+int or_run(const or_config *c, double *U, int nsteps, double t_end, double *t) {
+    int s;
+    for (s = 0; s < nsteps; s++) {
+        if (t_end > 0.0 && *t >= t_end) break;
+        double dt = or_step(c, U, *t, t_end);
+        if (!(dt > 0.0)) break;
+        if (t_end > 0.0 && *t + dt >= t_end) *t = t_end;
+        else *t += dt;
+    }
+    return s;
+}
+
+/* ---------------------------------------------------- whole-field helpers */
+/* sum_cells U * dV for the four conserved fields */
+void or_conservation_sums(const or_config *c, const double *U, double out[4]) {
+    long cells = (long)c->nx * c->ny * c->nz;
+    double dV = c->dx * c->dy * c->dz;
+    for (int q = 0; q < 4; q++) {
+        double s = 0.0;
+        for (long i = 0; i < cells; i++) s += U[q * cells + i];
+        out[q] = s * dV;
+    }
+}
+
+void or_prim2cons_field(const or_config *c, long cells, const double *e, const double *vx,
+                        const double *vy, const double *vz, double *U) {
+    for (long i = 0; i < cells; i++) {
+        double u[4];
+        or_prim2cons(c, e[i], vx[i], vy[i], vz[i], u);
+        for (int q = 0; q < 4; q++) U[q * cells + i] = u[q];
+    }
+}
+
+void or_cons2prim_field(const or_config *c, long cells, const double *U, double *e, double *vx,
+                        double *vy, double *vz, int *iters) {
+    for (long i = 0; i < cells; i++) {
+        double u[4] = {U[i], U[cells + i], U[2 * cells + i], U[3 * cells + i]};
+        double v[3], p;
+        int it = 0;
+        or_cons2prim(c, u, &e[i], v, &p, &it);
+        vx[i] = v[0]; vy[i] = v[1]; vz[i] = v[2];
+        if (iters) iters[i] = it;
+    }
+}

@@ -1,0 +1,93 @@
+"""Closed-form solutions of ideal relativistic hydrodynamics used to pin the oracle.
+
+Written from the physics, independently of the oracle's code:
+
+* the 1-D Riemann problem for p = c^2 e with both states at rest
+  (left-facing rarefaction + right-facing shock), from the Riemann invariant
+  atanh(v) + c/(1+c^2) ln e and the Taub jump conditions
+  s [T^00] = [T^01], s [T^01] = [T^11];
+* the Bjorken boost-invariant flow v = z/t, e = e0 (tau0/tau)^(1+c^2);
+* the Hubble-like 3-D expansion of Sec. 3.2.2, v = r/t,
+  e = e0 (tau0/tau)^(3(1+c^2)).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+from scipy.optimize import brentq
+
+
+def _tmunu(e, v, c2):
+    p = c2 * e
+    g2 = 1.0 / (1.0 - v * v)
+    w = (e + p) * g2
+    return w - p, w * v, w * v * v + p   # T00, T01, T11
+
+
+def _shock_velocity_behind(e_s, e_r, c2):
+    """Fluid velocity behind a right-moving shock into rest state e_r (Taub)."""
+    p_s, p_r = c2 * e_s, c2 * e_r
+
+    def resid(v):
+        t00, t01, t11 = _tmunu(e_s, v, c2)
+        # eliminate the shock speed s = T01 / (T00 - e_r)
+        return t01 * t01 - (t11 - p_r) * (t00 - e_r)
+
+    vmax = 1.0 - 1e-15
+    return brentq(resid, 1e-300, vmax, xtol=1e-16, rtol=1e-15, maxiter=500) if p_s > p_r else 0.0
+
+
+class Riemann:
+    """Exact solution for left state (e_l, v=0), right state (e_r, v=0), e_l > e_r."""
+
+    def __init__(self, e_l=10.0, e_r=1.0, c2=1.0 / 3.0):
+        self.e_l, self.e_r, self.c2 = e_l, e_r, c2
+        self.c = math.sqrt(c2)
+        k = self.c / (1.0 + c2)
+
+        def match(e_s):
+            v_rare = math.tanh(k * math.log(e_l / e_s))
+            return v_rare - _shock_velocity_behind(e_s, e_r, c2)
+
+        self.e_star = brentq(match, e_r * (1 + 1e-12), e_l * (1 - 1e-12), xtol=1e-15,
+                             rtol=1e-15)
+        self.v_star = math.tanh(k * math.log(e_l / self.e_star))
+        t00, t01, _ = _tmunu(self.e_star, self.v_star, c2)
+        self.shock_speed = t01 / (t00 - e_r)
+        self.head = -self.c
+        self.tail = (self.v_star - self.c) / (1.0 - self.v_star * self.c)
+
+    def jump_residuals(self):
+        t00, t01, t11 = _tmunu(self.e_star, self.v_star, self.c2)
+        s = self.shock_speed
+        return (s * (t00 - self.e_r) - t01, s * t01 - (t11 - self.c2 * self.e_r))
+
+    def sample(self, x, t):
+        xi = np.asarray(x, dtype=np.float64) / t
+        e = np.empty_like(xi)
+        v = np.empty_like(xi)
+        c, c2 = self.c, self.c2
+        left = xi < self.head
+        fan = (xi >= self.head) & (xi < self.tail)
+        star = (xi >= self.tail) & (xi < self.shock_speed)
+        right = xi >= self.shock_speed
+        e[left], v[left] = self.e_l, 0.0
+        vf = (xi[fan] + c) / (1.0 + xi[fan] * c)
+        v[fan] = vf
+        e[fan] = self.e_l * ((1.0 - vf) / (1.0 + vf)) ** ((1.0 + c2) / (2.0 * c))
+        e[star], v[star] = self.e_star, self.v_star
+        e[right], v[right] = self.e_r, 0.0
+        return e, v
+
+
+def bjorken(z, t, e0=1.0, tau0=1.0, c2=1.0 / 3.0):
+    z = np.asarray(z, dtype=np.float64)
+    tau = np.sqrt(t * t - z * z)
+    return e0 * (tau0 / tau) ** (1.0 + c2), z / t
+
+
+def hubble(r, t, e0=1.0, tau0=4.0, c2=1.0 / 3.0):
+    r = np.asarray(r, dtype=np.float64)
+    tau = np.sqrt(t * t - r * r)
+    return e0 * (tau0 / tau) ** (3.0 * (1.0 + c2)), r / t

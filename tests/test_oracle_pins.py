@@ -1,0 +1,473 @@
+"""Pins of the CPU oracle against things other than itself.
+
+Each test checks the oracle against a value fixed by the paper or by
+mathematics: the paper's printed limiter functions and their symmetry
+(Sec. 2.5), Lorentz-boosted stress tensors (Eq. 3-4), the paper's own
+fixed-point iteration for Eq. 23, the textbook FORCE flux, exact
+solutions (Riemann problem, Bjorken flow, Hubble-like expansion of
+Sec. 3.2.2), conservation, mirror and axis symmetry, closed forms of the
+tabulated EOS, finite differences for the MLP gradient.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1510_06340_b300 import inputs as I
+from tests import exact
+
+RNG = np.random.default_rng(1510_06340)
+
+
+# ---------------------------------------------------------------- limiters
+def xi_paper(kind, r):
+    """The limiter functions as printed in Sec. 2.5 (Eq. 18-21); MC from van Leer (1977)."""
+    if kind == "minmod":
+        return max(0.0, min(1.0, r))
+    if kind == "superbee":
+        return max(0.0, min(2 * r, 1.0), min(r, 2.0))
+    if kind == "vanleer":
+        return (r + abs(r)) / (1 + abs(r))
+    if kind == "vanalbada":       # clipped to r > 0 (reading R5)
+        return (r * r + r) / (r * r + 1) if r > 0 else 0.0
+    if kind == "mc":
+        return max(0.0, min(2 * r, 0.5 * (1 + r), 2.0))
+    raise KeyError(kind)
+
+
+@pytest.mark.parametrize("kind", ["minmod", "superbee", "vanleer", "vanalbada", "mc"])
+def test_limited_slope_is_a_times_xi_of_r(kind):
+    o = O.Oracle(4, limiter=kind)
+    for _ in range(2000):
+        a, b = RNG.normal(size=2) * 10.0 ** RNG.uniform(-3, 3, size=2)
+        want = a * xi_paper(kind, b / a)
+        got = o.limiter(a, b)
+        assert abs(got - want) <= 1e-14 * max(abs(a), abs(b)), (kind, a, b, got, want)
+
+
+@pytest.mark.parametrize("kind", ["minmod", "superbee", "vanleer", "vanalbada", "mc"])
+def test_limiter_symmetry_and_tvd_region(kind):
+    """xi(1/r) = xi(r)/r (Eq. 22) <=> phi(a, b) = phi(b, a); xi(1) = 1; TVD bounds."""
+    o = O.Oracle(4, limiter=kind)
+    for _ in range(2000):
+        a, b = RNG.normal(size=2)
+        s = o.limiter(a, b)
+        assert abs(s - o.limiter(b, a)) <= 1e-15 * max(abs(a), abs(b))
+        if a * b <= 0:
+            assert s == 0.0
+        else:
+            assert s * a >= 0
+            assert abs(s) <= 2 * min(abs(a), abs(b)) + 1e-15
+        assert abs(o.limiter(a, a) - a) <= 1e-15 * abs(a)
+
+
+def test_no_limiter_is_central_slope():
+    """Eq. 14: Delta_i = (U_{i+1} - U_{i-1}) / 2."""
+    o = O.Oracle(4, limiter="none")
+    for _ in range(100):
+        um, u0, up = RNG.normal(size=3)
+        assert abs(o.limiter(u0 - um, up - u0) - 0.5 * (up - um)) < 1e-15
+
+
+# --------------------------------------------------------- stress tensor
+def boosted_tensor(e, v, c2=1.0 / 3.0):
+    """T^{mu nu} = Lambda diag(e, p, p, p) Lambda^T for the boost taking rest to velocity v."""
+    v = np.asarray(v, dtype=np.float64)
+    v2 = v @ v
+    g = 1.0 / math.sqrt(1.0 - v2)
+    L = np.eye(4)
+    L[0, 0] = g
+    L[0, 1:] = L[1:, 0] = g * v
+    if v2 > 0:
+        L[1:, 1:] += (g - 1.0) * np.outer(v, v) / v2
+    p = c2 * e
+    return L @ np.diag([e, p, p, p]) @ L.T
+
+
+def random_prim(vmax=0.99):
+    e = 10.0 ** RNG.uniform(-2, 2)
+    d = RNG.normal(size=3)
+    d /= np.linalg.norm(d)
+    return e, d * vmax * RNG.uniform() ** (1 / 3)
+
+
+def test_prim2cons_is_boosted_rest_tensor():
+    o = O.Oracle(4)
+    for _ in range(500):
+        e, v = random_prim()
+        T = boosted_tensor(e, v)
+        U = o.prim2cons(e, v)
+        np.testing.assert_allclose(U, T[0], rtol=1e-13, atol=1e-13 * T[0, 0])
+
+
+def test_cons2prim_roundtrip_to_high_velocity():
+    o = O.Oracle(4)
+    for vmax in (0.5, 0.9, 0.999, 0.999999):
+        for _ in range(200):
+            e, v = random_prim(vmax)
+            U = boosted_tensor(e, v)[0]
+            e2, v2, p2, st, _ = o.cons2prim(U)
+            g2 = 1.0 / (1.0 - v @ v)
+            assert st == 0
+            assert np.abs(v2 - v).max() <= 2e-15 * g2 + 1e-15
+            assert abs(e2 - e) <= 1e-14 * e * g2
+            assert abs(p2 - e / 3.0) <= 1e-14 * e * g2
+
+
+def test_cons2prim_matches_paper_fixed_point():
+    """Sec. 2.6 solves Eq. 23 as a fixed point in v; the oracle's closed form is its limit."""
+    o = O.Oracle(4)
+    for _ in range(200):
+        e, v = random_prim(0.95)
+        U = boosted_tensor(e, v)[0]
+        E, M = U[0], np.linalg.norm(U[1:])
+        vv = 0.0
+        for _ in range(2000):
+            vv = M / (E + (E - M * vv) / 3.0)
+        _, v2, _, _, _ = o.cons2prim(U)
+        assert abs(np.linalg.norm(v2) - vv) <= 1e-14
+
+
+def test_cons2prim_caps_and_vacuum():
+    o = O.Oracle(4)
+    e, v, p, st, _ = o.cons2prim([1.0, 2.0, 0.0, 0.0])     # |M| > E
+    assert st == 1 and 0 < v[0] < 1 and p >= 0
+    e, v, p, st, _ = o.cons2prim([-1.0, 0.1, 0.0, 0.0])    # E <= 0
+    assert st == 2 and p == 0 and not v.any()
+
+
+@pytest.mark.parametrize("d", [0, 1, 2])
+def test_flux_is_row_of_boosted_tensor(d):
+    """Eq. 3: F_d = (T^{d0}, T^{dx}, T^{dy}, T^{dz})."""
+    o = O.Oracle(4)
+    for _ in range(300):
+        e, v = random_prim()
+        T = boosted_tensor(e, v)
+        F = o.flux(d, T[0])
+        np.testing.assert_allclose(F, T[1 + d], rtol=1e-12, atol=1e-13 * T[0, 0])
+
+
+# ------------------------------------------------------------ MUSTA-FORCE
+def test_musta_force_is_consistent():
+    for k in (1, 2, 3, 4):
+        o = O.Oracle(4, stages=k)
+        for _ in range(50):
+            e, v = random_prim()
+            U = boosted_tensor(e, v)[0]
+            for d in range(3):
+                F = o.musta_force(d, 0.37, U, U)
+                np.testing.assert_allclose(F, o.flux(d, U), rtol=1e-15, atol=1e-15 * U[0])
+
+
+def test_single_stage_is_textbook_force():
+    """k = 1 is Toro's FORCE flux 1/4 [F_L + 2 F(U_0) + F_R - (dx/dt)(U_R - U_L)],
+    U_0 = (U_L + U_R)/2 - (dt/2dx)(F_R - F_L)  (reading R1 of Eq. 10)."""
+    o = O.Oracle(4, stages=1)
+    lam = 0.31
+    for _ in range(200):
+        UL = boosted_tensor(*random_prim(0.8))[0]
+        UR = boosted_tensor(*random_prim(0.8))[0]
+        d = int(RNG.integers(3))
+        FL, FR = o.flux(d, UL), o.flux(d, UR)
+        U0 = 0.5 * (UL + UR) - 0.5 * lam * (FR - FL)
+        want = 0.25 * (FL + 2.0 * o.flux(d, U0) + FR - (UR - UL) / lam)
+        got = o.musta_force(d, lam, UL, UR)
+        np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-12 * max(UL[0], UR[0]))
+
+
+def test_musta_predictor_fixes_uniform_states():
+    """For U_L = U_R the local Riemann update of Eq. 8 leaves both states unchanged."""
+    o2 = O.Oracle(4, stages=2)
+    U = boosted_tensor(*random_prim(0.6))[0]
+    np.testing.assert_allclose(o2.musta_force(0, 0.4, U, U), o2.flux(0, U), rtol=1e-15)
+
+
+# ------------------------------------------------------------ signal speed
+def test_signal_speed_special_cases():
+    o = O.Oracle(4)
+    c = math.sqrt(1.0 / 3.0)
+    U = boosted_tensor(1.0, [0, 0, 0])[0]
+    for d in range(3):
+        assert abs(o.signal_speed(U, d) - c) < 1e-15
+    for _ in range(100):
+        s = RNG.uniform(-0.99, 0.99)
+        U = boosted_tensor(2.0, [s, 0, 0])[0]
+        # along the flow: relativistic velocity addition
+        assert abs(o.signal_speed(U, 0) - (abs(s) + c) / (1 + abs(s) * c)) < 1e-13
+        # across the flow
+        want = c * math.sqrt((1 - s * s) / (1 - s * s * c * c))
+        assert abs(o.signal_speed(U, 1) - want) < 1e-13
+    for _ in range(300):
+        U = boosted_tensor(*random_prim(0.999))[0]
+        for d in range(3):
+            assert 0 < o.signal_speed(U, d) <= 1.0
+
+
+# ------------------------------------------------------------- Riemann problem
+def test_exact_riemann_solver_jump_conditions():
+    R = exact.Riemann(10.0, 1.0)
+    r1, r2 = R.jump_residuals()
+    assert abs(r1) < 1e-12 and abs(r2) < 1e-12
+    # independently derived star state for e_L = 10, e_R = 1, p = e/3
+    assert abs(R.e_star - 3.139831558201) < 1e-11
+    assert abs(R.v_star - 0.463381465430) < 1e-11
+    assert abs(R.shock_speed - 0.752115385414) < 1e-11
+
+
+def run_shock_tube(n, limiter="minmod", stages=2, rk_order=2, hancock=1):
+    g, prim = I.shock_tube(n)
+    o = O.Oracle(n, dx=g["dx"], x0=-1.0, bc="outflow", limiter=limiter, stages=stages,
+                 rk_order=rk_order, hancock=hancock, cfl=0.4)
+    U = o.prim2cons_field(*prim)
+    nsteps, t = o.run(U, 100000, t_end=0.8)
+    e, vx, _, _, _ = o.cons2prim_field(U)
+    x = I.cell_centres(n, -1.0, g["dx"])
+    ex, vex = exact.Riemann().sample(x, 0.8)
+    l1e = np.abs(e.ravel() - ex).sum() / np.abs(ex).sum()
+    l1v = np.abs(vx.ravel() - vex).sum() / np.abs(vex).sum()
+    return l1e, l1v, nsteps, t, e.ravel(), vx.ravel()
+
+
+def test_shock_tube_converges_to_exact_solution():
+    errs = [run_shock_tube(n)[:2] for n in (250, 500, 1000)]
+    for (e1, v1), (e2, v2) in zip(errs, errs[1:]):
+        assert e2 < e1 / 1.5 and v2 < v1 / 1.5
+    l1e, l1v, nsteps, t, _, _ = run_shock_tube(1000)
+    assert t == 0.8 and 600 < nsteps < 1200
+    assert l1e < 6e-3 and l1v < 1.5e-2
+
+
+def test_more_musta_stages_reduce_error():
+    errs = [run_shock_tube(500, stages=k)[0] for k in (1, 2, 3, 4)]
+    assert all(b < a for a, b in zip(errs, errs[1:])), errs
+
+
+def test_minbee_overshoots_less_than_superbee():
+    """Sec. 3.2.1: Minbee removes most of the velocity overshoot, Superbee enhances it."""
+    R = exact.Riemann()
+    over = {lim: run_shock_tube(500, limiter=lim)[5].max() - R.v_star
+            for lim in ("minmod", "superbee")}
+    assert over["minmod"] < over["superbee"]
+
+
+# ------------------------------------------------------------- smooth flow
+def bjorken_error(n, limiter, rk_order, hancock, t0=2.0, t1=2.4):
+    dx = 2.0 / n
+    z = I.cell_centres(n, -1.0, dx)
+    e, v = exact.bjorken(z, t0)
+    o = O.Oracle(n, dx=dx, x0=-1.0, bc="outflow", limiter=limiter, rk_order=rk_order,
+                 hancock=hancock, fixed_dt=0.2 * dx)
+    zero = np.zeros((1, 1, n))
+    U = o.prim2cons_field(e.reshape(1, 1, n), v.reshape(1, 1, n), zero, zero)
+    o.run(U, 100000, t_end=t1, t=t0)
+    ee, vv, _, _, _ = o.cons2prim_field(U)
+    ex, vex = exact.bjorken(z, t1)
+    m = np.abs(z) < 0.5          # outside the light cone of the boundaries
+    return np.abs(ee.ravel() - ex)[m].mean(), np.abs(vv.ravel() - vex)[m].mean()
+
+
+@pytest.mark.parametrize("limiter,rk_order,hancock,lo,hi", [
+    ("none", 1, 1, 1.8, 2.6),     # single-stage MUSCL-Hancock: second order
+    ("none", 2, 0, 1.8, 2.3),     # RK2 on the plain MUSCL operator: second order
+    ("none", 3, 0, 1.8, 2.3),
+    ("minmod", 1, 1, 1.8, 2.3),
+    ("none", 2, 1, 0.9, 1.2),     # Hancock inside each RK2 stage: first order in time
+])
+def test_bjorken_convergence_order(limiter, rk_order, hancock, lo, hi):
+    e1, v1 = bjorken_error(200, limiter, rk_order, hancock)
+    e2, v2 = bjorken_error(400, limiter, rk_order, hancock)
+    assert lo < math.log2(e1 / e2) < hi
+    assert lo - 0.2 < math.log2(v1 / v2) < hi + 0.3
+
+
+@pytest.mark.parametrize("axis", [1, 2])
+def test_axis_embedding_equals_1d_run(axis):
+    """A 1-D problem along y or z of a 3-D grid (uniform across) equals the 1-D
+    run along x: the transverse sweeps change nothing, Strang gives two half
+    steps along y, one full step along z."""
+    n = 64
+    dx = 2.0 / n
+    z = I.cell_centres(n, -1.0, dx)
+    e, v = exact.bjorken(z, 2.0)
+    dt = 0.2 * dx
+    ref = O.Oracle(n, dx=dx, x0=-1.0, bc="outflow", fixed_dt=dt / 2 if axis == 1 else dt)
+    zero = np.zeros((1, 1, n))
+    U1 = ref.prim2cons_field(e.reshape(1, 1, n), v.reshape(1, 1, n), zero, zero)
+    ref.run(U1, 6 if axis == 1 else 3)
+    shape = [4, 4, 4]
+    shape[2 - axis] = n
+    bc = ["periodic"] * 3
+    bc[axis] = "outflow"
+    o = O.Oracle(shape[2], shape[1], shape[0], dx=dx, bc=tuple(bc), fixed_dt=dt)
+    sl = [None, None, None]
+    sl[2 - axis] = slice(None)
+    ee = np.broadcast_to(e[tuple(sl)], shape).copy()
+    vv = np.broadcast_to(v[tuple(sl)], shape).copy()
+    zz = np.zeros(shape)
+    vel = [zz, zz, zz]
+    vel[axis] = vv
+    U3 = o.prim2cons_field(ee, *vel)
+    o.run(U3, 3)
+    line = [slice(None), 1, 1, 1]
+    line[1 + (2 - axis)] = slice(None)
+    got = U3[tuple(line)]
+    assert np.array_equal(got[0], U1[0].ravel())
+    assert np.array_equal(got[1 + axis], U1[1].ravel())
+    others = [q for q in (1, 2, 3) if q != 1 + axis]
+    assert not got[others].any()
+
+
+def hubble_error(n, dx, dt, nsteps, t0=2.0):
+    lo = -0.5 * n * dx
+    c = I.cell_centres(n, lo, dx)
+    zz, yy, xx = np.meshgrid(c, c, c, indexing="ij")
+    r = np.sqrt(xx * xx + yy * yy + zz * zz)
+    inside = r < t0 - 0.5                      # vacuum outside r < t - 0.5 fm
+    e, vr = exact.hubble(np.where(inside, r, 0.0), t0)
+    e = np.where(inside, e, 0.0)
+    vr = np.where(inside, vr, 0.0)
+    rs = np.where(r > 0, r, 1.0)
+    o = O.Oracle(n, n, n, dx=dx, x0=lo, y0=lo, z0=lo, bc="outflow", fixed_dt=dt)
+    U = o.prim2cons_field(e, vr * xx / rs, vr * yy / rs, vr * zz / rs)
+    o.run(U, nsteps)
+    ee, vx, vy, vz, _ = o.cons2prim_field(U)
+    core = r < 0.5
+    ex, vex = exact.hubble(r[core], t0 + nsteps * dt)
+    vnum = (vx * xx + vy * yy + vz * zz)[core] / rs[core]
+    return np.abs(ee[core] / ex - 1).max(), np.abs(vnum - vex).max()
+
+
+@pytest.mark.slow
+def test_hubble_expansion_interior_converges():
+    """Sec. 3.2.2 (its table: e0 = 1, c_s^2 = 1/3, tau0 = 4, t0 = 2, dx = 0.1, dt = 0.03;
+    vacuum outside r < t - 0.5), on a reduced box: the core follows
+    e = e0 (tau0/tau)^4, v = r/t, and the error falls under refinement at fixed
+    Courant number."""
+    e1, v1 = hubble_error(32, 0.1, 0.03, 10)
+    e2, v2 = hubble_error(64, 0.05, 0.015, 20)
+    assert e1 < 0.04 and v1 < 0.01
+    assert e2 < e1 / 2 and v2 < v1 / 2
+
+
+# --------------------------------------------------------- 3-D invariants
+def blast_oracle(n, limiter="minmod"):
+    g, prim = I.spherical_blast(n)
+    o = O.Oracle(n, n, n, dx=g["dx"], x0=-1.0, y0=-1.0, z0=-1.0, bc="periodic",
+                 limiter=limiter, cfl=0.4)
+    return o, o.prim2cons_field(*prim)
+
+
+@pytest.mark.parametrize("limiter", ["minmod", "mc", "superbee"])
+def test_periodic_blast_conserves_energy_momentum(limiter):
+    o, U = blast_oracle(16, limiter)
+    s0 = o.conservation_sums(U)
+    o.run(U, 8)
+    s1 = o.conservation_sums(U)
+    assert abs(s1[0] - s0[0]) <= 1e-13 * s0[0]
+    assert np.abs(s1[1:]).max() <= 1e-13 * s0[0]
+
+
+def test_blast_mirror_symmetry():
+    """Reflection x -> -x maps the solution to itself with M_x odd (Sec. 2.5, Eq. 22)."""
+    o, U = blast_oracle(16)
+    o.run(U, 6)
+    scale = U[0].max()
+    for ax in range(3):
+        arr_ax = 3 - ax
+        R = np.flip(U, axis=arr_ax).copy()
+        R[1 + ax] *= -1.0
+        assert np.abs(R - U).max() <= 1e-14 * scale
+
+
+# ------------------------------------------------------------ tabulated EOS
+def test_eos_closed_form_derivative_is_cs2():
+    e = np.exp(np.linspace(math.log(1e-5), math.log(1e3), 400))
+    h = 1e-6 * e
+    dp = (I.eos_p_exact(e + h) - I.eos_p_exact(e - h)) / (2 * h)
+    np.testing.assert_allclose(dp, I.eos_cs2_exact(e), rtol=1e-7, atol=1e-9)
+    assert abs(I.eos_p_exact(1e-9) - 1e-9 / 3) < 1e-20       # p -> e/3 at low e
+
+
+def test_eos_table_interpolation_error():
+    tab = I.eos_table()
+    o = O.Oracle(4, eos=tab)
+    h = (tab["lne_max"] - tab["lne_min"]) / (tab["n"] - 1)
+    for e in 10.0 ** RNG.uniform(-5.9, 3.9, size=400):
+        p = o.eos_p(e)
+        # linear interpolation in u = ln e: error <= h^2/8 max|d2p/du2|, d2p/du2 <= ~2e
+        assert abs(p - I.eos_p_exact(e)) <= h * h / 8 * 2.0 * e * 1.01
+        assert abs(o.eos_cs2(e) - I.eos_cs2_exact(e)) <= h * h / 8 * 2.0
+    assert o.eos_p(1e-8) == 1e-8 / 3.0
+    emax = math.exp(tab["lne_max"])
+    assert abs(o.eos_p(2 * emax) - (tab["p"][-1] + tab["cs2"][-1] * emax)) < 1e-9 * emax
+
+
+def test_newton_cons2prim_roundtrip_table_eos():
+    tab = I.eos_table()
+    for seed_kind in (0, 1):
+        o = O.Oracle(4, eos=tab, seed_kind=seed_kind)
+        for _ in range(300):
+            e, v = random_prim(0.999)
+            U = o.prim2cons(e, v)
+            e2, v2, p2, st, it = o.cons2prim(U)
+            g2 = 1.0 / (1.0 - v @ v)
+            assert st == 0 and it < 50
+            assert np.abs(v2 - v).max() < 1e-13 * g2
+            assert abs(e2 - e) < 1e-12 * e * g2
+
+
+def test_newton_root_matches_bracketed_solver():
+    from scipy.optimize import brentq
+    tab = I.eos_table()
+    o = O.Oracle(4, eos=tab)
+    for _ in range(100):
+        e, v = random_prim(0.95)
+        U = o.prim2cons(e, v)
+        E, M = U[0], np.linalg.norm(U[1:])
+        root = brentq(lambda w: w - M / (E + o.eos_p(E - M * w)), 0.0, M / E, xtol=1e-16,
+                      rtol=1e-15)
+        assert abs(np.linalg.norm(o.cons2prim(U)[1]) - root) < 1e-14
+
+
+# ------------------------------------------------------------------- MLP
+def test_mlp_gradient_matches_finite_differences():
+    n = O.mlp_nparam()
+    P = RNG.normal(size=n) * 0.3
+    P[-4:] = [0.5, 2.0, 0.4, 0.3]
+    X = np.column_stack([RNG.uniform(-5, 5, 40), RNG.uniform(0, 0.99, 40)])
+    Y = RNG.uniform(0, 0.9, 40)
+    loss, G = O.mlp_loss_grad(P, X, Y)
+    for idx in list(RNG.choice(n - 4, 60, replace=False)):
+        h = 1e-6
+        Pp, Pm = P.copy(), P.copy()
+        Pp[idx] += h
+        Pm[idx] -= h
+        fd = (O.mlp_loss_grad(Pp, X, Y)[0] - O.mlp_loss_grad(Pm, X, Y)[0]) / (2 * h)
+        assert abs(fd - G[idx]) <= 1e-6 * max(1e-4, abs(G).max())
+    assert not G[-4:].any()
+
+
+def test_round_bf16_matches_library_conversion():
+    import torch
+    x = RNG.normal(size=2000) * 10.0 ** RNG.uniform(-10, 10, size=2000)
+    want = torch.tensor(x, dtype=torch.float32).to(torch.bfloat16).to(torch.float64).numpy()
+    got = np.array([O.round_bf16(v) for v in x])
+    assert np.array_equal(got, want)
+
+
+# --------------------------------------------------------------- jet source
+def test_jet_source_deposits_dedx_per_unit_time():
+    n, dx = 48, 0.1
+    lo = -0.5 * n * dx
+    jet = np.array([0.3, -0.2, 0.1, 0.6, 0.8, 0.0, 5.0, 0.3])
+    o = O.Oracle(n, n, n, dx=dx, x0=lo, y0=lo, z0=lo, jet=jet)
+    U = np.zeros(o.shape)
+    U[0] = 1.0
+    s0 = o.conservation_sums(U)
+    o.jet_source(U, 0.5, 0.02)
+    ds = o.conservation_sums(U) - s0
+    want = 0.02 * 5.0
+    # the Gaussian's tail beyond the box edge (6 sigma away) is ~1e-9 of its mass
+    assert abs(ds[0] - want) < 1e-8 * want
+    np.testing.assert_allclose(ds[1:], want * jet[3:6], atol=1e-8 * want)
