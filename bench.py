@@ -1,0 +1,291 @@
+#!/usr/bin/env python
+"""Benchmark of the MUSTA-FORCE hot path on B300.
+
+Workload (default): 3-D spherical blast on a 256^3 grid over [-1, 1]^3,
+p = e/3, e = 10 inside r < 0.2 and 1 outside, v = 0, periodic boundaries,
+minmod limiter, 2 MUSTA stages, RK2 with the Hancock half step, Strang
+splitting, CFL 0.4, FP32 state.  One step = CFL rate reduction + dt + 5
+directional sweeps.  Metric: cell-updates/s (cells x steps / time).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload blast256_fp32|blast256_fp64|batch512]
+
+Under torchrun each rank runs its own replica of the workload on its own GPU
+(the hot path has no data exchange between grids); value is the whole-job
+rate, the max time over ranks.  --impl reference times the FP64 CPU oracle on
+the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "blast256_fp32": dict(n=256, prec="fp32"),
+    "blast256_fp64": dict(n=256, prec="fp64"),
+}
+BYTES = {"fp32": 4, "fp64": 8}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6400.0), "measured"
+    return 6400.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        loaded = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_baseline_oracle(n=96, steps=1):
+    """The oracle, as it stands, on a bounded sample: the blast recipe on n^3."""
+    from oracle import oracle as O
+    from paper_1510_06340_b300 import inputs as I
+    g, prim = I.spherical_blast(n)
+    o = O.Oracle(n, n, n, dx=g["dx"], x0=-1.0, y0=-1.0, z0=-1.0, bc="periodic",
+                 limiter="minmod", stages=2, cfl=0.4)
+    U = o.prim2cons_field(*prim)
+    t0 = time.perf_counter()
+    o.run(U, steps)
+    el = time.perf_counter() - t0
+    return n ** 3 * steps / el, el, f"blast recipe on {n}^3 (same physics, smaller grid), {steps} step(s)"
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return 0
+    n = 64
+    for _ in range(args.warmup):
+        cpu_baseline_oracle(n, 1)
+    rates, total = [], 0.0
+    for _ in range(args.steps):
+        r, el, sample = cpu_baseline_oracle(n, 1)
+        rates.append(r)
+        total += el
+    value = n ** 3 * args.steps / total
+    line = {"impl": "reference", "metric": "cell_updates_per_s", "value": value,
+            "unit": "cell-updates/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": "3D spherical blast, p=e/3, minmod, "
+                                            "2 MUSTA stages, RK2+Hancock, Strang, periodic; "
+                                            f"oracle sample {n}^3 per step"},
+            "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": 1,
+                             "kind": "oracle", "sample": f"blast recipe on {n}^3, 1 step per timed step"},
+            "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    world, rank, local = dist_setup()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_1510_06340_b300 import build, hydro
+    from paper_1510_06340_b300 import inputs as I
+    if rank == 0:
+        build.build(verbose=False)
+    if world > 1:
+        dist.barrier()
+    wl = WORKLOADS[args.workload]
+    n, prec = wl["n"], wl["prec"]
+    dt_np = np.float64 if prec == "fp64" else np.float32
+    g, prim = I.spherical_blast(n)
+    prim = [np.ascontiguousarray(a, dtype=dt_np) for a in prim]
+    stream = torch.cuda.Stream()
+    grid = hydro.make_grid(n, n, n, dx=g["dx"], x0=-1.0, y0=-1.0, z0=-1.0, bc="periodic",
+                           prec=prec, cfl=0.4)
+    h = hydro.Hydro(grid, limiter="minmod", stages=2, stream=stream)
+    h.set_primitives(*prim)
+    cells = n ** 3
+
+    # warm-up (first call also autotunes the launch shapes)
+    h.step(args.warmup)
+    torch.cuda.synchronize()
+
+    # timed region: device-resident state (2 x state > L2), per-sweep CUDA events
+    h.set_kernel_timing(True)
+    h.kernel_timing()   # reset
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        h.step(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+    ms = e0.elapsed_time(e1)
+    (sweep_ms, other_ms), (n_sweep, n_other) = h.kernel_timing()
+    h.set_kernel_timing(False)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * cells * args.steps / (ms * 1e-3)
+
+    # e2e through the public API with host buffers: upload initial primitives
+    # from pinned memory, step, read each step's conservation sums, read back
+    # the final primitives.
+    pinned = [torch.from_numpy(a).pin_memory() for a in prim]
+    outs = [torch.empty(a.shape, dtype=pinned[0].dtype).pin_memory() for a in prim]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    h.set_primitives(*[p.numpy() for p in pinned])
+    for _ in range(args.steps):
+        h.step(1)
+        h.conservation_sums()
+    e_, vx_, vy_, vz_ = h.get_primitives()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_value = world * cells * args.steps / e2e_s
+    state_bytes = 4 * cells * BYTES[prec]
+
+    hbm, src = peaks()
+    bytes_per_sweep = 2 * 4 * BYTES[prec] * cells      # read + write of 4 fields
+    avg_sweep_ms = sweep_ms / max(n_sweep, 1)
+    achieved = bytes_per_sweep / (avg_sweep_ms * 1e-3) / 1e9
+    launches = n_sweep + 2 * n_other
+
+    cpu = None
+    if rank == 0 and world >= 1 and not args.no_cpu:
+        v, el, sample = cpu_baseline_oracle(96, 1)
+        cpu = {"value": v, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
+               "sample": sample + f", {el:.1f} s"}
+    if rank == 0:
+        line = {
+            "metric": "cell_updates_per_s", "value": value, "unit": "cell-updates/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "f64",
+            "data": "synthetic",
+            "config": {"workload": f"3D spherical blast {n}^3 on [-1,1]^3, p=e/3, "
+                                   f"{prec.upper()}, minmod, 2 MUSTA stages, RK2+Hancock, "
+                                   "Strang, periodic, CFL 0.4",
+                       "cells": cells, "parallelism": f"replicas x{world}",
+                       "l2": "inputs larger than L2 (two state copies of "
+                             f"{state_bytes / 1e6:.0f} MB)"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "traffic": None,
+                         "kernel": "k_sweep (one directional sweep, all RK stages)",
+                         "algorithmic_bytes_per_launch": bytes_per_sweep,
+                         "avg_launch_ms": avg_sweep_ms, "peak_source": src},
+            "kernel_ms": {"sweeps": sweep_ms, "sweep_launches": n_sweep,
+                          "rate_dt": other_ms, "rate_dt_groups": n_other},
+            "gpu_launches": launches,
+            "e2e": {"value": e2e_value, "unit": "cell-updates/s",
+                    "h2d_bytes_per_step": state_bytes / args.steps,
+                    "d2h_bytes_per_step": 32 + state_bytes / args.steps},
+            "clocks": clk.summary(),
+        }
+        if cpu:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="blast256_fp32", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,429 @@
+// aux.cu -- cell-wise kernels around the sweeps: prim->cons (Eq. 4),
+// cons->prim (Eq. 23), the CFL rate reduction, per-event time steps, the jet
+// source, FP64 conservation sums, hot-spot initial states and a finite check.
+#include <cuda_bf16.h>
+
+#include "device.cuh"
+#include "kernels.h"
+
+namespace hy {
+
+// ------------------------------------------------------------------ helpers
+template <class R>
+__device__ __forceinline__ void eos_pc2(const Scheme &sc, R e, R &p, R &c2) {
+    if (sc.eos_kind == EOS_CONFORMAL) {
+        p = R(sc.cs2) * e;
+        c2 = R(sc.cs2);
+    } else {
+        eos_table<R>(sc, e, p, c2);
+    }
+}
+
+// full cons -> prim of one cell: e, velocity vector (Eq. 23 with R9-R11)
+template <class R>
+__device__ __forceinline__ void c2p_full(const Scheme &sc, R E, R Mx, R My, R Mz, R &e, R &vx,
+                                         R &vy, R &vz, int &iters) {
+    iters = 0;
+    const R delta = R(sc.delta);
+    R M2 = Mx * Mx + My * My + Mz * Mz;
+    if (!(E > R(0))) { e = R(0); vx = vy = vz = R(0); return; }
+    const R cap = (R(1) - delta) * E;
+    R s = R(1);
+    if (M2 > cap * cap) {
+        s = cap / dsqrt_(M2);
+        M2 = cap * cap;
+    }
+    if (sc.eos_kind == EOS_CONFORMAL) {
+        const R cs2 = R(sc.cs2);
+        const R a = (R(1) + cs2) * E;
+        R disc = a * a - R(4) * cs2 * M2;
+        disc = disc < R(0) ? R(0) : disc;
+        const R W = R(0.5) * (a + dsqrt_(disc));
+        vx = s * Mx / W; vy = s * My / W; vz = s * Mz / W;
+        e = E - M2 / W;
+        return;
+    }
+    const R M = dsqrt_(M2);
+    R p;
+    const R v = newton_speed<R>(sc, E, M, M2, sc.seed, R(0), p, iters);
+    const R sc_ = M > R(0) ? s * v / M : R(0);
+    vx = Mx * sc_; vy = My * sc_; vz = Mz * sc_;
+    e = E - M * v;
+}
+
+// ------------------------------------------------------------------ prim -> cons
+template <class R>
+__global__ void k_prim2cons(const EventGeo *__restrict__ ev, const WorkItem *__restrict__ items,
+                            int nitems, const R *__restrict__ e, const R *__restrict__ vx,
+                            const R *__restrict__ vy, const R *__restrict__ vz, R *__restrict__ U,
+                            Scheme sc) {
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const WorkItem w = items[it];
+        const EventGeo &g = ev[w.event];
+        for (int k = threadIdx.x; k < w.count; k += blockDim.x) {
+            const long long c = w.first + k;
+            const R ee = e[c], x = vx[c], y = vy[c], z = vz[c];
+            R p, c2;
+            eos_pc2<R>(sc, ee, p, c2);
+            const R g2 = R(1) / (R(1) - (x * x + y * y + z * z));
+            const R wv = (ee + p) * g2;
+            R *u = U + g.off + c;
+            u[0] = wv - p;
+            u[g.cells] = wv * x;
+            u[2 * g.cells] = wv * y;
+            u[3 * g.cells] = wv * z;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ cons -> prim
+template <class R>
+__global__ void k_cons2prim(const EventGeo *__restrict__ ev, const WorkItem *__restrict__ items,
+                            int nitems, const R *__restrict__ U, R *__restrict__ e,
+                            R *__restrict__ vx, R *__restrict__ vy, R *__restrict__ vz, Scheme sc) {
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const WorkItem w = items[it];
+        const EventGeo &g = ev[w.event];
+        for (int k = threadIdx.x; k < w.count; k += blockDim.x) {
+            const long long c = w.first + k;
+            const R *u = U + g.off + c;
+            int iters;
+            c2p_full<R>(sc, u[0], u[g.cells], u[2 * g.cells], u[3 * g.cells], e[c], vx[c], vy[c],
+                        vz[c], iters);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ CFL rate
+// reading R8: largest |characteristic speed| / dx over cells and swept axes
+template <class R>
+__device__ __forceinline__ R char_speed(R vd, R v2, R c2) {
+    const R cs = dsqrt_(c2);
+    R rad = (R(1) - v2) * (R(1) - vd * vd - (v2 - vd * vd) * c2);
+    rad = rad < R(0) ? R(0) : rad;
+    const R den = R(1) - v2 * c2;
+    const R a = vd * (R(1) - c2), b = cs * dsqrt_(rad);
+    return fmax_(fabs_((a + b) / den), fabs_((a - b) / den));
+}
+
+template <class R>
+__global__ void k_rate(const EventGeo *__restrict__ ev, const WorkItem *__restrict__ items,
+                       int nitems, const R *__restrict__ U, EventClock *__restrict__ clk,
+                       Scheme sc) {
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const WorkItem w = items[it];
+        const EventGeo &g = ev[w.event];
+        double m = 0.0;
+        for (int k = threadIdx.x; k < w.count; k += blockDim.x) {
+            const long long c = w.first + k;
+            const R *u = U + g.off + c;
+            R e, vx, vy, vz;
+            int iters;
+            c2p_full<R>(sc, u[0], u[g.cells], u[2 * g.cells], u[3 * g.cells], e, vx, vy, vz, iters);
+            R p, c2;
+            eos_pc2<R>(sc, e, p, c2);
+            const R v2 = vx * vx + vy * vy + vz * vz;
+            const R vd[3] = {vx, vy, vz};
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                if (g.n[d] <= 1) continue;
+                const double r = double(char_speed<R>(vd[d], v2, c2)) / g.h[d];
+                m = (r > m || r != r) ? r : m;   // NaN propagates
+            }
+        }
+        // warp shuffle max, then one atomic per warp
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double x = __shfl_xor_sync(0xffffffffu, m, o);
+            m = (x > m || x != x) ? x : m;
+        }
+        if ((threadIdx.x & 31) == 0)
+            atomicMax(&clk[w.event].rate_bits, (unsigned long long)__double_as_longlong(m));
+    }
+}
+
+// ------------------------------------------------------------------ dt
+// reading R8: dt = cfl / rate (or the fixed dt), clipped to t_end
+__global__ void k_dt(EventClock *__restrict__ clk, double cfl, double fixed_dt, int nevents) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nevents) return;
+    EventClock c = clk[i];
+    const double rate = __longlong_as_double((long long)c.rate_bits);
+    double dt = fixed_dt > 0.0 ? fixed_dt : cfl / rate;
+    if (c.t_end > 0.0 && c.t + dt > c.t_end) dt = c.t_end - c.t;
+    if (!(dt > 0.0)) dt = 0.0;
+    c.t_step = c.t;
+    c.dt = dt;
+    if (dt > 0.0) c.t = (c.t_end > 0.0 && c.t + dt >= c.t_end) ? c.t_end : c.t + dt;
+    if (!(rate == rate) || !(dt == dt)) c.status = 6;
+    c.rate_bits = 0ull;
+    clk[i] = c;
+}
+
+// ------------------------------------------------------------------ jet source
+// reading R12: U += dt S(t_step), S = dEdx (1, n) g(x - x0 - n t)
+template <class R>
+__global__ void k_jet(const EventGeo *__restrict__ ev, const WorkItem *__restrict__ items,
+                      int nitems, R *__restrict__ U, const EventClock *__restrict__ clk) {
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const WorkItem w = items[it];
+        const EventGeo &g = ev[w.event];
+        if (!g.jet_on) continue;
+        const double dt = clk[w.event].dt;
+        if (!(dt > 0.0)) continue;
+        const double t = clk[w.event].t_step;
+        const double *j = g.jet;
+        const double sig = j[7];
+        const double norm = 1.0 / (pow(2.0 * 3.14159265358979323846, 1.5) * sig * sig * sig);
+        const double cx = j[0] + j[3] * t, cy = j[1] + j[4] * t, cz = j[2] + j[5] * t;
+        const double inv2s2 = 1.0 / (2.0 * sig * sig);
+        const int nx = g.n[0], ny = g.n[1];
+        for (int k = threadIdx.x; k < w.count; k += blockDim.x) {
+            const long long c = w.first + k;
+            const int x = int(c % nx);
+            const int y = int((c / nx) % ny);
+            const int z = int(c / ((long long)nx * ny));
+            const double px = g.lo[0] + (x + 0.5) * g.h[0] - cx;
+            const double py = g.lo[1] + (y + 0.5) * g.h[1] - cy;
+            const double pz = g.lo[2] + (z + 0.5) * g.h[2] - cz;
+            const double r2 = (px * px + py * py + pz * pz) * inv2s2;
+            if (r2 > 700.0) continue;   // exp underflows to 0 in double
+            const double s = dt * j[6] * norm * exp(-r2);
+            R *u = U + g.off + c;
+            u[0] = R(double(u[0]) + s);
+            u[g.cells] = R(double(u[g.cells]) + s * j[3]);
+            u[2 * g.cells] = R(double(u[2 * g.cells]) + s * j[4]);
+            u[3 * g.cells] = R(double(u[3 * g.cells]) + s * j[5]);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ FP64 sums
+template <class R>
+__global__ void k_sums(const EventGeo *__restrict__ ev, const WorkItem *__restrict__ items,
+                       int nitems, const R *__restrict__ U, double *__restrict__ partial) {
+    __shared__ double red[4][32];
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const WorkItem w = items[it];
+        const EventGeo &g = ev[w.event];
+        double s[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int k = threadIdx.x; k < w.count; k += blockDim.x) {
+            const R *u = U + g.off + w.first + k;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) s[q] += double(u[q * g.cells]);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s[q] += __shfl_xor_sync(0xffffffffu, s[q], o);
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        if (lane == 0)
+            for (int q = 0; q < 4; ++q) red[q][wid] = s[q];
+        __syncthreads();
+        if (threadIdx.x < 4) {
+            double t = 0.0;
+            for (int k = 0; k < int(blockDim.x >> 5); ++k) t += red[threadIdx.x][k];
+            partial[4LL * it + threadIdx.x] = t;
+        }
+        __syncthreads();
+    }
+}
+
+// one thread per (event, field): items of an event are consecutive
+__global__ void k_sums_final(const WorkItem *__restrict__ items, int nitems,
+                             const double *__restrict__ partial, const EventGeo *__restrict__ ev,
+                             double *__restrict__ out, int nevents) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 4 * nevents) return;
+    const int e = i / 4, q = i % 4;
+    // binary search for the first item of event e
+    int lo = 0, hi = nitems;
+    while (lo < hi) {
+        const int mid = (lo + hi) / 2;
+        if (items[mid].event < e) lo = mid + 1; else hi = mid;
+    }
+    double s = 0.0;
+    for (int it = lo; it < nitems && items[it].event == e; ++it) s += partial[4LL * it + q];
+    const EventGeo &g = ev[e];
+    out[i] = s * (g.h[0] * g.h[1] * g.h[2]);
+}
+
+// ------------------------------------------------------------------ hot spots
+template <class R>
+__global__ void k_hotspots(const EventGeo *__restrict__ ev, const WorkItem *__restrict__ items,
+                           int nitems, const double *__restrict__ spots, int nspots, double sigma,
+                           double e_bg, R *__restrict__ U, Scheme sc) {
+    const double inv = 1.0 / (2.0 * sigma * sigma);
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const WorkItem w = items[it];
+        const EventGeo &g = ev[w.event];
+        const double *sp = spots + (long long)w.event * nspots * 7;
+        const int nx = g.n[0], ny = g.n[1];
+        for (int k = threadIdx.x; k < w.count; k += blockDim.x) {
+            const long long c = w.first + k;
+            const int x = int(c % nx);
+            const int y = int((c / nx) % ny);
+            const int z = int(c / ((long long)nx * ny));
+            const double px = g.lo[0] + (x + 0.5) * g.h[0];
+            const double py = g.lo[1] + (y + 0.5) * g.h[1];
+            const double pz = g.lo[2] + (z + 0.5) * g.h[2];
+            double e = e_bg, mx = 0.0, my = 0.0, mz = 0.0;
+            for (int s = 0; s < nspots; ++s) {
+                const double *q = sp + 7 * s;
+                const double dx = px - q[0], dy = py - q[1], dz = pz - q[2];
+                const double a = q[3] * exp(-(dx * dx) * inv) * exp(-(dy * dy) * inv) *
+                                 exp(-(dz * dz) * inv);
+                e += a;
+                mx += a * q[4];
+                my += a * q[5];
+                mz += a * q[6];
+            }
+            const double vx = mx / e, vy = my / e, vz = mz / e;
+            double p, c2;
+            eos_pc2<double>(sc, e, p, c2);
+            const double g2 = 1.0 / (1.0 - (vx * vx + vy * vy + vz * vz));
+            const double wv = (e + p) * g2;
+            R *u = U + g.off + c;
+            u[0] = R(wv - p);
+            u[g.cells] = R(wv * vx);
+            u[2 * g.cells] = R(wv * vy);
+            u[3 * g.cells] = R(wv * vz);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ finite check
+template <class R>
+__global__ void k_finite(const EventGeo *__restrict__ ev, const WorkItem *__restrict__ items,
+                         int nitems, const R *__restrict__ U, EventClock *__restrict__ clk) {
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const WorkItem w = items[it];
+        const EventGeo &g = ev[w.event];
+        bool bad = false;
+        for (int k = threadIdx.x; k < w.count; k += blockDim.x) {
+            const R *u = U + g.off + w.first + k;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) bad |= !isfinite(double(u[q * g.cells]));
+        }
+        if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) clk[w.event].status = 6;
+    }
+}
+
+// ------------------------------------------------------------------ Newton test hook
+template <class R>
+__global__ void k_c2p_newton(Scheme sc, const R *__restrict__ U, long long n, int seed,
+                             R *__restrict__ vmag, int *__restrict__ iters) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const R E = U[i], Mx = U[n + i], My = U[2 * n + i], Mz = U[3 * n + i];
+    R M2 = Mx * Mx + My * My + Mz * Mz;
+    if (!(E > R(0))) { vmag[i] = R(0); iters[i] = 0; return; }
+    const R cap = (R(1) - R(sc.delta)) * E;
+    if (M2 > cap * cap) M2 = cap * cap;
+    const R M = dsqrt_(M2);
+    R p;
+    int it;
+    vmag[i] = newton_speed<R>(sc, E, M, M2, seed, R(0), p, it);
+    iters[i] = it;
+}
+
+// ------------------------------------------------------------------ launchers
+#define HY_DISPATCH(prec, call_d, call_f) \
+    do {                                  \
+        if ((prec) == 0) { call_d; }      \
+        else { call_f; }                  \
+    } while (0)
+
+cudaError_t launch_prim2cons(const CellLaunch &c, const void *e, const void *vx, const void *vy,
+                             const void *vz, void *U) {
+    HY_DISPATCH(c.prec,
+        (k_prim2cons<double><<<c.blocks, c.threads, 0, c.stream>>>(c.ev, c.items, c.nitems,
+            (const double *)e, (const double *)vx, (const double *)vy, (const double *)vz,
+            (double *)U, c.sc)),
+        (k_prim2cons<float><<<c.blocks, c.threads, 0, c.stream>>>(c.ev, c.items, c.nitems,
+            (const float *)e, (const float *)vx, (const float *)vy, (const float *)vz,
+            (float *)U, c.sc)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cons2prim(const CellLaunch &c, const void *U, void *e, void *vx, void *vy,
+                             void *vz) {
+    HY_DISPATCH(c.prec,
+        (k_cons2prim<double><<<c.blocks, c.threads, 0, c.stream>>>(c.ev, c.items, c.nitems,
+            (const double *)U, (double *)e, (double *)vx, (double *)vy, (double *)vz, c.sc)),
+        (k_cons2prim<float><<<c.blocks, c.threads, 0, c.stream>>>(c.ev, c.items, c.nitems,
+            (const float *)U, (float *)e, (float *)vx, (float *)vy, (float *)vz, c.sc)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rate(const CellLaunch &c, const void *U, EventClock *clk, double) {
+    HY_DISPATCH(c.prec,
+        (k_rate<double><<<c.blocks, c.threads, 0, c.stream>>>(c.ev, c.items, c.nitems,
+            (const double *)U, clk, c.sc)),
+        (k_rate<float><<<c.blocks, c.threads, 0, c.stream>>>(c.ev, c.items, c.nitems,
+            (const float *)U, clk, c.sc)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dt(EventClock *clk, const double *cfl_fixed, int nevents, cudaStream_t s) {
+    k_dt<<<(nevents + 127) / 128, 128, 0, s>>>(clk, cfl_fixed[0], cfl_fixed[1], nevents);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_jet(const CellLaunch &c, void *U, const EventClock *clk) {
+    HY_DISPATCH(c.prec,
+        (k_jet<double><<<c.blocks, c.threads, 0, c.stream>>>(c.ev, c.items, c.nitems,
+            (double *)U, clk)),
+        (k_jet<float><<<c.blocks, c.threads, 0, c.stream>>>(c.ev, c.items, c.nitems,
+            (float *)U, clk)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sums(const CellLaunch &c, const void *U, double *partial) {
+    HY_DISPATCH(c.prec,
+        (k_sums<double><<<c.blocks, c.threads, 0, c.stream>>>(c.ev, c.items, c.nitems,
+            (const double *)U, partial)),
+        (k_sums<float><<<c.blocks, c.threads, 0, c.stream>>>(c.ev, c.items, c.nitems,
+            (const float *)U, partial)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sums_final(const WorkItem *items, int nitems, const double *partial,
+                              const EventGeo *ev, double *out, int nevents, cudaStream_t s) {
+    k_sums_final<<<(4 * nevents + 127) / 128, 128, 0, s>>>(items, nitems, partial, ev, out,
+                                                           nevents);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hotspots(const CellLaunch &c, const double *spots, int nspots, double sigma,
+                            double e_bg, void *U) {
+    HY_DISPATCH(c.prec,
+        (k_hotspots<double><<<c.blocks, c.threads, 0, c.stream>>>(c.ev, c.items, c.nitems, spots,
+            nspots, sigma, e_bg, (double *)U, c.sc)),
+        (k_hotspots<float><<<c.blocks, c.threads, 0, c.stream>>>(c.ev, c.items, c.nitems, spots,
+            nspots, sigma, e_bg, (float *)U, c.sc)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finite(const CellLaunch &c, const void *U, EventClock *clk) {
+    HY_DISPATCH(c.prec,
+        (k_finite<double><<<c.blocks, c.threads, 0, c.stream>>>(c.ev, c.items, c.nitems,
+            (const double *)U, clk)),
+        (k_finite<float><<<c.blocks, c.threads, 0, c.stream>>>(c.ev, c.items, c.nitems,
+            (const float *)U, clk)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_c2p_newton(int prec, const Scheme &sc, const void *U, long long n, int seed,
+                              void *vmag, int *iters, cudaStream_t s) {
+    const int th = 128;
+    const long long bl = (n + th - 1) / th;
+    HY_DISPATCH(prec,
+        (k_c2p_newton<double><<<(unsigned)bl, th, 0, s>>>(sc, (const double *)U, n, seed,
+            (double *)vmag, iters)),
+        (k_c2p_newton<float><<<(unsigned)bl, th, 0, s>>>(sc, (const float *)U, n, seed,
+            (float *)vmag, iters)));
+    return cudaGetLastError();
+}
+
+}  // namespace hy

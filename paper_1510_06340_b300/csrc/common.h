@@ -1,0 +1,82 @@
+// common.h -- constants and plain structs shared by the host code and the
+// kernels of libhydro (no CUDA types).
+#pragma once
+
+namespace hy {
+
+enum { LIM_NONE = 0, LIM_MINMOD = 1, LIM_MC = 2, LIM_SUPERBEE = 3, LIM_VANLEER = 4,
+       LIM_VANALBADA = 5 };
+enum { BC_PERIODIC = 0, BC_OUTFLOW = 1 };
+enum { EOS_CONFORMAL = 0, EOS_TABLE = 1 };
+enum { SEED_ZERO = 0, SEED_CONFORMAL = 1, SEED_MLP = 2 };
+enum { CNT_CAPPED = 0, CNT_FACE_FALLBACK = 1, CNT_NEWTON_CALLS = 2, CNT_NEWTON_ITERS = 3,
+       CNT_NEWTON_FAIL = 4, CNT_F64_REDO = 5, NCOUNTERS = 6 };
+
+constexpr int NEWTON_MAX_IT = 50;
+constexpr double DELTA_F64 = 1e-12;   // admissibility margin |M| < (1 - delta) E
+constexpr double DELTA_F32 = 1e-6;
+
+// Newton seed MLP: W1[32][2] b1[32] W2[32][32] b2[32] W3[32] b3 mu0 s0 mu1 s1
+constexpr int MLP_H = 32;
+constexpr int MLP_NPARAM = MLP_H * 2 + MLP_H + MLP_H * MLP_H + MLP_H + MLP_H + 1 + 4;
+constexpr int MLP_OFF_W1 = 0;
+constexpr int MLP_OFF_B1 = MLP_OFF_W1 + 2 * MLP_H;
+constexpr int MLP_OFF_W2 = MLP_OFF_B1 + MLP_H;
+constexpr int MLP_OFF_B2 = MLP_OFF_W2 + MLP_H * MLP_H;
+constexpr int MLP_OFF_W3 = MLP_OFF_B2 + MLP_H;
+constexpr int MLP_OFF_B3 = MLP_OFF_W3 + MLP_H;
+constexpr int MLP_OFF_NORM = MLP_OFF_B3 + 1;
+
+// Per-event geometry, resident on the device.
+struct EventGeo {
+    long long off;       // element offset of field 0 of this event in the state buffer
+    long long cells;     // nx * ny * nz; field f starts at off + f * cells
+    int n[3];
+    int bc[3];
+    int seg[3];          // pencil segments per axis (launch shape)
+    int segL[3];         // nominal segment length per axis
+    double h[3];
+    double lo[3];        // lower corner
+    double jet[8];
+    int jet_on;
+    int pad;
+};
+
+// Per-event time keeping, resident on the device.
+struct EventClock {
+    double t;            // time reached
+    double t_step;       // time at the start of the current step
+    double dt;           // current step
+    double t_end;        // > 0: stop here
+    unsigned long long rate_bits;   // max over cells of speed/dx (double bits, >= 0)
+    int status;
+    int pad;
+};
+
+// A block's share of a launch: `count` consecutive units of one event
+// starting at `first` (pencil-segment tasks for sweeps, cells otherwise).
+struct WorkItem {
+    int event;
+    int count;
+    long long first;
+};
+
+// Scheme constants of one launch (uniform over its threads).
+struct Scheme {
+    int limiter, stages, hancock;
+    double alpha;
+    double delta;            // admissibility margin of this precision
+    int eos_kind;            // EOS_CONFORMAL / EOS_TABLE
+    double cs2;
+    int tab_n;
+    double lne_min, lne_max, inv_h, e_max;
+    const double *p_tab64, *c2_tab64;
+    const float *p_tab32, *c2_tab32;
+    int seed;
+    double tol;
+    const void *mlp_w;            // bf16 W1 [32][2], W2 [32][32], W3 [32]
+    const float *mlp_f;           // fp32 copy of the full parameter vector
+    unsigned long long *counters; // [NCOUNTERS] or null
+};
+
+}  // namespace hy

@@ -1,0 +1,544 @@
+// device.cuh -- device-side physics and the streaming pencil sweep of the
+// MUSTA-FORCE update (Sec. 2.3-2.6 of the paper).
+//
+// Design: one thread marches one pencil segment along the sweep axis.  Each
+// Runge-Kutta stage is a streaming "engine" holding a three-cell window: a
+// new cell value arriving lets it finish the limited faces and Hancock half
+// step of the previous cell (Eq. 13, 15-17), the MUSTA-FORCE flux of the
+// interface before it (Eq. 8-11) and the divergence of the cell before that.
+// Stages are chained in registers, so a sweep reads and writes every cell
+// once; the halo of a segment (2 cells per stage on each side) is
+// recomputed by the neighbouring segment instead of exchanged.
+//
+// The momentum component along the sweep axis is always carried in slot n of
+// V4, so one kernel serves all three axes; only the addressing differs.
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "common.h"
+
+namespace hy {
+
+template <class R>
+struct V4 {
+    R e, n, t1, t2;   // E, M along the sweep axis, the two transverse M
+};
+
+template <class R>
+__device__ __forceinline__ V4<R> v4(R a, R b, R c, R d) {
+    V4<R> v; v.e = a; v.n = b; v.t1 = c; v.t2 = d; return v;
+}
+
+// ---------------------------------------------------------------- math helpers
+__device__ __forceinline__ double dsqrt_(double x) { return sqrt(x); }
+__device__ __forceinline__ float dsqrt_(float x) { return sqrtf(x); }
+__device__ __forceinline__ double rcp_(double x) { return 1.0 / x; }
+__device__ __forceinline__ float rcp_(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double fmax_(double a, double b) { return fmax(a, b); }
+__device__ __forceinline__ float fmax_(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double fmin_(double a, double b) { return fmin(a, b); }
+__device__ __forceinline__ float fmin_(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ double fabs_(double a) { return fabs(a); }
+__device__ __forceinline__ float fabs_(float a) { return fabsf(a); }
+
+// ---------------------------------------------------------------- limiters
+// Sec. 2.5 (Eq. 15-21), division-free: returns a * xi(b / a).
+template <class R>
+__device__ __forceinline__ R limited_slope(int kind, R a, R b) {
+    const R ab = a * b;
+    const R half = R(0.5), two = R(2);
+    if (kind == LIM_NONE) return half * (a + b);
+    if (!(ab > R(0))) return R(0);
+    const R aa = fabs_(a), bb = fabs_(b);
+    R m;
+    switch (kind) {
+    case LIM_MINMOD: m = fmin_(aa, bb); break;
+    case LIM_MC: m = fmin_(fmin_(two * aa, two * bb), half * fabs_(a + b)); break;
+    case LIM_SUPERBEE: m = fmax_(fmin_(two * aa, bb), fmin_(aa, two * bb)); break;
+    case LIM_VANLEER: return two * ab / (a + b);
+    default: return ab * (a + b) / (a * a + b * b);   // van Albada (r > 0)
+    }
+    return a > R(0) ? m : -m;
+}
+
+__device__ __forceinline__ void count(const Scheme &s, int which, unsigned long long v = 1) {
+    if (s.counters) atomicAdd(s.counters + which, v);
+}
+
+// ---------------------------------------------------------------- cons -> prim
+// What a flux evaluation needs from Eq. 23: velocity along the sweep axis and p.
+template <class R>
+struct Prim {
+    R vn, p;
+};
+
+// Conformal EOS p = cs2 e (reading R10): W = E + p is the positive root of
+// W^2 - (1+cs2) E W + cs2 M^2 = 0; |M| is capped at (1 - delta) E (R9).
+template <class R>
+__device__ __forceinline__ Prim<R> c2p_conformal(const V4<R> &U, R cs2, R delta, R &M2out,
+                                                 R &Wout, const Scheme &sc) {
+    Prim<R> q;
+    const R E = U.e;
+    R M2 = U.n * U.n + U.t1 * U.t1 + U.t2 * U.t2;
+    if (!(E > R(0))) {
+        q.vn = R(0); q.p = R(0); M2out = R(0); Wout = R(0);
+        return q;
+    }
+    const R cap = (R(1) - delta) * E;
+    R s = R(1);
+    if (M2 > cap * cap) {
+        s = cap / dsqrt_(M2);
+        M2 = cap * cap;
+        count(sc, CNT_CAPPED);
+    }
+    const R a = (R(1) + cs2) * E;
+    R disc = a * a - R(4) * cs2 * M2;
+    disc = disc < R(0) ? R(0) : disc;
+    const R W = R(0.5) * (a + dsqrt_(disc));
+    q.vn = (s * U.n) / W;
+    q.p = W - E;
+    M2out = M2; Wout = W;
+    return q;
+}
+
+// Tabulated EOS (reading R11): linear interpolation in ln e.
+template <class R>
+__device__ __forceinline__ void eos_table(const Scheme &sc, R e, R &p, R &c2);
+
+template <>
+__device__ __forceinline__ void eos_table<double>(const Scheme &sc, double e, double &p,
+                                                  double &c2) {
+    if (!(e > 0.0)) { p = 0.0; c2 = 1.0 / 3.0; return; }
+    const double lne = log(e);
+    if (lne < sc.lne_min) { p = e / 3.0; c2 = 1.0 / 3.0; return; }
+    const double u = (lne - sc.lne_min) * sc.inv_h;
+    const int n = sc.tab_n;
+    if (u >= double(n - 1)) {
+        p = __ldg(sc.p_tab64 + n - 1) + __ldg(sc.c2_tab64 + n - 1) * (e - sc.e_max);
+        c2 = __ldg(sc.c2_tab64 + n - 1);
+        return;
+    }
+    const int i = int(floor(u));
+    const double f = u - double(i);
+    const double p0 = __ldg(sc.p_tab64 + i), p1 = __ldg(sc.p_tab64 + i + 1);
+    const double c0 = __ldg(sc.c2_tab64 + i), c1 = __ldg(sc.c2_tab64 + i + 1);
+    p = p0 + f * (p1 - p0);
+    c2 = c0 + f * (c1 - c0);
+}
+
+template <>
+__device__ __forceinline__ void eos_table<float>(const Scheme &sc, float e, float &p, float &c2) {
+    if (!(e > 0.0f)) { p = 0.0f; c2 = 1.0f / 3.0f; return; }
+    const float lne = __logf(e);
+    if (lne < float(sc.lne_min)) { p = e * (1.0f / 3.0f); c2 = 1.0f / 3.0f; return; }
+    const float u = (lne - float(sc.lne_min)) * float(sc.inv_h);
+    const int n = sc.tab_n;
+    if (u >= float(n - 1)) {
+        p = __ldg(sc.p_tab32 + n - 1) + __ldg(sc.c2_tab32 + n - 1) * (e - float(sc.e_max));
+        c2 = __ldg(sc.c2_tab32 + n - 1);
+        return;
+    }
+    const int i = int(floorf(u));
+    const float f = u - float(i);
+    const float p0 = __ldg(sc.p_tab32 + i), p1 = __ldg(sc.p_tab32 + i + 1);
+    const float c0 = __ldg(sc.c2_tab32 + i), c1 = __ldg(sc.c2_tab32 + i + 1);
+    p = fmaf(f, p1 - p0, p0);
+    c2 = fmaf(f, c1 - c0, c0);
+}
+
+}  // namespace hy
+#include "mlp_device.cuh"
+namespace hy {
+
+// Safeguarded Newton on f(v) = v - M / (E + p(E - M v)) in [0, M/E] (R11).
+// Returns |v|; iters receives the iteration count.
+enum { SEED_GIVEN = 100 };   // internal: start from the value passed in
+
+template <class R>
+__device__ __forceinline__ R newton_speed(const Scheme &sc, R E, R M, R M2, int seed, R given,
+                                          R &p_out, int &iters) {
+    R lo = R(0), hi = M / E;
+    R v;
+    if (seed == SEED_GIVEN) {
+        v = given;
+    } else if (seed == SEED_CONFORMAL) {
+        const R a = R(4.0 / 3.0) * E;
+        R disc = a * a - R(4.0 / 3.0) * M2;
+        disc = disc < R(0) ? R(0) : disc;
+        v = M / (R(0.5) * (a + dsqrt_(disc)));
+    } else if (seed == SEED_MLP) {
+        v = R(mlp_seed_scalar(sc, float(log(double(E))), float(M / E)));
+    } else {
+        v = R(0);
+    }
+    v = v < lo ? lo : v;
+    v = v > hi ? hi : v;
+    R p = R(0), c2 = R(0);
+    int it = 0;
+    bool conv = false;
+    if (M == R(0)) {
+        v = R(0);
+        conv = true;
+    } else {
+        for (it = 1; it <= NEWTON_MAX_IT; ++it) {
+            eos_table<R>(sc, E - M * v, p, c2);
+            const R W = E + p;
+            const R f = v - M / W;
+            if (f == R(0)) { conv = true; break; }
+            if (f > R(0)) hi = v; else lo = v;
+            const R fp = R(1) - c2 * M2 / (W * W);
+            R vn = v - f / fp;
+            if (!(vn > lo && vn < hi)) vn = R(0.5) * (lo + hi);
+            const R dv = vn - v;
+            v = vn;
+            if (fabs_(dv) <= R(sc.tol)) { conv = true; break; }
+        }
+        if (it > NEWTON_MAX_IT) it = NEWTON_MAX_IT;
+    }
+    if (sc.counters) {
+        count(sc, CNT_NEWTON_CALLS);
+        count(sc, CNT_NEWTON_ITERS, (unsigned long long)it);
+        if (!conv) count(sc, CNT_NEWTON_FAIL);
+    }
+    eos_table<R>(sc, E - M * v, p, c2);
+    p_out = p;
+    iters = it;
+    return v;
+}
+
+template <class R>
+__device__ __forceinline__ Prim<R> c2p_table(const V4<R> &U, R delta, const Scheme &sc,
+                                             int seed, R given, R &vmag) {
+    // seed == SEED_MLP requires the whole warp to be converged here
+    Prim<R> q;
+    const R E = U.e;
+    R M2 = U.n * U.n + U.t1 * U.t1 + U.t2 * U.t2;
+    if (seed == SEED_MLP) {
+        // warp-wide tensor-core seed, taken before any lane-dependent branch
+        const float Ef = E > R(0) ? float(E) : 1.0f;
+        float xf = E > R(0) ? float(dsqrt_(M2) / E) : 0.0f;
+        xf = fminf(xf, 1.0f - float(delta));
+        given = R(mlp_seed_warp(sc, __logf(Ef), xf));
+        seed = SEED_GIVEN;
+    }
+    if (!(E > R(0))) { q.vn = R(0); q.p = R(0); vmag = R(0); return q; }
+    const R cap = (R(1) - delta) * E;
+    if (M2 > cap * cap) {
+        M2 = cap * cap;
+        count(sc, CNT_CAPPED);
+    }
+    const R M = dsqrt_(M2);
+    R p;
+    int it;
+    const R v = newton_speed<R>(sc, E, M, M2, seed, given, p, it);
+    vmag = v;
+    const R Mfull = dsqrt_(U.n * U.n + U.t1 * U.t1 + U.t2 * U.t2);
+    q.vn = Mfull > R(0) ? U.n * (v / Mfull) : R(0);
+    q.p = p;
+    return q;
+}
+
+// Precision policy of a sweep: storage/flux type R and the cons->prim rule.
+enum { PREC_F64 = 0, PREC_F32 = 1, PREC_MIXED = 2 };
+
+template <class R, int PREC, int EOSK>
+struct Physics {
+    Scheme sc;
+    R cs2, delta;
+
+    // cons -> prim for a flux evaluation (Eq. 23)
+    __device__ __forceinline__ Prim<R> prim(const V4<R> &U) const {
+        if (EOSK == EOS_CONFORMAL) {
+            R M2, W;
+            Prim<R> q = c2p_conformal<R>(U, cs2, delta, M2, W, sc);
+            if (PREC == PREC_MIXED) {
+                // |v|^2 = M2 / W^2 > 0.99^2: redo in double (cancellation in W - E)
+                if (M2 > R(0.9801) * W * W) {
+                    V4<double> D = v4<double>(U.e, U.n, U.t1, U.t2);
+                    double M2d, Wd;
+                    Prim<double> qd = c2p_conformal<double>(D, double(cs2), DELTA_F64, M2d, Wd, sc);
+                    q.vn = R(qd.vn);
+                    q.p = R(qd.p);
+                    count(sc, CNT_F64_REDO);
+                }
+            }
+            return q;
+        } else {
+            R vmag;
+            Prim<R> q = c2p_table<R>(U, delta, sc, sc.seed, R(0), vmag);
+            if (PREC == PREC_MIXED) {
+                if (vmag > R(0.99)) {   // redo in double, seeded by the float root
+                    V4<double> D = v4<double>(U.e, U.n, U.t1, U.t2);
+                    double vd;
+                    Prim<double> qd = c2p_table<double>(D, DELTA_F64, sc, SEED_GIVEN,
+                                                        double(vmag), vd);
+                    q.vn = R(qd.vn);
+                    q.p = R(qd.p);
+                    count(sc, CNT_F64_REDO);
+                }
+            }
+            return q;
+        }
+    }
+
+    // Eq. 3 along the sweep axis
+    __device__ __forceinline__ V4<R> flux(const V4<R> &U) const {
+        const Prim<R> q = prim(U);
+        V4<R> F;
+        F.e = (U.e + q.p) * q.vn;
+        F.n = U.n * q.vn + q.p;
+        F.t1 = U.t1 * q.vn;
+        F.t2 = U.t2 * q.vn;
+        return F;
+    }
+
+    __device__ __forceinline__ bool admissible(const V4<R> &U) const {
+        const R M2 = U.n * U.n + U.t1 * U.t1 + U.t2 * U.t2;
+        const R cap = (R(1) - delta) * U.e;
+        return U.e > R(0) && M2 < cap * cap;
+    }
+
+    // Limited MUSCL faces (Eq. 15-17) and the Hancock half step (Eq. 13, the
+    // sweep-axis term), with the admissibility fallback (R9).
+    __device__ __forceinline__ void faces(const V4<R> &vm, const V4<R> &v0, const V4<R> &vp, R lam,
+                                          V4<R> &ul, V4<R> &ur) const {
+        const int lim = sc.limiter;
+        const R half = R(0.5);
+        R s;
+        s = limited_slope<R>(lim, v0.e - vm.e, vp.e - v0.e);
+        ul.e = v0.e - half * s; ur.e = v0.e + half * s;
+        s = limited_slope<R>(lim, v0.n - vm.n, vp.n - v0.n);
+        ul.n = v0.n - half * s; ur.n = v0.n + half * s;
+        s = limited_slope<R>(lim, v0.t1 - vm.t1, vp.t1 - v0.t1);
+        ul.t1 = v0.t1 - half * s; ur.t1 = v0.t1 + half * s;
+        s = limited_slope<R>(lim, v0.t2 - vm.t2, vp.t2 - v0.t2);
+        ul.t2 = v0.t2 - half * s; ur.t2 = v0.t2 + half * s;
+        if (sc.hancock) {
+            const V4<R> FL = flux(ul), FR = flux(ur);
+            const R hl = half * lam;
+            R d;
+            d = FL.e - FR.e;  ul.e += hl * d;  ur.e += hl * d;
+            d = FL.n - FR.n;  ul.n += hl * d;  ur.n += hl * d;
+            d = FL.t1 - FR.t1; ul.t1 += hl * d; ur.t1 += hl * d;
+            d = FL.t2 - FR.t2; ul.t2 += hl * d; ur.t2 += hl * d;
+        }
+        if (!admissible(ul) || !admissible(ur)) {
+            ul = v0; ur = v0;
+            count(sc, CNT_FACE_FALLBACK);
+        }
+    }
+
+    // MUSTA-FORCE interface flux (Sec. 2.4 steps 1-5, Eq. 8-11; R1, R2, R4)
+    __device__ __forceinline__ V4<R> musta(V4<R> UL, V4<R> UR, R lam) const {
+        const R al = R(sc.alpha) * lam;
+        const R clw = R(0.5) * al;
+        const R clf = R(0.5) / al;
+        const R half = R(0.5);
+        V4<R> Fc;
+        const int k = sc.stages;
+#pragma unroll 1
+        for (int l = 0; l < k; ++l) {
+            const V4<R> FL = flux(UL), FR = flux(UR);
+            V4<R> Ulw;
+            Ulw.e = half * (UL.e + UR.e) - clw * (FR.e - FL.e);
+            Ulw.n = half * (UL.n + UR.n) - clw * (FR.n - FL.n);
+            Ulw.t1 = half * (UL.t1 + UR.t1) - clw * (FR.t1 - FL.t1);
+            Ulw.t2 = half * (UL.t2 + UR.t2) - clw * (FR.t2 - FL.t2);
+            const V4<R> Flw = flux(Ulw);
+            Fc.e = half * (Flw.e + (half * (FL.e + FR.e) - clf * (UR.e - UL.e)));
+            Fc.n = half * (Flw.n + (half * (FL.n + FR.n) - clf * (UR.n - UL.n)));
+            Fc.t1 = half * (Flw.t1 + (half * (FL.t1 + FR.t1) - clf * (UR.t1 - UL.t1)));
+            Fc.t2 = half * (Flw.t2 + (half * (FL.t2 + FR.t2) - clf * (UR.t2 - UL.t2)));
+            if (l < k - 1) {
+                UL.e = UL.e - lam * (Fc.e - FL.e);
+                UL.n = UL.n - lam * (Fc.n - FL.n);
+                UL.t1 = UL.t1 - lam * (Fc.t1 - FL.t1);
+                UL.t2 = UL.t2 - lam * (Fc.t2 - FL.t2);
+                UR.e = UR.e - lam * (FR.e - Fc.e);
+                UR.n = UR.n - lam * (FR.n - Fc.n);
+                UR.t1 = UR.t1 - lam * (FR.t1 - Fc.t1);
+                UR.t2 = UR.t2 - lam * (FR.t2 - Fc.t2);
+            }
+        }
+        return Fc;
+    }
+};
+
+// One Runge-Kutta stage as a streaming engine.  After push(V_j):
+//   window (w0, w1, w2) = (V_{j-2}, V_{j-1}, V_j); faces of cell j-1 are
+//   computed; the flux of interface (j-2)+1/2 once faces of j-2 exist; and
+//   the divergence D_{j-2} = F_{j-3/2} - F_{j-5/2} once both fluxes exist.
+template <class R>
+struct Stage {
+    V4<R> w0, w1, w2, urp, fp;
+    int n;
+
+    template <class PH>
+    __device__ __forceinline__ bool push(const V4<R> &v, const PH &ph, R lam, V4<R> &cell,
+                                         V4<R> &D) {
+        w0 = w1; w1 = w2; w2 = v;
+        ++n;
+        if (n < 3) return false;
+        V4<R> ul, ur;
+        ph.faces(w0, w1, w2, lam, ul, ur);
+        bool out = false;
+        if (n >= 4) {
+            const V4<R> F = ph.musta(urp, ul, lam);
+            if (n >= 5) {
+                D.e = F.e - fp.e; D.n = F.n - fp.n; D.t1 = F.t1 - fp.t1; D.t2 = F.t2 - fp.t2;
+                cell = w0;
+                out = true;
+            }
+            fp = F;
+        }
+        urp = ur;
+        return out;
+    }
+};
+
+// Where a thread's pencil lives.
+template <class R>
+struct Pencil {
+    const R *f0, *f1, *f2, *f3;   // input: E, M_axis, M_t1, M_t2 (pencil base applied)
+    R *g0, *g1, *g2, *g3;         // output
+    long long stride;
+    int N;
+
+    __device__ __forceinline__ V4<R> load(int j) const {
+        const long long o = (long long)j * stride;
+        return v4<R>(__ldg(f0 + o), __ldg(f1 + o), __ldg(f2 + o), __ldg(f3 + o));
+    }
+    __device__ __forceinline__ void store(int j, const V4<R> &v) const {
+        const long long o = (long long)j * stride;
+        g0[o] = v.e; g1[o] = v.n; g2[o] = v.t1; g3[o] = v.t2;
+    }
+};
+
+__device__ __forceinline__ int wrap_index(int j, int N, int bc) {
+    if (bc == BC_OUTFLOW) return j < 0 ? 0 : (j >= N ? N - 1 : j);
+    while (j < 0) j += N;
+    while (j >= N) j -= N;
+    return j;
+}
+
+// Pick the value stage k+1 receives for position p from the last outputs of
+// stage k (q[0] newest, age a = cell index of q[0] minus the wanted cell).
+// With outflow ends, ghost positions p < 0 take the output of cell 0 and
+// p >= N the output of cell N-1 (saved in `last`), as the ghost fill of a
+// stage input does.
+template <class R, int DEPTH>
+__device__ __forceinline__ V4<R> pick(const V4<R> (&q)[DEPTH], int newest, int p, int N, int bc,
+                                      const V4<R> &last) {
+    if (bc == BC_OUTFLOW) {
+        if (p >= N) return last;
+        if (p < 0) p = 0;
+    }
+    const int age = newest - p;
+    V4<R> x = q[DEPTH - 1];
+#pragma unroll
+    for (int a = 0; a < DEPTH - 1; ++a)
+        if (age == a) x = q[a];
+    return x;
+}
+
+template <class R, int DEPTH>
+__device__ __forceinline__ void shift_in(V4<R> (&q)[DEPTH], const V4<R> &v) {
+#pragma unroll
+    for (int a = DEPTH - 1; a > 0; --a) q[a] = q[a - 1];
+    q[0] = v;
+}
+
+// March one segment of a pencil: the RK stages of Eq. 5-7 fused in registers.
+// Every thread runs the same schedule (T = L + 4, L + 10 or L + 18 steps for
+// RK1/2/3), so a warp stays converged; stage k+1 starts a fixed number of
+// steps after stage k, reading stage k's outputs from a short register queue.
+// Cells [s0, s_end) are stored; the segment's nominal length L may run past
+// the pencil end (those cells are computed with wrapped or clamped inputs and
+// not stored).
+template <class R, int RK, class PH>
+__device__ __forceinline__ void march(const PH &ph, const Pencil<R> &P, int s0, int L, int s_end,
+                                      int bc, R lam, bool do_store) {
+    const int N = P.N;
+    if (!(lam > R(0))) {   // finished event: copy through
+        if (do_store)
+            for (int o = s0; o < s_end; ++o) P.store(o, P.load(o));
+        return;
+    }
+    const R third = R(1.0 / 3.0), two3 = R(2.0 / 3.0), q3 = R(0.75), q1 = R(0.25), half = R(0.5);
+    Stage<R> st1, st2, st3;
+    st1.n = 0; st2.n = 0; st3.n = 0;
+    V4<R> cell, D;
+    constexpr int H = 2 * RK;                 // halo of the stage-1 input
+    constexpr int T_EXTRA = RK == 1 ? 4 : (RK == 2 ? 10 : 18);
+    const int T = L + T_EXTRA;
+    const int js = s0 - H;
+    V4<R> qa[RK == 3 ? 5 : 3], qb[3];
+    V4<R> lastA = v4<R>(0, 0, 0, 0), lastB = lastA;
+    V4<R> nxt = P.load(wrap_index(js, N, bc));
+#pragma unroll 1
+    for (int t = 0; t < T; ++t) {
+        const V4<R> V = nxt;
+        if (t + 1 < T) nxt = P.load(wrap_index(js + t + 1, N, bc));
+        if (!st1.push(V, ph, lam, cell, D)) continue;
+        // stage-1 output: cell i = js + t - 2
+        const int i = js + t - 2;
+        V4<R> X;
+        X.e = cell.e - lam * D.e; X.n = cell.n - lam * D.n;
+        X.t1 = cell.t1 - lam * D.t1; X.t2 = cell.t2 - lam * D.t2;
+        if (RK == 1) {
+            if (do_store && i < s_end) P.store(i, X);
+            continue;
+        }
+        if (RK == 2) {
+            shift_in(qa, X);
+            if (i == N - 1) lastA = X;
+            if (t < 6) continue;
+            const int p = t + s0 - 8;            // stage-2 input position
+            const V4<R> Y = pick(qa, i, p, N, bc, lastA);
+            V4<R> c, Dl;
+            if (!st2.push(Y, ph, lam, c, Dl)) continue;
+            const int o = t + s0 - 10;           // finished cell
+            const V4<R> U0 = P.load(wrap_index(o, N, bc));
+            V4<R> r;   // Eq. 6: U^{n+1} = 1/2 (U + U1 + dt L(U1))
+            r.e = half * (U0.e + c.e - lam * Dl.e);
+            r.n = half * (U0.n + c.n - lam * Dl.n);
+            r.t1 = half * (U0.t1 + c.t1 - lam * Dl.t1);
+            r.t2 = half * (U0.t2 + c.t2 - lam * Dl.t2);
+            if (do_store && o < s_end) P.store(o, r);
+        } else {   // RK == 3, Eq. 7
+            shift_in(qa, X);
+            if (i == N - 1) lastA = X;
+            if (t < 8) continue;
+            const int p2 = t + s0 - 12;
+            const V4<R> Y = pick(qa, i, p2, N, bc, lastA);
+            V4<R> c2, D2;
+            if (!st2.push(Y, ph, lam, c2, D2)) continue;
+            const int i2 = t + s0 - 14;
+            const V4<R> U0 = P.load(wrap_index(i2, N, bc));
+            V4<R> Z;   // U2 = 3/4 U + 1/4 (U1 + dt L(U1))
+            Z.e = q3 * U0.e + q1 * (c2.e - lam * D2.e);
+            Z.n = q3 * U0.n + q1 * (c2.n - lam * D2.n);
+            Z.t1 = q3 * U0.t1 + q1 * (c2.t1 - lam * D2.t1);
+            Z.t2 = q3 * U0.t2 + q1 * (c2.t2 - lam * D2.t2);
+            shift_in(qb, Z);
+            if (i2 == N - 1) lastB = Z;
+            if (t < 14) continue;
+            const int p3 = t + s0 - 16;
+            const V4<R> Y3 = pick(qb, i2, p3, N, bc, lastB);
+            V4<R> c3, D3;
+            if (!st3.push(Y3, ph, lam, c3, D3)) continue;
+            const int o = t + s0 - 18;
+            const V4<R> U00 = P.load(wrap_index(o, N, bc));
+            V4<R> r;   // U^{n+1} = 1/3 U + 2/3 (U2 + dt L(U2))
+            r.e = U00.e * third + two3 * (c3.e - lam * D3.e);
+            r.n = U00.n * third + two3 * (c3.n - lam * D3.n);
+            r.t1 = U00.t1 * third + two3 * (c3.t1 - lam * D3.t1);
+            r.t2 = U00.t2 * third + two3 * (c3.t2 - lam * D3.t2);
+            if (do_store && o < s_end) P.store(o, r);
+        }
+    }
+}
+
+}  // namespace hy

@@ -1,0 +1,65 @@
+// kernels.h -- host-side entry points of the kernels (C++ linkage, internal).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "common.h"
+
+namespace hy {
+
+struct SweepLaunch {
+    const void *in;
+    void *out;
+    const EventGeo *ev;
+    const WorkItem *items;
+    int nitems;
+    int axis;
+    double frac;             // the sweep's share of the step dt
+    const EventClock *clk;
+    Scheme sc;
+    int rk;
+    int threads, blocks;
+    cudaStream_t stream;
+};
+
+cudaError_t launch_sweep_f64(const SweepLaunch &a);
+cudaError_t launch_sweep_f32(const SweepLaunch &a);
+cudaError_t launch_sweep_mixed(const SweepLaunch &a);
+
+// Cell-wise kernels over work items of cells (prec: 0 double, 1/2 float).
+struct CellLaunch {
+    const EventGeo *ev;
+    const WorkItem *items;
+    int nitems;
+    int threads, blocks;
+    cudaStream_t stream;
+    int prec;
+    Scheme sc;
+};
+
+cudaError_t launch_prim2cons(const CellLaunch &c, const void *e, const void *vx, const void *vy,
+                             const void *vz, void *U);
+cudaError_t launch_cons2prim(const CellLaunch &c, const void *U, void *e, void *vx, void *vy,
+                             void *vz);
+// max over cells and swept axes of speed/dx into clk[event].rate_bits (atomic max)
+cudaError_t launch_rate(const CellLaunch &c, const void *U, EventClock *clk, double cfl_unused);
+// per-event dt from rate_bits (resets it), t_step = t, t += dt
+cudaError_t launch_dt(EventClock *clk, const double *cfl_fixed, int nevents, cudaStream_t s);
+cudaError_t launch_jet(const CellLaunch &c, void *U, const EventClock *clk);
+// FP64 partial sums per work item: partial[item][4]
+cudaError_t launch_sums(const CellLaunch &c, const void *U, double *partial);
+cudaError_t launch_sums_final(const WorkItem *items, int nitems, const double *partial,
+                              const EventGeo *ev, double *out, int nevents, cudaStream_t s);
+cudaError_t launch_hotspots(const CellLaunch &c, const double *spots, int nspots, double sigma,
+                            double e_bg, void *U);
+cudaError_t launch_finite(const CellLaunch &c, const void *U, EventClock *clk);
+cudaError_t launch_c2p_newton(int prec, const Scheme &sc, const void *U, long long n, int seed,
+                              void *vmag, int *iters, cudaStream_t s);
+
+// Newton-seed MLP
+cudaError_t launch_mlp_forward(const float *params, const float *X, int n, float *out,
+                               cudaStream_t s);
+cudaError_t launch_mlp_loss_grad(const float *params, const float *X, const float *Y, int n,
+                                 float *grad, float *loss, cudaStream_t s);
+cudaError_t launch_mlp_prepare(const float *params, void *w_bf16, cudaStream_t s);
+
+}  // namespace hy

@@ -1,0 +1,21 @@
+"""Error metrics of the parity tests (reading R13).
+
+max_rel_per_cell: max over cells and components of |U - U_ref| / E_ref, the
+cell's T^00 (|M| < E, so it is the natural scale of every component).
+rel_l1: per field, sum |a - b| / max(sum |b|, 1e-3 sum E_ref).
+"""
+import numpy as np
+
+
+def max_rel_per_cell(U, Uref):
+    U = np.asarray(U, dtype=np.float64)
+    Uref = np.asarray(Uref, dtype=np.float64)
+    return float((np.abs(U - Uref) / np.abs(Uref[0])[None]).max())
+
+
+def rel_l1(U, Uref):
+    U = np.asarray(U, dtype=np.float64)
+    Uref = np.asarray(Uref, dtype=np.float64)
+    floor = 1e-3 * np.abs(Uref[0]).sum()
+    return [float(np.abs(U[q] - Uref[q]).sum() / max(np.abs(Uref[q]).sum(), floor))
+            for q in range(4)]

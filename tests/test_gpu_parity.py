@@ -1,0 +1,322 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 CPU oracle.
+
+Tolerances (reading R13): FP64 <= 1e-10 max relative per cell; FP32 and
+mixed <= 1e-4 relative L1 per field.  Sizes are small enough for the oracle
+and span several blocks, several pencil segments and ragged tails.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1510_06340_b300 import inputs as I
+from tests import exact
+from tests.metrics import max_rel_per_cell, rel_l1
+
+pytestmark = pytest.mark.gpu
+
+F64_TOL = 1e-10
+F32_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def H():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_1510_06340_b300 import build, hydro
+    build.build(verbose=False)
+    return hydro
+
+
+def pair(H, g, prim, prec="fp64", bc="periodic", limiter="minmod", stages=2, rk_order=2,
+         hancock=1, cfl=0.4, fixed_dt=0.0, eos=None, seed="zero", jet=None, newton_tol=0.0):
+    """A GPU handle and an oracle on the same grid and initial state."""
+    grid = H.make_grid(g["nx"], g.get("ny", 1), g.get("nz", 1), dx=g["dx"], x0=g.get("x0", 0.0),
+                       y0=g.get("y0", 0.0), z0=g.get("z0", 0.0), bc=bc, prec=prec,
+                       rk_order=rk_order, hancock=hancock, cfl=cfl, fixed_dt=fixed_dt)
+    h = H.Hydro(grid, H.make_eos(eos, seed=seed, newton_tol=newton_tol), limiter=limiter,
+                stages=stages)
+    o = O.Oracle(g["nx"], g.get("ny", 1), g.get("nz", 1), dx=g["dx"], x0=g.get("x0", 0.0),
+                 y0=g.get("y0", 0.0), z0=g.get("z0", 0.0), bc=bc, limiter=limiter,
+                 stages=stages, rk_order=rk_order, hancock=hancock, cfl=cfl, fixed_dt=fixed_dt,
+                 eos=eos, seed_kind=H.SEEDS[seed], jet=jet)
+    U0 = o.prim2cons_field(*prim)
+    h.set_conserved(U0.astype(h.dtype))
+    if jet is not None:
+        h.set_jet(jet)
+    return h, o, U0
+
+
+def check(h, U_ref, prec):
+    U = h.get_conserved()
+    if prec == "fp64":
+        err = max_rel_per_cell(U, U_ref)
+        assert err <= F64_TOL, err
+    else:
+        err = max(rel_l1(U, U_ref))
+        assert err <= F32_TOL, err
+    return err
+
+
+# ------------------------------------------------------------------ 1-D shock tube
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_shock_tube_to_t08(H, prec):
+    """1000 cells, e_L = 10, e_R = 1, outflow, CFL 0.4, minmod, 2 stages, RK2, t = 0.8."""
+    g, prim = I.shock_tube(1000)
+    h, o, U = pair(H, g, prim, prec=prec, bc="outflow")
+    n_or, t_or = o.run(U, 100000, t_end=0.8)
+    t = h.step(100000, t_end=0.8)
+    assert t == 0.8 and t_or == 0.8
+    check(h, U, prec)
+    # and the GPU solution is close to the exact one
+    e, vx, _, _ = h.get_primitives()
+    x = I.cell_centres(1000, -1.0, g["dx"])
+    ex, _ = exact.Riemann().sample(x, 0.8)
+    assert np.abs(e.ravel() - ex).sum() / np.abs(ex).sum() < 6e-3
+
+
+@pytest.mark.parametrize("limiter", ["none", "minmod", "mc", "superbee", "vanleer", "vanalbada"])
+@pytest.mark.parametrize("rk_order,hancock,stages", [(2, 1, 2), (1, 1, 3), (3, 0, 1), (3, 1, 4)])
+def test_scheme_variants_1d(H, limiter, rk_order, hancock, stages):
+    n = 203   # ragged against every segment length
+    rng = np.random.default_rng(7)
+    x = I.cell_centres(n, -1.0, 2.0 / n)
+    e = 1.0 + 0.5 * np.sin(3 * np.pi * x) + (x > 0.3) * 2.0 + 0.05 * rng.random(n)
+    v = 0.3 * np.cos(2 * np.pi * x) * (np.abs(x) < 0.7)
+    z = np.zeros(n)
+    prim = tuple(a.reshape(1, 1, n) for a in (e, v, 0.2 * v, z))
+    g = dict(nx=n, dx=2.0 / n, x0=-1.0)
+    for bc in ("periodic", "outflow"):
+        h, o, U = pair(H, g, prim, bc=bc, limiter=limiter, stages=stages, rk_order=rk_order,
+                       hancock=hancock, fixed_dt=0.3 * 2.0 / n)
+        for segs in (1, 4):
+            h.force_launch(0, 64, segs)
+            h.set_conserved(U)
+            h.set_time(0.0)
+            h.step(12)
+            Uo = U.copy()
+            o.run(Uo, 12)
+            check(h, Uo, "fp64")
+
+
+# ------------------------------------------------------------------ 3-D blast
+@pytest.mark.parametrize("limiter", ["minmod", "mc", "superbee"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_blast_3d(H, limiter, prec):
+    g, prim = I.spherical_blast(32)
+    h, o, U = pair(H, g, prim, prec=prec, limiter=limiter)
+    o.run(U, 10)
+    h.step(10)
+    check(h, U, prec)
+
+
+def test_blast_3d_ragged_shapes_bitwise(H):
+    """Launch shape (threads per block, pencil segments) changes no bit."""
+    g = dict(nx=37, ny=29, nz=23, dx=2.0 / 37, x0=-1.0, y0=-0.8, z0=-0.6)
+    c = [I.cell_centres(g[k], g[o], g["dx"]) for k, o in (("nz", "z0"), ("ny", "y0"), ("nx", "x0"))]
+    zz, yy, xx = np.meshgrid(*c, indexing="ij")
+    e = np.where(xx ** 2 + yy ** 2 + zz ** 2 < 0.3, 8.0, 1.0)
+    zero = np.zeros_like(e)
+    prim = (e, 0.1 * np.sin(3 * yy), zero, 0.05 * np.cos(2 * xx))
+    ref = None
+    for threads, segs in ((256, 1), (64, 3), (96, 5), (32, 2)):
+        h, o, U = pair(H, g, prim, bc=("periodic", "outflow", "periodic"))
+        for ax in range(3):
+            h.force_launch(ax, threads, segs)
+        h.step(4)
+        out = h.get_conserved()
+        if ref is None:
+            ref = out
+            o.run(U, 4)
+            assert max_rel_per_cell(out, U) <= F64_TOL
+        else:
+            assert np.array_equal(out, ref), (threads, segs)
+
+
+def test_graph_and_eager_steps_agree_bitwise(H):
+    g, prim = I.spherical_blast(24)
+    h1, _, U = pair(H, g, prim)
+    h1.step(1)
+    h1.step(1)
+    h1.step(1)       # eager (single steps)
+    h2, _, _ = pair(H, g, prim)
+    h2.step(3)       # one graph launch of two steps + one eager
+    assert np.array_equal(h1.get_conserved(), h2.get_conserved())
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_periodic_conservation(H, prec):
+    g, prim = I.spherical_blast(32)
+    h, o, U = pair(H, g, prim, prec=prec)
+    s0 = h.conservation_sums()
+    np.testing.assert_allclose(s0, o.conservation_sums(U.astype(h.dtype).astype(np.float64)),
+                               rtol=1e-12, atol=1e-12 * s0[0])
+    h.step(20)
+    s1 = h.conservation_sums()
+    tol = 1e-13 if prec == "fp64" else 2e-6
+    assert abs(s1[0] - s0[0]) <= tol * s0[0]
+    assert np.abs(s1[1:]).max() <= tol * s0[0]
+
+
+def test_cfl_rate_matches_oracle(H):
+    g = I.event_grid(20, 0.1)
+    spots = I.hotspots(3, flow_max=0.9)
+    prim = I.hotspot_primitives(g, spots)
+    h, o, U = pair(H, g, prim, bc="outflow")
+    r = h.max_rate()
+    assert abs(r - o.max_rate(U)) <= 1e-14 * r
+
+
+# ------------------------------------------------------------------ outflow + flow + jet
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "mixed"])
+def test_hotspots_with_flow_and_jet(H, prec):
+    g = I.event_grid(24, 0.1)
+    spots = I.hotspots(11, flow_max=0.95)
+    prim = I.hotspot_primitives(g, spots)
+    jet = I.jet(11)
+    jet[:3] = [0.2, -0.3, 0.0]    # start inside this small box
+    h, o, U = pair(H, g, prim, prec=prec, bc="outflow", jet=jet)
+    o.run(U, 8)
+    h.step(8)
+    check(h, U, prec)
+
+
+def test_hotspot_initial_state_matches_generator(H):
+    g = I.event_grid(18, 0.1)
+    spots = I.hotspots(5, flow_max=0.9)
+    e, vx, vy, vz = I.hotspot_primitives(g, spots)
+    grid = H.make_grid(18, 18, 18, dx=0.1, x0=g["x0"], y0=g["y0"], z0=g["z0"], bc="outflow")
+    h = H.Hydro(grid)
+    h.init_hotspots(spots, I.SPOT_SIGMA, I.E_BACKGROUND)
+    eg, vxg, vyg, vzg = h.get_primitives()
+    np.testing.assert_allclose(eg, e, rtol=1e-12)
+    for a, b in ((vxg, vx), (vyg, vy), (vzg, vz)):
+        np.testing.assert_allclose(a, b, atol=1e-12)
+
+
+# ------------------------------------------------------------------ full-size sweeps, sampled
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_full_size_blast_sweeps_sampled(H, prec):
+    """256^3 blast in the benchmark's launch configuration: after two steps,
+    one sweep per axis on the GPU; sampled pencils recomputed one by one by
+    the oracle from the same input state."""
+    n = 256
+    g, prim = I.spherical_blast(n)
+    grid = H.make_grid(n, n, n, dx=g["dx"], x0=-1.0, y0=-1.0, z0=-1.0, prec=prec)
+    h = H.Hydro(grid)
+    h.set_primitives(*[a.astype(h.dtype) for a in prim])
+    h.step(2)
+    rng = np.random.default_rng(3)
+    dt = 0.4 * g["dx"] * 0.5
+    for axis in range(3):
+        U_in = h.get_conserved()
+        h.sweep(axis, dt)
+        U_out = h.get_conserved()
+        for _ in range(12):
+            a, b = rng.integers(0, n, size=2)
+            idx = [a, b]
+            idx.insert(2 - axis, slice(None))
+            pen = U_in[(slice(None),) + tuple(idx)].astype(np.float64)   # [4][n]
+            shape = [1, 1, 1]
+            shape[axis] = n
+            o = O.Oracle(*shape, dx=g["dx"], bc="periodic")
+            Up = pen.reshape((4,) + tuple(shape[::-1])).copy()
+            o.sweep(Up, axis, dt)
+            got = U_out[(slice(None),) + tuple(idx)]
+            if prec == "fp64":
+                assert max_rel_per_cell(got, Up.reshape(4, n)) <= F64_TOL
+            else:
+                assert max(rel_l1(got, Up.reshape(4, n))) <= F32_TOL
+
+
+# ------------------------------------------------------------------ batch
+def test_batch_equals_single_runs_bitwise(H):
+    sizes = [17, 24, 31, 20]
+    grids, prims = [], []
+    for k, n in enumerate(sizes):
+        g = I.event_grid(n, 0.1)
+        grids.append(H.make_grid(n, n, n, dx=0.1, x0=g["x0"], y0=g["y0"], z0=g["z0"],
+                                 bc="outflow", prec="fp32"))
+        prims.append(I.hotspot_primitives(g, I.hotspots(k, nspots=40)))
+    b = H.Batch(grids)
+    for k, p in enumerate(prims):
+        b.set_primitives(k, *[a.astype(np.float32) for a in p])
+    b.step(6)
+    times = b.times()
+    for k, p in enumerate(prims):
+        h = H.Hydro(grids[k])
+        h.set_primitives(*[a.astype(np.float32) for a in p])
+        h.step(6)
+        assert h.time() == times[k]
+        assert np.array_equal(h.get_conserved(), b.get_conserved(k)), k
+
+
+def test_batch_hotspots_jets_against_oracle(H):
+    sizes = [16, 22, 19]
+    grids, jets, spots = [], [], []
+    for k, n in enumerate(sizes):
+        g = I.event_grid(n, 0.1)
+        grids.append(H.make_grid(n, n, n, dx=0.1, x0=g["x0"], y0=g["y0"], z0=g["z0"],
+                                 bc="outflow", prec="fp64"))
+        j = I.jet(k)
+        j[:3] = [0.1 * k, -0.2, 0.0]
+        jets.append(j)
+        spots.append(I.hotspots(k, nspots=64))
+    b = H.Batch(grids)
+    b.init_hotspots(np.stack(spots), I.SPOT_SIGMA, I.E_BACKGROUND)
+    b.set_jets(np.stack(jets))
+    b.step(5)
+    for k, n in enumerate(sizes):
+        g = I.event_grid(n, 0.1)
+        o = O.Oracle(n, n, n, dx=0.1, x0=g["x0"], y0=g["y0"], z0=g["z0"], bc="outflow",
+                     jet=jets[k])
+        U = o.prim2cons_field(*I.hotspot_primitives(g, spots[k]))
+        o.run(U, 5)
+        assert max_rel_per_cell(b.get_conserved(k), U) <= F64_TOL
+
+
+# ------------------------------------------------------------------ tabulated EOS
+@pytest.mark.parametrize("seed", ["zero", "conformal"])
+def test_table_eos_fp64(H, seed):
+    tab = I.eos_table()
+    g = I.event_grid(16, 0.1)
+    prim = I.hotspot_primitives(g, I.hotspots(2, nspots=60, flow_max=0.8))
+    h, o, U = pair(H, g, prim, bc="outflow", eos=tab, seed=seed)
+    o.run(U, 4)
+    h.step(4)
+    check(h, U, "fp64")
+
+
+def test_table_eos_fp32(H):
+    tab = I.eos_table()
+    g = I.event_grid(16, 0.1)
+    prim = I.hotspot_primitives(g, I.hotspots(2, nspots=60, flow_max=0.8))
+    h, o, U = pair(H, g, prim, prec="fp32", bc="outflow", eos=tab)
+    o.run(U, 4)
+    h.step(4)
+    check(h, U, "fp32")
+
+
+# ------------------------------------------------------------------ failure reporting
+def test_nonfinite_state_is_reported(H):
+    g, prim = I.spherical_blast(8)
+    h, o, U = pair(H, g, prim)
+    h.check_finite()
+    U[0, 1, 2, 3] = np.nan
+    h.set_conserved(U)
+    with pytest.raises(H.HydroError) as ei:
+        h.check_finite()
+    assert ei.value.status == 6
+
+
+def test_invalid_configurations_are_rejected(H):
+    with pytest.raises(H.HydroError) as ei:
+        H.Hydro(H.make_grid(0, 1, 1, dx=0.1))
+    assert ei.value.status == 1
+    with pytest.raises(H.HydroError):
+        H.Hydro(H.make_grid(8, dx=0.1), limiter=9)
+    with pytest.raises(H.HydroError):
+        H.Hydro(H.make_grid(8, dx=0.1), stages=0)
+    with pytest.raises(H.HydroError):
+        H.Hydro(H.make_grid(8, dx=0.1, rk_order=4))
