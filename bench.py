@@ -8,7 +8,8 @@ splitting, CFL 0.4, FP32 state.  One step = CFL rate reduction + dt + 5
 directional sweeps.  Metric: cell-updates/s (cells x steps / time).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload blast256_fp32|blast256_fp64|batch512]
+                  [--workload blast256_fp32|blast256_fp64|blast128_fp32]
+                  [--launch THREADS,SEGMENTS] [--no-cpu] [--no-e2e]
 
 Under torchrun each rank runs its own replica of the workload on its own GPU
 (the hot path has no data exchange between grids); value is the whole-job
@@ -34,6 +35,7 @@ sys.path.insert(0, ROOT)
 WORKLOADS = {
     "blast256_fp32": dict(n=256, prec="fp32"),
     "blast256_fp64": dict(n=256, prec="fp64"),
+    "blast128_fp32": dict(n=128, prec="fp32"),   # small case for ncu captures
 }
 BYTES = {"fp32": 4, "fp64": 8}
 
@@ -180,6 +182,10 @@ def run_ours(args):
     h = hydro.Hydro(grid, limiter="minmod", stages=2, stream=stream)
     h.set_primitives(*prim)
     cells = n ** 3
+    if args.launch:
+        th, sg = (int(x) for x in args.launch.split(","))
+        for ax in range(3):
+            h.force_launch(ax, th, sg)
 
     # warm-up (first call also autotunes the launch shapes)
     h.step(args.warmup)
@@ -202,6 +208,7 @@ def run_ours(args):
             dist.barrier()
     ms = e0.elapsed_time(e1)
     (sweep_ms, other_ms), (n_sweep, n_other) = h.kernel_timing()
+    shapes = [h.get_launch(ax) for ax in range(3)]
     h.set_kernel_timing(False)
     if world > 1:
         t = torch.tensor([ms], device="cuda")
@@ -212,18 +219,18 @@ def run_ours(args):
     # e2e through the public API with host buffers: upload initial primitives
     # from pinned memory, step, read each step's conservation sums, read back
     # the final primitives.
-    pinned = [torch.from_numpy(a).pin_memory() for a in prim]
-    outs = [torch.empty(a.shape, dtype=pinned[0].dtype).pin_memory() for a in prim]
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    h.set_primitives(*[p.numpy() for p in pinned])
-    for _ in range(args.steps):
-        h.step(1)
-        h.conservation_sums()
-    e_, vx_, vy_, vz_ = h.get_primitives()
-    torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    e2e_value = world * cells * args.steps / e2e_s
+    e2e_value = None
+    if not args.no_e2e:
+        pinned = [torch.from_numpy(a).pin_memory() for a in prim]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h.set_primitives(*[p.numpy() for p in pinned])
+        for _ in range(args.steps):
+            h.step(1)
+            h.conservation_sums()
+        h.get_primitives()
+        torch.cuda.synchronize()
+        e2e_value = world * cells * args.steps / (time.perf_counter() - t0)
     state_bytes = 4 * cells * BYTES[prec]
 
     hbm, src = peaks()
@@ -248,6 +255,7 @@ def run_ours(args):
                                    f"{prec.upper()}, minmod, 2 MUSTA stages, RK2+Hancock, "
                                    "Strang, periodic, CFL 0.4",
                        "cells": cells, "parallelism": f"replicas x{world}",
+                       "launch_threads_segments_xyz": shapes,
                        "l2": "inputs larger than L2 (two state copies of "
                              f"{state_bytes / 1e6:.0f} MB)"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
@@ -279,6 +287,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="blast256_fp32", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--launch", default="", help="force 'threads,segments' for every axis")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer e2e pass")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -95,17 +95,9 @@ __global__ void k_cons2prim(const EventGeo *__restrict__ ev, const WorkItem *__r
 }
 
 // ------------------------------------------------------------------ CFL rate
-// reading R8: largest |characteristic speed| / dx over cells and swept axes
-template <class R>
-__device__ __forceinline__ R char_speed(R vd, R v2, R c2) {
-    const R cs = dsqrt_(c2);
-    R rad = (R(1) - v2) * (R(1) - vd * vd - (v2 - vd * vd) * c2);
-    rad = rad < R(0) ? R(0) : rad;
-    const R den = R(1) - v2 * c2;
-    const R a = vd * (R(1) - c2), b = cs * dsqrt_(rad);
-    return fmax_(fabs_((a + b) / den), fabs_((a - b) / den));
-}
-
+// reading R8: largest |characteristic speed| / dx over cells and swept axes,
+// computed in the state's precision.  With b = c sqrt(rad) >= 0,
+// max(|a + b|, |a - b|) = |a| + b.
 template <class R>
 __global__ void k_rate(const EventGeo *__restrict__ ev, const WorkItem *__restrict__ items,
                        int nitems, const R *__restrict__ U, EventClock *__restrict__ clk,
@@ -113,7 +105,9 @@ __global__ void k_rate(const EventGeo *__restrict__ ev, const WorkItem *__restri
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
         const WorkItem w = items[it];
         const EventGeo &g = ev[w.event];
-        double m = 0.0;
+        const R invh[3] = {R(1.0 / g.h[0]), R(1.0 / g.h[1]), R(1.0 / g.h[2])};
+        const bool act[3] = {g.n[0] > 1, g.n[1] > 1, g.n[2] > 1};
+        R m = R(0);
         for (int k = threadIdx.x; k < w.count; k += blockDim.x) {
             const long long c = w.first + k;
             const R *u = U + g.off + c;
@@ -123,22 +117,28 @@ __global__ void k_rate(const EventGeo *__restrict__ ev, const WorkItem *__restri
             R p, c2;
             eos_pc2<R>(sc, e, p, c2);
             const R v2 = vx * vx + vy * vy + vz * vz;
+            const R cs = dsqrt_(c2);
+            const R inv_den = R(1) / (R(1) - v2 * c2);
             const R vd[3] = {vx, vy, vz};
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
-                if (g.n[d] <= 1) continue;
-                const double r = double(char_speed<R>(vd[d], v2, c2)) / g.h[d];
+                if (!act[d]) continue;
+                R rad = (R(1) - v2) * (R(1) - vd[d] * vd[d] - (v2 - vd[d] * vd[d]) * c2);
+                rad = rad < R(0) ? R(0) : rad;
+                const R a = vd[d] * (R(1) - c2);
+                const R r = (fabs_(a) + cs * dsqrt_(rad)) * inv_den * invh[d];
                 m = (r > m || r != r) ? r : m;   // NaN propagates
             }
         }
         // warp shuffle max, then one atomic per warp
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            const double x = __shfl_xor_sync(0xffffffffu, m, o);
+            const R x = __shfl_xor_sync(0xffffffffu, m, o);
             m = (x > m || x != x) ? x : m;
         }
         if ((threadIdx.x & 31) == 0)
-            atomicMax(&clk[w.event].rate_bits, (unsigned long long)__double_as_longlong(m));
+            atomicMax(&clk[w.event].rate_bits,
+                      (unsigned long long)__double_as_longlong(double(m)));
     }
 }
 
