@@ -167,6 +167,22 @@ hydro_status hydro_counters(hydro_t *h, long long out[6]);
 /* HYDRO_E_NONFINITE if any state value is NaN or Inf, else HYDRO_OK. */
 hydro_status hydro_check_finite(hydro_t *h);
 
+/* The same four FP64 sums for callers that cannot allocate device memory
+ * (the paper has no counterpart; this is an interface for such callers).
+ * U is the caller's device array [4][nz][ny][nx] (double for HYDRO_FP64,
+ * float otherwise); out is a host array of 4 doubles, written before the
+ * call returns (the call synchronises `stream`, a cudaStream_t or NULL).
+ * The call allocates nothing: its scratch is a 131,104-byte array built into
+ * the library and resident on every GPU that loads it until the process
+ * exits.  Grids above 268,435,456 cells are rejected with HYDRO_E_INVALID.
+ * The first call on each device looks up that array's device address (with
+ * that device current), so make the first call before any stream capture.
+ * All calls share the array: calls that overlap on the GPU (other streams,
+ * other threads) race and must be serialised by the caller. */
+hydro_status hydro_conservation_sums_noalloc(const void *U, int prec, int nx, int ny, int nz,
+                                             double dx, double dy, double dz, double out[4],
+                                             void *stream);
+
 /* ---------------------------------------------------------------- batch of events */
 
 /* nevents independent grids (each may differ in size; all share precision,

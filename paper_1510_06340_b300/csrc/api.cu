@@ -750,6 +750,8 @@ struct Solver {
 
 }  // namespace
 
+void hy::set_last_error(const char *msg) { g_err = msg; }
+
 struct hydro_s {
     Solver s;
 };

@@ -62,4 +62,7 @@ cudaError_t launch_mlp_loss_grad(const float *params, const float *X, const floa
                                  float *grad, float *loss, cudaStream_t s);
 cudaError_t launch_mlp_prepare(const float *params, void *w_bf16, cudaStream_t s);
 
+// message returned by hydro_last_error() (thread-local)
+void set_last_error(const char *msg);
+
 }  // namespace hy

@@ -98,6 +98,7 @@ def lib():
             "hydro_batch_event_status": [H, ip],
             "hydro_batch_enable_counters": [H, i],
             "hydro_batch_counters": [H, C.POINTER(C.c_longlong)],
+            "hydro_conservation_sums_noalloc": [vp, i, i, i, i, d, d, d, dp, vp],
             "hydro_mlp_forward": [vp, vp, i, vp, vp],
             "hydro_mlp_loss_grad": [vp, vp, vp, i, vp, vp, vp],
             "hydro_mlp_train": [vp, vp, vp, i, i, i, C.c_float, C.c_ulonglong, vp, vp],
@@ -414,6 +415,17 @@ class Batch(_Base):
         out = (C.c_longlong * 6)()
         _check(lib().hydro_batch_counters(self.h, out))
         return dict(zip(COUNTERS, out[:]))
+
+
+def conservation_sums_noalloc(U, prec, nx, ny, nz, dx, dy=None, dz=None, stream=None):
+    """FP64 sums of a caller-held device state U [4][nz][ny][nx] without any
+    device allocation by the library (see hydro_conservation_sums_noalloc)."""
+    out = (C.c_double * 4)()
+    _check(lib().hydro_conservation_sums_noalloc(
+        C.c_void_p(U.data_ptr()), PRECISIONS[prec] if isinstance(prec, str) else int(prec),
+        nx, ny, nz, dx, dx if dy is None else dy, dx if dz is None else dz, out,
+        _stream_ptr(stream)))
+    return np.array(out[:])
 
 
 # ------------------------------------------------------------------ MLP
