@@ -109,7 +109,7 @@ const char *hydro_last_error(void);
 
 /* Validate the grid, EOS, limiter and MUSTA stage count (>= 1), allocate the
  * device state (two copies for ping-pong sweeps) and return a handle.
- * Errors: HYDRO_E_INVALID (sizes < 1, unknown enums, rk_order not 1..3,
+ * Errors: HYDRO_E_INVALID (sizes < 1, more than 536,870,911 cells, unknown enums, rk_order not 1..3,
  * stages < 1, dx <= 0, EOS table with n < 2), HYDRO_E_OOM, HYDRO_E_CUDA. */
 hydro_status hydro_create(const hydro_grid_t *grid, const hydro_eos_t *eos, int limiter,
                           int stages, hydro_t **out);
@@ -239,7 +239,9 @@ hydro_status hydro_get_launch(hydro_t *h, int axis, int *threads, int *segments)
 
 /* Parameter count of the seed network: W1[32][2] b1[32] W2[32][32] b2[32]
  * W3[32] b3 mu0 s0 mu1 s1 (inputs standardised as ((ln E - mu0)/s0,
- * (|M|/E - mu1)/s1), tanh hidden layers, output v0 = (|M|/E) sigmoid(z)). */
+ * (x - mu1)/s1), x = |M|/E, tanh hidden layers, output
+ * v0 = vc + (x - vc) sigmoid(z) with vc = 3x/(2 + sqrt(4 - 3x^2)) the p = e/3
+ * root; for 0 <= p <= e/3 the root lies in [vc, x]). */
 int hydro_mlp_nparam(void);
 
 /* Forward on the device: X [n][2] = (ln E, |M|/E) float, out [n] float seed

@@ -154,8 +154,10 @@ double or_eos_cs2(const or_config *c, double e) {
 
 /* ------------------------------------------------------------------ MLP */
 /*
- * Newton seed network (not in the paper): inputs (ln E, |M|/E) standardised,
- * two tanh hidden layers of 32, output r = sigmoid(z), seed v0 = (|M|/E) r.
+ * Newton seed network (not in the paper): inputs (ln E, x = |M|/E)
+ * standardised, two tanh hidden layers of 32, output r = sigmoid(z), seed
+ * v0 = vc + (x - vc) r with vc = 3x / (2 + sqrt(4 - 3x^2)) the root for
+ * p = e/3.  Any EOS with 0 <= p <= e/3 has its root in [vc, x].
  * Parameter layout: W1[32][2] b1[32] W2[32][32] b2[32] W3[32] b3 mu0 s0 mu1 s1.
  */
 #define MLP_H 32
@@ -202,6 +204,7 @@ static double mlp_forward1(const double *P, int q, double lnE, double x, double 
         z += w * h2[k];
     }
     double r = 1.0 / (1.0 + exp(-z));
+    double vc = 3.0 * x / (2.0 + sqrt(4.0 - 3.0 * x * x));
     if (cache) {
         memcpy(cache, h1, sizeof h1);
         memcpy(cache + MLP_H, h2, sizeof h2);
@@ -209,7 +212,7 @@ static double mlp_forward1(const double *P, int q, double lnE, double x, double 
         cache[2 * MLP_H + 1] = in0;
         cache[2 * MLP_H + 2] = in1;
     }
-    return x * r;
+    return vc + (x - vc) * r;
 }
 
 /* batch forward: X[n][2] = (ln E, |M|/E), out[n] = seed velocity */
@@ -238,7 +241,8 @@ double or_mlp_loss_grad(const double *P, int q, int n, const double *X, const do
         double d = v0 - Y[i];
         loss += d * d;
         double dv = 2.0 * d / (double)n;
-        double dz = dv * x * r * (1.0 - r);
+        double vc = 3.0 * x / (2.0 + sqrt(4.0 - 3.0 * x * x));
+        double dz = dv * (x - vc) * r * (1.0 - r);
         gb3[0] += dz;
         double da2[MLP_H];
         for (int k = 0; k < MLP_H; k++) {

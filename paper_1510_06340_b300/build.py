@@ -15,8 +15,10 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 INC = os.path.join(os.path.dirname(HERE), "include")
-OUT = os.path.join(HERE, "libhydro.so")
-BUILD = os.path.join(HERE, "_build")
+OUT = os.environ.get("HYDRO_LIB_OUT", os.path.join(HERE, "libhydro.so"))
+BUILD = os.environ.get("HYDRO_BUILD_DIR", os.path.join(HERE, "_build"))
+# extra nvcc flags (e.g. -DHY_SWEEP_MAXNREG=112) for launch-shape experiments
+EXTRA = os.environ.get("HYDRO_NVCC_FLAGS", "").split()
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 BASE = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + SRC, "-I" + INC]
@@ -42,7 +44,7 @@ def needs_build() -> bool:
 
 def _compile(src: str) -> str:
     obj = os.path.join(BUILD, os.path.basename(src) + ".o")
-    flags = list(BASE)
+    flags = list(BASE) + EXTRA
     if os.path.basename(src) in FAST:
         flags.append("--use_fast_math")
     cmd = [NVCC] + flags + ["-c", src, "-o", obj]

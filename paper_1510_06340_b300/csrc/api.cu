@@ -179,6 +179,8 @@ struct Solver {
                     return fail(HYDRO_E_INVALID, "unknown boundary condition");
                 q.n[a] = nn[a];
                 q.h[a] = h[a] > 0.0 ? h[a] : 1.0;
+                q.inv_h[a] = 1.0 / q.h[a];
+                q.inv_hf[a] = (float)q.inv_h[a];
                 q.bc[a] = g.bc[a];
                 q.seg[a] = 1;
                 q.segL[a] = nn[a];
@@ -186,6 +188,8 @@ struct Solver {
             }
             q.lo[0] = g.x0; q.lo[1] = g.y0; q.lo[2] = g.z0;
             q.cells = (long long)g.nx * g.ny * g.nz;
+            if (4 * q.cells > 2147483647LL)   // sweeps index fields with 32-bit offsets
+                return fail(HYDRO_E_INVALID, "an event may hold at most 536,870,911 cells");
             q.off = off;
             off += 4 * q.cells;
             total_cells += q.cells;

@@ -105,7 +105,12 @@ __global__ void k_rate(const EventGeo *__restrict__ ev, const WorkItem *__restri
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
         const WorkItem w = items[it];
         const EventGeo &g = ev[w.event];
-        const R invh[3] = {R(1.0 / g.h[0]), R(1.0 / g.h[1]), R(1.0 / g.h[2])};
+        R invh[3];
+        if (sizeof(R) == 8) {
+            invh[0] = R(g.inv_h[0]); invh[1] = R(g.inv_h[1]); invh[2] = R(g.inv_h[2]);
+        } else {
+            invh[0] = R(g.inv_hf[0]); invh[1] = R(g.inv_hf[1]); invh[2] = R(g.inv_hf[2]);
+        }
         const bool act[3] = {g.n[0] > 1, g.n[1] > 1, g.n[2] > 1};
         R m = R(0);
         for (int k = threadIdx.x; k < w.count; k += blockDim.x) {
@@ -161,7 +166,8 @@ __global__ void k_dt(EventClock *__restrict__ clk, double cfl, double fixed_dt, 
 }
 
 // ------------------------------------------------------------------ jet source
-// reading R12: U += dt S(t_step), S = dEdx (1, n) g(x - x0 - n t)
+// reading R12: U += dt S(t_step), S = dEdx (1, n) g(x - x0 - n t), in the
+// state's precision; cells farther than 9 sigma (g < 1e-17 g(0)) get nothing.
 template <class R>
 __global__ void k_jet(const EventGeo *__restrict__ ev, const WorkItem *__restrict__ items,
                       int nitems, R *__restrict__ U, const EventClock *__restrict__ clk) {
@@ -174,26 +180,35 @@ __global__ void k_jet(const EventGeo *__restrict__ ev, const WorkItem *__restric
         const double t = clk[w.event].t_step;
         const double *j = g.jet;
         const double sig = j[7];
-        const double norm = 1.0 / (pow(2.0 * 3.14159265358979323846, 1.5) * sig * sig * sig);
-        const double cx = j[0] + j[3] * t, cy = j[1] + j[4] * t, cz = j[2] + j[5] * t;
-        const double inv2s2 = 1.0 / (2.0 * sig * sig);
         const int nx = g.n[0], ny = g.n[1];
+        const double cz = j[2] + j[5] * t;
+        // whole chunk in z planes farther than the cutoff: nothing to add
+        const int z_lo = int(w.first / ((long long)nx * ny));
+        const int z_hi = int((w.first + w.count - 1) / ((long long)nx * ny));
+        const double zc_lo = g.lo[2] + (z_lo + 0.5) * g.h[2] - cz;
+        const double zc_hi = g.lo[2] + (z_hi + 0.5) * g.h[2] - cz;
+        if (zc_lo > 9.0 * sig || zc_hi < -9.0 * sig) continue;
+        const R amp = R(dt * j[6] / (pow(2.0 * 3.14159265358979323846, 1.5) * sig * sig * sig));
+        const R cx = R(j[0] + j[3] * t), cy = R(j[1] + j[4] * t), czr = R(cz);
+        const R inv2s2 = R(1.0 / (2.0 * sig * sig));
+        const R cut2 = R(81.0 * sig * sig);
+        const R nxr = R(j[3]), nyr = R(j[4]), nzr = R(j[5]);
         for (int k = threadIdx.x; k < w.count; k += blockDim.x) {
             const long long c = w.first + k;
             const int x = int(c % nx);
             const int y = int((c / nx) % ny);
             const int z = int(c / ((long long)nx * ny));
-            const double px = g.lo[0] + (x + 0.5) * g.h[0] - cx;
-            const double py = g.lo[1] + (y + 0.5) * g.h[1] - cy;
-            const double pz = g.lo[2] + (z + 0.5) * g.h[2] - cz;
-            const double r2 = (px * px + py * py + pz * pz) * inv2s2;
-            if (r2 > 700.0) continue;   // exp underflows to 0 in double
-            const double s = dt * j[6] * norm * exp(-r2);
+            const R px = R(g.lo[0]) + (R(x) + R(0.5)) * R(g.h[0]) - cx;
+            const R py = R(g.lo[1]) + (R(y) + R(0.5)) * R(g.h[1]) - cy;
+            const R pz = R(g.lo[2]) + (R(z) + R(0.5)) * R(g.h[2]) - czr;
+            const R r2 = px * px + py * py + pz * pz;
+            if (r2 > cut2) continue;
+            const R s = amp * exp(-r2 * inv2s2);
             R *u = U + g.off + c;
-            u[0] = R(double(u[0]) + s);
-            u[g.cells] = R(double(u[g.cells]) + s * j[3]);
-            u[2 * g.cells] = R(double(u[2 * g.cells]) + s * j[4]);
-            u[3 * g.cells] = R(double(u[3 * g.cells]) + s * j[5]);
+            u[0] += s;
+            u[g.cells] += s * nxr;
+            u[2 * g.cells] += s * nyr;
+            u[3 * g.cells] += s * nzr;
         }
     }
 }
@@ -249,11 +264,16 @@ __global__ void k_sums_final(const WorkItem *__restrict__ items, int nitems,
 }
 
 // ------------------------------------------------------------------ hot spots
+// e = e_bg + sum_j A_j g_j, v = sum_j A_j g_j u_j / e, computed in the state's
+// precision.  A spot farther than 9 sigma along any axis adds less than
+// A exp(-40.5) and is skipped (relative to e_bg = 0.01 and A = 2 that is
+// below 1e-15).
 template <class R>
 __global__ void k_hotspots(const EventGeo *__restrict__ ev, const WorkItem *__restrict__ items,
                            int nitems, const double *__restrict__ spots, int nspots, double sigma,
                            double e_bg, R *__restrict__ U, Scheme sc) {
-    const double inv = 1.0 / (2.0 * sigma * sigma);
+    const R inv = R(1.0 / (2.0 * sigma * sigma));
+    const R cut = R(9.0 * sigma);
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
         const WorkItem w = items[it];
         const EventGeo &g = ev[w.event];
@@ -264,30 +284,35 @@ __global__ void k_hotspots(const EventGeo *__restrict__ ev, const WorkItem *__re
             const int x = int(c % nx);
             const int y = int((c / nx) % ny);
             const int z = int(c / ((long long)nx * ny));
-            const double px = g.lo[0] + (x + 0.5) * g.h[0];
-            const double py = g.lo[1] + (y + 0.5) * g.h[1];
-            const double pz = g.lo[2] + (z + 0.5) * g.h[2];
-            double e = e_bg, mx = 0.0, my = 0.0, mz = 0.0;
+            const R px = R(g.lo[0] + (x + 0.5) * g.h[0]);
+            const R py = R(g.lo[1] + (y + 0.5) * g.h[1]);
+            const R pz = R(g.lo[2] + (z + 0.5) * g.h[2]);
+            R e = R(e_bg), mx = R(0), my = R(0), mz = R(0);
             for (int s = 0; s < nspots; ++s) {
                 const double *q = sp + 7 * s;
-                const double dx = px - q[0], dy = py - q[1], dz = pz - q[2];
-                const double a = q[3] * exp(-(dx * dx) * inv) * exp(-(dy * dy) * inv) *
-                                 exp(-(dz * dz) * inv);
+                const R dz = pz - R(q[2]);
+                if (fabs_(dz) > cut) continue;
+                const R dy = py - R(q[1]);
+                if (fabs_(dy) > cut) continue;
+                const R dx = px - R(q[0]);
+                if (fabs_(dx) > cut) continue;
+                const R a = R(q[3]) * exp(-(dz * dz) * inv) * exp(-(dy * dy) * inv) *
+                            exp(-(dx * dx) * inv);
                 e += a;
-                mx += a * q[4];
-                my += a * q[5];
-                mz += a * q[6];
+                mx += a * R(q[4]);
+                my += a * R(q[5]);
+                mz += a * R(q[6]);
             }
-            const double vx = mx / e, vy = my / e, vz = mz / e;
-            double p, c2;
-            eos_pc2<double>(sc, e, p, c2);
-            const double g2 = 1.0 / (1.0 - (vx * vx + vy * vy + vz * vz));
-            const double wv = (e + p) * g2;
+            const R vx = mx / e, vy = my / e, vz = mz / e;
+            R p, c2;
+            eos_pc2<R>(sc, e, p, c2);
+            const R g2 = R(1) / (R(1) - (vx * vx + vy * vy + vz * vz));
+            const R wv = (e + p) * g2;
             R *u = U + g.off + c;
-            u[0] = R(wv - p);
-            u[g.cells] = R(wv * vx);
-            u[2 * g.cells] = R(wv * vy);
-            u[3 * g.cells] = R(wv * vz);
+            u[0] = wv - p;
+            u[g.cells] = wv * vx;
+            u[2 * g.cells] = wv * vy;
+            u[3 * g.cells] = wv * vz;
         }
     }
 }

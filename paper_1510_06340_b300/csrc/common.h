@@ -37,6 +37,9 @@ struct EventGeo {
     int segL[3];         // nominal segment length per axis
     double h[3];
     double lo[3];        // lower corner
+    double inv_h[3];     // 1 / h, computed on the host
+    float inv_hf[3];
+    float pad_f;
     double jet[8];
     int jet_on;
     int pad;

@@ -63,6 +63,33 @@ __device__ __forceinline__ R limited_slope(int kind, R a, R b) {
     return a > R(0) ? m : -m;
 }
 
+// Compile-time limiter.  Minbee, MC and Superbee in median form:
+// median(0, a, b) = max(min(a, b), min(max(a, b), 0)) is a*xi_MB(b/a) exactly
+// (both pick the smaller magnitude when a, b share a sign, else 0); the 3-way
+// minmod of MC and the two minmods of Superbee follow from it.
+__device__ __forceinline__ float med0(float a, float b) {
+    return fmaxf(fminf(a, b), fminf(fmaxf(a, b), 0.0f));
+}
+__device__ __forceinline__ double med0(double a, double b) {
+    return fmax(fmin(a, b), fmin(fmax(a, b), 0.0));
+}
+
+template <int LIM, class R>
+__device__ __forceinline__ R slope_ct(int kind, R a, R b) {
+    if (LIM == LIM_MINMOD) return med0(a, b);
+    if (LIM == LIM_MC) {
+        const R m = med0(R(2) * a, R(2) * b);
+        const R h = R(0.5) * (a + b);
+        return fmax_(fmin_(m, h), fmin_(fmax_(m, h), R(0)));
+    }
+    if (LIM == LIM_SUPERBEE) {
+        const R s1 = med0(R(2) * a, b), s2 = med0(a, R(2) * b);
+        return a > R(0) ? fmax_(s1, s2) : fmin_(s1, s2);
+    }
+    if (LIM == LIM_NONE) return R(0.5) * (a + b);
+    return limited_slope<R>(kind, a, b);   // runtime choice (van Leer, van Albada, any)
+}
+
 __device__ __forceinline__ void count(const Scheme &s, int which, unsigned long long v = 1) {
     if (s.counters) atomicAdd(s.counters + which, v);
 }
@@ -78,28 +105,29 @@ struct Prim {
 // W^2 - (1+cs2) E W + cs2 M^2 = 0; |M| is capped at (1 - delta) E (R9).
 template <class R>
 __device__ __forceinline__ Prim<R> c2p_conformal(const V4<R> &U, R cs2, R delta, R &M2out,
-                                                 R &Wout, const Scheme &sc) {
+                                                 R &Wout, const Scheme &sc, bool counting) {
     Prim<R> q;
     const R E = U.e;
-    R M2 = U.n * U.n + U.t1 * U.t1 + U.t2 * U.t2;
-    if (!(E > R(0))) {
-        q.vn = R(0); q.p = R(0); M2out = R(0); Wout = R(0);
-        return q;
+    const R M2 = U.n * U.n + U.t1 * U.t1 + U.t2 * U.t2;
+    const R E2 = E * E;
+    const R capf = (R(1) - delta) * (R(1) - delta);
+    const R cap2 = capf * E2;
+    const R M2c = fmin_(M2, cap2);
+    const R apc = R(1) + cs2;
+    // W^2 - (1+c2) E W + c2 M^2 = 0: 2W = (1+c2) E + sqrt((1+c2)^2 E^2 - 4 c2 M^2),
+    // the discriminant being positive for |M| < E
+    const R disc = (apc * apc) * E2 - (R(4) * cs2) * M2c;
+    const R W2 = apc * E + dsqrt_(disc);
+    R s = R(2);
+    if (M2 > cap2) {      // |M| capped at (1 - delta) E (R9)
+        s = R(2) * dsqrt_(cap2 / M2);
+        if (counting) count(sc, CNT_CAPPED);
     }
-    const R cap = (R(1) - delta) * E;
-    R s = R(1);
-    if (M2 > cap * cap) {
-        s = cap / dsqrt_(M2);
-        M2 = cap * cap;
-        count(sc, CNT_CAPPED);
-    }
-    const R a = (R(1) + cs2) * E;
-    R disc = a * a - R(4) * cs2 * M2;
-    disc = disc < R(0) ? R(0) : disc;
-    const R W = R(0.5) * (a + dsqrt_(disc));
-    q.vn = (s * U.n) / W;
-    q.p = W - E;
-    M2out = M2; Wout = W;
+    const bool ok = E > R(0);   // E <= 0: vacuum, v = p = 0
+    q.vn = ok ? (s * U.n) / W2 : R(0);
+    q.p = ok ? R(0.5) * W2 - E : R(0);
+    M2out = ok ? M2c : R(0);
+    Wout = ok ? R(0.5) * W2 : R(0);
     return q;
 }
 
@@ -243,7 +271,7 @@ __device__ __forceinline__ Prim<R> c2p_table(const V4<R> &U, R delta, const Sche
 // Precision policy of a sweep: storage/flux type R and the cons->prim rule.
 enum { PREC_F64 = 0, PREC_F32 = 1, PREC_MIXED = 2 };
 
-template <class R, int PREC, int EOSK>
+template <class R, int PREC, int EOSK, int LIM = -1, bool COUNT = true>
 struct Physics {
     Scheme sc;
     R cs2, delta;
@@ -252,16 +280,17 @@ struct Physics {
     __device__ __forceinline__ Prim<R> prim(const V4<R> &U) const {
         if (EOSK == EOS_CONFORMAL) {
             R M2, W;
-            Prim<R> q = c2p_conformal<R>(U, cs2, delta, M2, W, sc);
+            Prim<R> q = c2p_conformal<R>(U, cs2, delta, M2, W, sc, COUNT);
             if (PREC == PREC_MIXED) {
                 // |v|^2 = M2 / W^2 > 0.99^2: redo in double (cancellation in W - E)
                 if (M2 > R(0.9801) * W * W) {
                     V4<double> D = v4<double>(U.e, U.n, U.t1, U.t2);
                     double M2d, Wd;
-                    Prim<double> qd = c2p_conformal<double>(D, double(cs2), DELTA_F64, M2d, Wd, sc);
+                    Prim<double> qd =
+                        c2p_conformal<double>(D, double(cs2), DELTA_F64, M2d, Wd, sc, COUNT);
                     q.vn = R(qd.vn);
                     q.p = R(qd.p);
-                    count(sc, CNT_F64_REDO);
+                    if (COUNT) count(sc, CNT_F64_REDO);
                 }
             }
             return q;
@@ -307,13 +336,13 @@ struct Physics {
         const int lim = sc.limiter;
         const R half = R(0.5);
         R s;
-        s = limited_slope<R>(lim, v0.e - vm.e, vp.e - v0.e);
+        s = slope_ct<LIM, R>(lim, v0.e - vm.e, vp.e - v0.e);
         ul.e = v0.e - half * s; ur.e = v0.e + half * s;
-        s = limited_slope<R>(lim, v0.n - vm.n, vp.n - v0.n);
+        s = slope_ct<LIM, R>(lim, v0.n - vm.n, vp.n - v0.n);
         ul.n = v0.n - half * s; ur.n = v0.n + half * s;
-        s = limited_slope<R>(lim, v0.t1 - vm.t1, vp.t1 - v0.t1);
+        s = slope_ct<LIM, R>(lim, v0.t1 - vm.t1, vp.t1 - v0.t1);
         ul.t1 = v0.t1 - half * s; ur.t1 = v0.t1 + half * s;
-        s = limited_slope<R>(lim, v0.t2 - vm.t2, vp.t2 - v0.t2);
+        s = slope_ct<LIM, R>(lim, v0.t2 - vm.t2, vp.t2 - v0.t2);
         ul.t2 = v0.t2 - half * s; ur.t2 = v0.t2 + half * s;
         if (sc.hancock) {
             const V4<R> FL = flux(ul), FR = flux(ur);
@@ -326,7 +355,7 @@ struct Physics {
         }
         if (!admissible(ul) || !admissible(ur)) {
             ul = v0; ur = v0;
-            count(sc, CNT_FACE_FALLBACK);
+            if (COUNT) count(sc, CNT_FACE_FALLBACK);
         }
     }
 
@@ -335,7 +364,7 @@ struct Physics {
         const R al = R(sc.alpha) * lam;
         const R clw = R(0.5) * al;
         const R clf = R(0.5) / al;
-        const R half = R(0.5);
+        const R half = R(0.5), q4 = R(0.25), hclf = R(0.5) * clf;
         V4<R> Fc;
         const int k = sc.stages;
 #pragma unroll 1
@@ -347,10 +376,11 @@ struct Physics {
             Ulw.t1 = half * (UL.t1 + UR.t1) - clw * (FR.t1 - FL.t1);
             Ulw.t2 = half * (UL.t2 + UR.t2) - clw * (FR.t2 - FL.t2);
             const V4<R> Flw = flux(Ulw);
-            Fc.e = half * (Flw.e + (half * (FL.e + FR.e) - clf * (UR.e - UL.e)));
-            Fc.n = half * (Flw.n + (half * (FL.n + FR.n) - clf * (UR.n - UL.n)));
-            Fc.t1 = half * (Flw.t1 + (half * (FL.t1 + FR.t1) - clf * (UR.t1 - UL.t1)));
-            Fc.t2 = half * (Flw.t2 + (half * (FL.t2 + FR.t2) - clf * (UR.t2 - UL.t2)));
+            // F = 1/2 F_lw + 1/2 F_lf = 1/2 F_lw + 1/4 (F_L + F_R) - (clf/2) (U_R - U_L)
+            Fc.e = half * Flw.e + (q4 * (FL.e + FR.e) - hclf * (UR.e - UL.e));
+            Fc.n = half * Flw.n + (q4 * (FL.n + FR.n) - hclf * (UR.n - UL.n));
+            Fc.t1 = half * Flw.t1 + (q4 * (FL.t1 + FR.t1) - hclf * (UR.t1 - UL.t1));
+            Fc.t2 = half * Flw.t2 + (q4 * (FL.t2 + FR.t2) - hclf * (UR.t2 - UL.t2));
             if (l < k - 1) {
                 UL.e = UL.e - lam * (Fc.e - FL.e);
                 UL.n = UL.n - lam * (Fc.n - FL.n);
@@ -398,21 +428,23 @@ struct Stage {
     }
 };
 
-// Where a thread's pencil lives.
+// Where a thread's pencil lives: field q of cell j is base[fo[q] + j * stride],
+// with fo = (0, M_axis, M_t1, M_t2) field offsets in elements.
 template <class R>
 struct Pencil {
-    const R *f0, *f1, *f2, *f3;   // input: E, M_axis, M_t1, M_t2 (pencil base applied)
-    R *g0, *g1, *g2, *g3;         // output
-    long long stride;
+    const R *in;
+    R *out;
+    int fo1, fo2, fo3;    // offsets of the three momentum slots (E is at 0)
+    int stride;
     int N;
 
     __device__ __forceinline__ V4<R> load(int j) const {
-        const long long o = (long long)j * stride;
-        return v4<R>(__ldg(f0 + o), __ldg(f1 + o), __ldg(f2 + o), __ldg(f3 + o));
+        const R *p = in + j * stride;
+        return v4<R>(__ldg(p), __ldg(p + fo1), __ldg(p + fo2), __ldg(p + fo3));
     }
     __device__ __forceinline__ void store(int j, const V4<R> &v) const {
-        const long long o = (long long)j * stride;
-        g0[o] = v.e; g1[o] = v.n; g2[o] = v.t1; g3[o] = v.t2;
+        R *p = out + j * stride;
+        p[0] = v.e; p[fo1] = v.n; p[fo2] = v.t1; p[fo3] = v.t2;
     }
 };
 

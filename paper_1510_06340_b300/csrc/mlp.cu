@@ -1,6 +1,7 @@
 // mlp.cu -- the Newton-seed MLP (not in the paper): a 2 -> 32 -> 32 -> 1 tanh
-// network that maps (ln E, |M|/E) to the ratio v/(|M|/E), giving the start of
-// the Newton cons->prim solve for a tabulated EOS.  The 32x32 layer runs on
+// network that maps (ln E, x = |M|/E) to where the root v lies between the
+// p = e/3 root vc and x, giving the start of the Newton cons->prim solve for a
+// tabulated EOS.  The 32x32 layer runs on
 // the tensor cores (mma.sync m16n8k16, BF16 operands, FP32 accumulation);
 // its inputs and the weights are rounded to BF16, everything else is FP32.
 // Training (loss gradient + Adam) runs on the GPU with the same forward and
@@ -74,7 +75,8 @@ k_mlp_loss_grad(const float *__restrict__ F, const __nv_bfloat16 *__restrict__ W
                                             H2 + wbase * LDH, LDH, z);
     const float r = 1.0f / (1.0f + __expf(-z));
     const float d = ok ? v0 - y : 0.f;
-    DZ[t] = 2.0f * d * inv_n * x * r * (1.0f - r);
+    const float vc = 3.0f * x / (2.0f + sqrtf(4.0f - 3.0f * x * x));
+    DZ[t] = 2.0f * d * inv_n * (x - vc) * r * (1.0f - r);
     IN0[t] = in0;
     IN1[t] = in1;
     LS[t] = d * d;

@@ -34,7 +34,8 @@ __device__ __forceinline__ float mlp_seed_scalar(const Scheme &sc, float lnE, fl
             s = fmaf(__bfloat162float(Wb[MLP_OFF_W2 + j * MLP_H + k]), h1[k], s);
         z = fmaf(__bfloat162float(Wb[MLP_OFF_W3 + j]), tanhf(s + __ldg(F + MLP_OFF_B2 + j)), z);
     }
-    return x / (1.0f + __expf(-z));
+    const float vc = 3.0f * x / (2.0f + sqrtf(4.0f - 3.0f * x * x));
+    return vc + (x - vc) / (1.0f + __expf(-z));
 }
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
@@ -143,7 +144,8 @@ __device__ __forceinline__ float mlp_warp_forward(const float *__restrict__ F,
     const float z = (tile == 0 ? (hh == 0 ? z00 : z01) : (hh == 0 ? z10 : z11)) +
                     __ldg(F + MLP_OFF_B3);
     z_out = z;
-    return x / (1.0f + __expf(-z));
+    const float vc = 3.0f * x / (2.0f + sqrtf(4.0f - 3.0f * x * x));
+    return vc + (x - vc) / (1.0f + __expf(-z));
 }
 
 

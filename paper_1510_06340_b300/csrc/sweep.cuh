@@ -11,12 +11,20 @@ namespace hy {
 // Task -> (pencil, segment): pencil = task % P, segment = task / P, so
 // neighbouring threads march neighbouring pencils (coalesced along x for the
 // y and z sweeps).
-template <class R, int PREC, int EOSK, int RK>
-__global__ void __launch_bounds__(256)
+// HY_SWEEP_MAXNREG (a build-time define) caps the registers of the sweep
+// kernels instead of the default bound of 256 threads per block.
+#ifdef HY_SWEEP_MAXNREG
+#define HY_SWEEP_BOUNDS __maxnreg__(HY_SWEEP_MAXNREG)
+#else
+#define HY_SWEEP_BOUNDS __launch_bounds__(256)
+#endif
+
+template <class R, int PREC, int EOSK, int RK, int LIM, bool COUNT>
+__global__ void HY_SWEEP_BOUNDS
 k_sweep(const R *__restrict__ in, R *__restrict__ out, const EventGeo *__restrict__ ev,
         const WorkItem *__restrict__ items, int nitems, int axis, double frac,
         const EventClock *__restrict__ clk, Scheme sc) {
-    Physics<R, PREC, EOSK> ph;
+    Physics<R, PREC, EOSK, LIM, COUNT> ph;
     ph.sc = sc;
     ph.cs2 = R(sc.cs2);
     ph.delta = R(sc.delta);
@@ -48,17 +56,12 @@ k_sweep(const R *__restrict__ in, R *__restrict__ out, const EventGeo *__restric
         }
         const int ta = axis == 0 ? 2 : 1, tb = axis == 2 ? 2 : 3;
         Pencil<R> Pc;
-        const R *ib = in + g.off + base;
-        R *ob = out + g.off + base;
-        Pc.f0 = ib;
-        Pc.f1 = ib + (1 + axis) * cells;
-        Pc.f2 = ib + ta * cells;
-        Pc.f3 = ib + tb * cells;
-        Pc.g0 = ob;
-        Pc.g1 = ob + (1 + axis) * cells;
-        Pc.g2 = ob + ta * cells;
-        Pc.g3 = ob + tb * cells;
-        Pc.stride = stride;
+        Pc.in = in + g.off + base;
+        Pc.out = out + g.off + base;
+        Pc.fo1 = int((1 + axis) * cells);
+        Pc.fo2 = int(ta * cells);
+        Pc.fo3 = int(tb * cells);
+        Pc.stride = int(stride);
         Pc.N = N;
         const R lam = R(frac * clk[w.event].dt / g.h[axis]);
         const int s0 = seg * L;
@@ -71,18 +74,32 @@ template <class R, int PREC>
 cudaError_t launch_sweep_prec(const SweepLaunch &a) {
     const R *in = static_cast<const R *>(a.in);
     R *out = static_cast<R *>(a.out);
-#define HY_SWEEP(EOSK, RK)                                                                   \
-    if (a.sc.eos_kind == EOSK && a.rk == RK) {                                              \
-        k_sweep<R, PREC, EOSK, RK><<<a.blocks, a.threads, 0, a.stream>>>(                    \
+#define HY_SWEEP(EOSK, RK, LIM, COUNT)                                                       \
+    {                                                                                       \
+        k_sweep<R, PREC, EOSK, RK, LIM, COUNT><<<a.blocks, a.threads, 0, a.stream>>>(       \
             in, out, a.ev, a.items, a.nitems, a.axis, a.frac, a.clk, a.sc);                 \
         return cudaGetLastError();                                                          \
     }
-    HY_SWEEP(EOS_CONFORMAL, 1)
-    HY_SWEEP(EOS_CONFORMAL, 2)
-    HY_SWEEP(EOS_CONFORMAL, 3)
-    HY_SWEEP(EOS_TABLE, 1)
-    HY_SWEEP(EOS_TABLE, 2)
-    HY_SWEEP(EOS_TABLE, 3)
+    // specialised kernels (limiter fixed at compile time, no counters) for the
+    // conformal RK2 scheme; everything else takes the runtime-limiter kernel
+    if (a.sc.eos_kind == EOS_CONFORMAL && a.rk == 2 && !a.sc.counters) {
+        switch (a.sc.limiter) {
+        case LIM_MINMOD: HY_SWEEP(EOS_CONFORMAL, 2, LIM_MINMOD, false)
+        case LIM_MC: HY_SWEEP(EOS_CONFORMAL, 2, LIM_MC, false)
+        case LIM_SUPERBEE: HY_SWEEP(EOS_CONFORMAL, 2, LIM_SUPERBEE, false)
+        case LIM_NONE: HY_SWEEP(EOS_CONFORMAL, 2, LIM_NONE, false)
+        default: break;
+        }
+    }
+    if (a.sc.eos_kind == EOS_CONFORMAL) {
+        if (a.rk == 1) HY_SWEEP(EOS_CONFORMAL, 1, -1, true)
+        if (a.rk == 2) HY_SWEEP(EOS_CONFORMAL, 2, -1, true)
+        if (a.rk == 3) HY_SWEEP(EOS_CONFORMAL, 3, -1, true)
+    } else {
+        if (a.rk == 1) HY_SWEEP(EOS_TABLE, 1, -1, true)
+        if (a.rk == 2) HY_SWEEP(EOS_TABLE, 2, -1, true)
+        if (a.rk == 3) HY_SWEEP(EOS_TABLE, 3, -1, true)
+    }
 #undef HY_SWEEP
     return cudaErrorInvalidValue;
 }
