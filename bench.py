@@ -365,6 +365,124 @@ def run_batch(args):
     return 0
 
 
+def train_seed_mlp(hydro, I, tab, n=65536, epochs=150, seed=13):
+    """Train the Newton-seed MLP on the GPU on (T^{0mu}, v) pairs made by the
+    solver itself (device prim->cons, then the plain Newton solve)."""
+    import torch
+    rng = np.random.default_rng(seed)
+    e = np.exp(rng.uniform(np.log(1e-3), np.log(1e2), n))
+    v = 0.95 * rng.uniform(0, 1, n) ** 0.5
+    d = rng.normal(size=(3, n))
+    d /= np.linalg.norm(d, axis=0)
+    h = hydro.Hydro(hydro.make_grid(n, dx=1.0, prec="fp64"), hydro.make_eos(tab, seed="zero"))
+    h.set_primitives(*[a.reshape(1, 1, n) for a in (e, v * d[0], v * d[1], v * d[2])])
+    U = torch.tensor(h.get_conserved().reshape(4, n), device="cuda")
+    vm = torch.empty(n, dtype=torch.float64, device="cuda")
+    it = torch.empty(n, dtype=torch.int32, device="cuda")
+    h.c2p_newton(U, "zero", vm, it)
+    Uh = U.cpu().numpy()
+    E, M = Uh[0], np.linalg.norm(Uh[1:], axis=0)
+    X = np.column_stack([np.log(E), M / E])
+    P = rng.normal(size=hydro.mlp_nparam()) * 0.3
+    P[-4:] = [X[:, 0].mean(), X[:, 0].std(), X[:, 1].mean(), X[:, 1].std()]
+    params = torch.tensor(P, dtype=torch.float32, device="cuda")
+    hist = torch.zeros(epochs, dtype=torch.float32, device="cuda")
+    t0 = time.perf_counter()
+    hydro.mlp_train(params, torch.tensor(X, dtype=torch.float32, device="cuda"),
+                    torch.tensor(vm.cpu().numpy(), dtype=torch.float32, device="cuda"),
+                    512, epochs, 3e-3, 7, hist)
+    torch.cuda.synchronize()
+    return params.cpu().numpy(), float(hist[-1].item()), time.perf_counter() - t0
+
+
+def run_learned(args):
+    """Tabulated non-conformal EOS: 128 events on 128^3 hot-spot grids, FP32
+    batch with cons->prim by Newton seeded by the trained MLP, against the
+    same batch with the plain seeds and against the plain FP64 per-event path
+    (one event at a time, FP64, v0 = 0).  Metric: events/s (100 steps each)."""
+    import torch
+    from paper_1510_06340_b300 import build, hydro
+    from paper_1510_06340_b300 import inputs as I
+
+    def rel_l1(a, b):
+        a = np.asarray(a, dtype=np.float64)
+        b = np.asarray(b, dtype=np.float64)
+        fl = 1e-3 * np.abs(b[0]).sum()
+        return [float(np.abs(a[q] - b[q]).sum() / max(np.abs(b[q]).sum(), fl)) for q in range(4)]
+    torch.cuda.set_device(0)
+    build.build(verbose=False)
+    tab = I.eos_table()
+    params, loss, train_s = train_seed_mlp(hydro, I, tab)
+    nev, n = args.events, 128
+    g0 = I.event_grid(n, 0.1)
+    spots = np.stack([I.hotspots(e) for e in range(nev)])
+    stream = torch.cuda.Stream()
+
+    def batch(seed, steps, prec="fp32", events=nev, counters=False):
+        grids = [hydro.make_grid(n, n, n, dx=0.1, x0=g0["x0"], y0=g0["y0"], z0=g0["z0"],
+                                 bc="outflow", prec=prec, cfl=0.4) for _ in range(events)]
+        b = hydro.Batch(grids, hydro.make_eos(tab, seed=seed, mlp_params=params),
+                        limiter="minmod", stages=2, stream=stream)
+        b.init_hotspots(spots[:events], I.SPOT_SIGMA, I.E_BACKGROUND)
+        b.step(args.warmup)
+        torch.cuda.synchronize()
+        if counters:
+            b.enable_counters(True)
+            b.step(1)
+            c = b.counters()
+            return None, c["newton_iters"] / max(c["newton_calls"], 1), b
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        return events * steps / 100.0 / (ms * 1e-3), None, b
+
+    res = {}
+    with Clocks(0) as clk:
+        for seed in ("mlp", "zero", "conformal"):
+            res[seed] = batch(seed, args.steps)[0]
+    iters = {seed: batch(seed, 1, events=4, counters=True)[1] for seed in ("mlp", "zero", "conformal")}
+    # plain FP64 per-event path: one event, v0 = 0, timed over 2 steps
+    h = hydro.Hydro(hydro.make_grid(n, n, n, dx=0.1, x0=g0["x0"], y0=g0["y0"], z0=g0["z0"],
+                                    bc="outflow", prec="fp64", cfl=0.4),
+                    hydro.make_eos(tab, seed="zero"), limiter="minmod", stages=2, stream=stream)
+    h.init_hotspots(spots[0], I.SPOT_SIGMA, I.E_BACKGROUND)
+    h.step(1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    h.step(2)
+    torch.cuda.synchronize()
+    fp64_event_s = (time.perf_counter() - t0) / 2 * 100
+    # error of the learned FP32 batch against the FP64 path after the same steps
+    k = 4
+    _, _, bl = batch("mlp", 0, events=1)
+    bl.step(k)
+    h2 = hydro.Hydro(hydro.make_grid(n, n, n, dx=0.1, x0=g0["x0"], y0=g0["y0"], z0=g0["z0"],
+                                     bc="outflow", prec="fp64", cfl=0.4),
+                     hydro.make_eos(tab, seed="zero"), limiter="minmod", stages=2, stream=stream)
+    h2.init_hotspots(spots[0], I.SPOT_SIGMA, I.E_BACKGROUND)
+    h2.step(args.warmup + k)
+    err = rel_l1(bl.get_conserved(0), h2.get_conserved())
+    line = {"metric": "events_per_s", "value": res["mlp"], "unit": "events/s (100 steps each)",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"{nev} events on 128^3, tabulated EOS (4096 nodes), "
+                                   "hot spots, FP32, minmod, 2 MUSTA stages, RK2+Hancock, Strang, "
+                                   "Newton cons->prim seeded by the BF16 tensor-core MLP"},
+            "events_per_s_by_seed": res,
+            "newton_iterations_per_solve": iters,
+            "fp64_per_event_events_per_s": 1.0 / fp64_event_s,
+            "learned_fp32_vs_fp64_rel_l1": err,
+            "mlp_final_loss": loss, "mlp_train_s": train_s,
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -372,7 +490,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="blast256_fp32",
-                    choices=sorted(WORKLOADS) + ["batch512"])
+                    choices=sorted(WORKLOADS) + ["batch512", "learned128"])
     ap.add_argument("--events", type=int, default=512, help="events per GPU (batch512)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--launch", default="", help="force 'threads,segments' for every axis")
@@ -384,6 +502,10 @@ def main():
         return run_reference(args)
     if args.workload == "batch512":
         return run_batch(args)
+    if args.workload == "learned128":
+        if args.events == 512:
+            args.events = 128
+        return run_learned(args)
     return run_ours(args)
 
 

@@ -255,7 +255,8 @@ hydro_status hydro_mlp_forward(const float *params, const float *X, int n, float
 hydro_status hydro_mlp_loss_grad(const float *params, const float *X, const float *Y, int n,
                                  float *grad, float *loss, void *stream);
 /* Adam training on the device: params (device, [nparam], updated in place),
- * X [n][2], Y [n]; minibatches of `batch`, `epochs` passes, learning rate lr.
+ * X [n][2], Y [n]; minibatches of `batch` (reshuffled every epoch with `seed`),
+ * `epochs` passes, learning rate lr decayed along a half cosine to 0.
  * loss_hist (device, [epochs]) receives the mean loss of each epoch. */
 hydro_status hydro_mlp_train(float *params, const float *X, const float *Y, int n, int batch,
                              int epochs, float lr, unsigned long long seed, float *loss_hist,

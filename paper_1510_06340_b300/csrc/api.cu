@@ -136,6 +136,7 @@ struct Solver {
         c.blocks = (int)std::min<size_t>(cell_items.size(), (size_t)sms * 8);
         c.stream = stream;
         c.prec = prec == HYDRO_FP64 ? 0 : 1;
+        c.mixed = prec == HYDRO_MIXED ? 1 : 0;
         c.sc = scheme();
         return c;
     }

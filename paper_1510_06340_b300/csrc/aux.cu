@@ -80,7 +80,8 @@ __global__ void k_prim2cons(const EventGeo *__restrict__ ev, const WorkItem *__r
 template <class R>
 __global__ void k_cons2prim(const EventGeo *__restrict__ ev, const WorkItem *__restrict__ items,
                             int nitems, const R *__restrict__ U, R *__restrict__ e,
-                            R *__restrict__ vx, R *__restrict__ vy, R *__restrict__ vz, Scheme sc) {
+                            R *__restrict__ vx, R *__restrict__ vy, R *__restrict__ vz, Scheme sc,
+                            int mixed) {
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
         const WorkItem w = items[it];
         const EventGeo &g = ev[w.event];
@@ -88,8 +89,18 @@ __global__ void k_cons2prim(const EventGeo *__restrict__ ev, const WorkItem *__r
             const long long c = w.first + k;
             const R *u = U + g.off + c;
             int iters;
-            c2p_full<R>(sc, u[0], u[g.cells], u[2 * g.cells], u[3 * g.cells], e[c], vx[c], vy[c],
-                        vz[c], iters);
+            R ee, x, y, z;
+            c2p_full<R>(sc, u[0], u[g.cells], u[2 * g.cells], u[3 * g.cells], ee, x, y, z, iters);
+            if (mixed && x * x + y * y + z * z > R(0.9801)) {
+                // e = E - M v cancels as |v| -> 1: redo from the same inputs in double
+                Scheme sd = sc;
+                sd.delta = DELTA_F64;
+                double de, dx_, dy_, dz_;
+                c2p_full<double>(sd, double(u[0]), double(u[g.cells]), double(u[2 * g.cells]),
+                                 double(u[3 * g.cells]), de, dx_, dy_, dz_, iters);
+                ee = R(de); x = R(dx_); y = R(dy_); z = R(dz_);
+            }
+            e[c] = ee; vx[c] = x; vy[c] = y; vz[c] = z;
         }
     }
 }
@@ -97,13 +108,43 @@ __global__ void k_cons2prim(const EventGeo *__restrict__ ev, const WorkItem *__r
 // ------------------------------------------------------------------ CFL rate
 // reading R8: largest |characteristic speed| / dx over cells and swept axes,
 // computed in the state's precision.  With b = c sqrt(rad) >= 0,
-// max(|a + b|, |a - b|) = |a| + b.
+// max(|a + b|, |a - b|) = |a| + b.  Each block keeps a running max over its
+// consecutive work items of one event and adds it with one atomic.
+template <class R>
+__device__ __forceinline__ R max_nan(R a, R b) { return (b > a || b != b) ? b : a; }
+
+// block-wide max of m (NaN propagates), then one atomic per block and event run
+template <class R>
+__device__ __forceinline__ void flush_rate(R m, int event, EventClock *clk, R *red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max_nan(m, __shfl_xor_sync(0xffffffffu, m, o));
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) red[wid] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        R t = red[0];
+        for (int k = 1; k < int(blockDim.x >> 5); ++k) t = max_nan(t, red[k]);
+        atomicMax(&clk[event].rate_bits, (unsigned long long)__double_as_longlong(double(t)));
+    }
+    __syncthreads();
+}
+
 template <class R>
 __global__ void k_rate(const EventGeo *__restrict__ ev, const WorkItem *__restrict__ items,
                        int nitems, const R *__restrict__ U, EventClock *__restrict__ clk,
                        Scheme sc) {
-    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    __shared__ R red[32];
+    R m = R(0);
+    int cur_event = -1;
+    const int per = (nitems + gridDim.x - 1) / gridDim.x;   // a contiguous range per block
+    const int it_end = min(nitems, (blockIdx.x + 1) * per);
+    for (int it = blockIdx.x * per; it < it_end; ++it) {
         const WorkItem w = items[it];
+        if (w.event != cur_event) {     // block-uniform
+            if (cur_event >= 0) flush_rate<R>(m, cur_event, clk, red);
+            m = R(0);
+            cur_event = w.event;
+        }
         const EventGeo &g = ev[w.event];
         R invh[3];
         if (sizeof(R) == 8) {
@@ -112,7 +153,6 @@ __global__ void k_rate(const EventGeo *__restrict__ ev, const WorkItem *__restri
             invh[0] = R(g.inv_hf[0]); invh[1] = R(g.inv_hf[1]); invh[2] = R(g.inv_hf[2]);
         }
         const bool act[3] = {g.n[0] > 1, g.n[1] > 1, g.n[2] > 1};
-        R m = R(0);
         for (int k = threadIdx.x; k < w.count; k += blockDim.x) {
             const long long c = w.first + k;
             const R *u = U + g.off + c;
@@ -131,20 +171,11 @@ __global__ void k_rate(const EventGeo *__restrict__ ev, const WorkItem *__restri
                 R rad = (R(1) - v2) * (R(1) - vd[d] * vd[d] - (v2 - vd[d] * vd[d]) * c2);
                 rad = rad < R(0) ? R(0) : rad;
                 const R a = vd[d] * (R(1) - c2);
-                const R r = (fabs_(a) + cs * dsqrt_(rad)) * inv_den * invh[d];
-                m = (r > m || r != r) ? r : m;   // NaN propagates
+                m = max_nan(m, (fabs_(a) + cs * dsqrt_(rad)) * inv_den * invh[d]);
             }
         }
-        // warp shuffle max, then one atomic per warp
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const R x = __shfl_xor_sync(0xffffffffu, m, o);
-            m = (x > m || x != x) ? x : m;
-        }
-        if ((threadIdx.x & 31) == 0)
-            atomicMax(&clk[w.event].rate_bits,
-                      (unsigned long long)__double_as_longlong(double(m)));
     }
+    if (cur_event >= 0) flush_rate<R>(m, cur_event, clk, red);
 }
 
 // ------------------------------------------------------------------ dt
@@ -375,9 +406,10 @@ cudaError_t launch_cons2prim(const CellLaunch &c, const void *U, void *e, void *
                              void *vz) {
     HY_DISPATCH(c.prec,
         (k_cons2prim<double><<<c.blocks, c.threads, 0, c.stream>>>(c.ev, c.items, c.nitems,
-            (const double *)U, (double *)e, (double *)vx, (double *)vy, (double *)vz, c.sc)),
+            (const double *)U, (double *)e, (double *)vx, (double *)vy, (double *)vz, c.sc, 0)),
         (k_cons2prim<float><<<c.blocks, c.threads, 0, c.stream>>>(c.ev, c.items, c.nitems,
-            (const float *)U, (float *)e, (float *)vx, (float *)vy, (float *)vz, c.sc)));
+            (const float *)U, (float *)e, (float *)vx, (float *)vy, (float *)vz, c.sc,
+            c.mixed)));
     return cudaGetLastError();
 }
 

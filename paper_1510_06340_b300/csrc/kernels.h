@@ -32,7 +32,8 @@ struct CellLaunch {
     int nitems;
     int threads, blocks;
     cudaStream_t stream;
-    int prec;
+    int prec;             // 0 double, 1 float
+    int mixed;            // float state, cons->prim redone in double where |v| > 0.99
     Scheme sc;
 };
 

@@ -9,6 +9,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdint>
 #include <random>
 #include <vector>
@@ -236,6 +237,8 @@ extern "C" hydro_status hydro_mlp_train(float *params, const float *X, const flo
     std::mt19937_64 rng(seed);
     double b1t = 1.0, b2t = 1.0;
     const int nb = n / batch;   // full minibatches per epoch
+    const double total = double(nb) * epochs;
+    long long step = 0;
     for (int ep = 0; ep < epochs && e == cudaSuccess; ++ep) {
         std::shuffle(perm.begin(), perm.end(), rng);
         e = cudaMemcpyAsync(idx, perm.data(), (size_t)n * sizeof(int), cudaMemcpyHostToDevice, s);
@@ -248,7 +251,9 @@ extern "C" hydro_status hydro_mlp_train(float *params, const float *X, const flo
             cudaMemsetAsync(lbuf, 0, sizeof(float), s);
             e = loss_grad_into(params, w, X, Y, idx, (long long)b * batch, batch, g, lbuf, s);
             if (e != cudaSuccess) break;
-            k_adam<<<(MLP_NPARAM + 255) / 256, 256, 0, s>>>(params, g, m, v, lr, (float)b1t,
+            // cosine decay of the learning rate over the whole run
+            const float lr_t = (float)(0.5 * lr * (1.0 + cos(3.14159265358979 * double(step++) / total)));
+            k_adam<<<(MLP_NPARAM + 255) / 256, 256, 0, s>>>(params, g, m, v, lr_t, (float)b1t,
                                                             (float)b2t);
             k_accumulate<<<1, 32, 0, s>>>(loss_hist + ep, lbuf);
             e = cudaGetLastError();

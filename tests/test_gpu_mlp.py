@@ -103,16 +103,17 @@ def trained(H):
     P = rng.normal(size=nP) * 0.3
     P[-4:] = [X[:, 0].mean(), X[:, 0].std(), X[:, 1].mean(), X[:, 1].std()]
     params = torch.tensor(P, dtype=torch.float32, device="cuda")
-    hist = torch.zeros(40, dtype=torch.float32, device="cuda")
+    hist = torch.zeros(150, dtype=torch.float32, device="cuda")
     H.mlp_train(params, torch.tensor(X, dtype=torch.float32, device="cuda"),
-                torch.tensor(Y, dtype=torch.float32, device="cuda"), 1024, 40, 3e-3, 7, hist)
+                torch.tensor(Y, dtype=torch.float32, device="cuda"), 512, 150, 3e-3, 7, hist)
+    print("training loss by epoch:", hist.cpu().numpy()[::10])
     return tab, params.cpu().numpy(), hist.cpu().numpy()
 
 
 def test_training_on_solver_pairs_lowers_the_loss(H, trained):
     _, _, hist = trained
-    assert hist[-1] < hist[0] / 10, hist
-    assert hist[-1] < 1e-4
+    assert hist[-1] < hist[0] / 100, hist
+    assert hist[-1] < 1e-6
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
@@ -135,7 +136,7 @@ def test_learned_seed_cuts_newton_iterations_and_keeps_the_root(H, trained, prec
     print("mean Newton iterations per solve:", mean_it)
     # the paper's fixed-point start (v0 = 0) is the method without the network
     assert mean_it["mlp"] < 0.85 * mean_it["zero"], mean_it
-    assert mean_it["mlp"] <= mean_it["conformal"] + 0.05, mean_it
+    assert mean_it["mlp"] <= mean_it["conformal"] + 0.1, mean_it
     tol = 1e-12 if prec == "fp64" else 1e-5
     assert np.abs(res["mlp"][0] - res["zero"][0]).max() <= tol
 
