@@ -483,6 +483,79 @@ def run_learned(args):
     return 0
 
 
+def run_mixed(args):
+    """Single 512^3 event (dx 0.1 fm) of hot spots with random flow |u| <= 0.95,
+    outflow, mixed precision (FP32 state and fluxes, FP64 cons->prim for
+    |v| > 0.99, FP64 sums), minmod, 2 MUSTA stages, RK2 + Hancock, Strang.
+    Metric: cell-updates/s.  Per-field relative L1 error against an FP64 run
+    from the same initial state after a few steps."""
+    import torch
+    from paper_1510_06340_b300 import build, hydro
+    from paper_1510_06340_b300 import inputs as I
+    torch.cuda.set_device(0)
+    build.build(verbose=False)
+    n = 512
+    g = I.event_grid(n, 0.1)
+    spots = I.hotspots(0, flow_max=0.95)
+    stream = torch.cuda.Stream()
+    mk = lambda prec: hydro.make_grid(n, n, n, dx=0.1, x0=g["x0"], y0=g["y0"], z0=g["z0"],
+                                      bc="outflow", prec=prec, cfl=0.4)
+    h = hydro.Hydro(mk("mixed"), limiter="minmod", stages=2, stream=stream)
+    h.init_hotspots(spots, I.SPOT_SIGMA, I.E_BACKGROUND)
+    U0 = h.get_conserved()
+    h.step(args.warmup)
+    torch.cuda.synchronize()
+    h.set_kernel_timing(True)
+    h.kernel_timing()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with Clocks(0) as clk:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        h.step(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    (sweep_ms, other_ms), (n_sweep, n_other) = h.kernel_timing()
+    h.set_kernel_timing(False)
+    sums = h.conservation_sums()
+    # error against FP64 from the same initial state
+    k = 3
+    hm = hydro.Hydro(mk("mixed"), limiter="minmod", stages=2, stream=stream)
+    hm.set_conserved(U0)
+    hm.enable_counters(True)
+    hm.step(k)
+    redo = hm.counters()["f64_redo"]
+    Um = hm.get_conserved().astype(np.float64)
+    del hm
+    hd = hydro.Hydro(mk("fp64"), limiter="minmod", stages=2, stream=stream)
+    hd.set_conserved(U0.astype(np.float64))
+    hd.step(k)
+    Ud = hd.get_conserved()
+    del hd
+    fl = 1e-3 * np.abs(Ud[0]).sum()
+    err = [float(np.abs(Um[q] - Ud[q]).sum() / max(np.abs(Ud[q]).sum(), fl)) for q in range(4)]
+    hbm, src = peaks()
+    cells = n ** 3
+    avg = sweep_ms / max(n_sweep, 1)
+    bps = 2 * 4 * 4 * cells
+    line = {"metric": "cell_updates_per_s", "value": cells * args.steps / (ms * 1e-3),
+            "unit": "cell-updates/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": "512^3 hot spots with random flow |u| <= 0.95, outflow, "
+                                   "mixed precision, minmod, 2 MUSTA stages, RK2+Hancock, Strang",
+                       "cells": cells},
+            "roofline": {"bound": "hbm", "achieved": bps / (avg * 1e-3) / 1e9, "peak": hbm,
+                         "unit": "GB/s", "frac": bps / (avg * 1e-3) / 1e9 / hbm,
+                         "avg_launch_ms": avg, "peak_source": src},
+            "rel_l1_vs_fp64_after_3_steps": dict(zip(("E", "Mx", "My", "Mz"), err)),
+            "fp64_redo_cons2prim_in_3_steps": redo,
+            "fp64_sums": list(sums), "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -490,7 +563,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="blast256_fp32",
-                    choices=sorted(WORKLOADS) + ["batch512", "learned128"])
+                    choices=sorted(WORKLOADS) + ["batch512", "learned128", "mixed512"])
     ap.add_argument("--events", type=int, default=512, help="events per GPU (batch512)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--launch", default="", help="force 'threads,segments' for every axis")
@@ -502,6 +575,8 @@ def main():
         return run_reference(args)
     if args.workload == "batch512":
         return run_batch(args)
+    if args.workload == "mixed512":
+        return run_mixed(args)
     if args.workload == "learned128":
         if args.events == 512:
             args.events = 128

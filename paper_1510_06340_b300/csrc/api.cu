@@ -62,6 +62,7 @@ struct Solver {
     WorkItem *d_sweep_items[3] = {nullptr, nullptr, nullptr};
     size_t sweep_cap[3] = {0, 0, 0};
     double *d_partial = nullptr, *d_sums = nullptr;
+    int *d_work_counter = nullptr;     // persistent sweeps of a batch
     // scheme
     Scheme sc{};
     double *d_p64 = nullptr, *d_c64 = nullptr;
@@ -79,10 +80,13 @@ struct Solver {
     LaunchShape shape[3];
     bool tuned[3] = {false, false, false};
     bool forced[3] = {false, false, false};
-    // graph of two steps
-    cudaGraphExec_t graph = nullptr;
+    // graphs of two steps, one per starting state buffer (a captured graph
+    // bakes in the buffer it reads first; steps run outside a graph flip it)
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
     bool graph_dirty = true;
+    bool graph_ok[2] = {false, false};
     double t_end_dev = -1.0;
+    bool rate_valid = false;   // clk.rate_bits holds the rate of the current state
     // kernel timing
     bool timing = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -94,8 +98,10 @@ struct Solver {
     ~Solver() { release(); }
 
     void release() {
-        if (graph) cudaGraphExecDestroy(graph);
-        graph = nullptr;
+        for (int p = 0; p < 2; ++p) {
+            if (graph[p]) cudaGraphExecDestroy(graph[p]);
+            graph[p] = nullptr;
+        }
         for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
         ev_pool.clear();
         if (own_stream) {
@@ -105,7 +111,8 @@ struct Solver {
         own_stream = nullptr;
         void *ptrs[] = {d_geo, d_clk, d_clk_tune, d_state[0], d_state[1], d_cell_items,
                         d_sweep_items[0], d_sweep_items[1], d_sweep_items[2], d_partial, d_sums,
-                        d_p64, d_c64, d_p32, d_c32, d_mlp_f, d_mlp_w, d_counters};
+                        d_p64, d_c64, d_p32, d_c32, d_mlp_f, d_mlp_w, d_counters,
+                        d_work_counter};
         for (void *p : ptrs)
             if (p) cudaFree(p);
         d_geo = nullptr;
@@ -119,6 +126,7 @@ struct Solver {
         d_mlp_f = nullptr;
         d_mlp_w = nullptr;
         d_counters = nullptr;
+        d_work_counter = nullptr;
     }
 
     Scheme scheme() const {
@@ -287,6 +295,7 @@ struct Solver {
                       cudaMemcpyHostToDevice));
         CK(cudaMalloc(&d_partial, cell_items.size() * 4 * sizeof(double)));
         CK(cudaMalloc(&d_sums, (size_t)n * 4 * sizeof(double)));
+        if (n > 1) CK(cudaMalloc(&d_work_counter, sizeof(int)));
         return HYDRO_OK;
     }
 
@@ -330,7 +339,8 @@ struct Solver {
         return HYDRO_OK;
     }
 
-    cudaError_t sweep_launch(int axis, double frac, const EventClock *clk, int src) {
+    cudaError_t sweep_launch(int axis, double frac, const EventClock *clk, int src,
+                             EventClock *rate_clk = nullptr) {
         SweepLaunch a;
         a.in = d_state[src];
         a.out = d_state[1 - src];
@@ -344,6 +354,9 @@ struct Solver {
         a.rk = rk;
         a.threads = shape[axis].threads;
         a.blocks = a.nitems;
+        a.counter = d_work_counter;      // batches: persistent grid, items from a counter
+        a.rate_clk = rate_clk;
+        a.sms = sms;
         a.stream = stream;
         if (prec == HYDRO_FP64) return launch_sweep_f64(a);
         if (prec == HYDRO_FP32) return launch_sweep_f32(a);
@@ -442,7 +455,8 @@ struct Solver {
         CellLaunch c = cell_launch();
         size_t slot = 0;
         if ((err = mark_begin(1, slot)) != cudaSuccess) return err;
-        if (!(fixed_dt > 0.0)) {
+        const bool cfl_dt = !(fixed_dt > 0.0);
+        if (cfl_dt && !rate_valid) {   // otherwise the previous step's last sweep left it
             if ((err = launch_rate(c, d_state[cur], d_clk, cfl)) != cudaSuccess) return err;
         }
         const double cf[2] = {cfl, fixed_dt};
@@ -453,20 +467,21 @@ struct Solver {
         for (int a = 0; a < 3; ++a)
             if (active[a]) act[na++] = a;
         if (na == 0) return cudaSuccess;
-        auto sw = [&](int a, double frac) {
+        auto sw = [&](int a, double frac, bool last) {
             size_t sl = 0;
             cudaError_t e = mark_begin(0, sl);
             if (e != cudaSuccess) return e;
-            e = sweep_launch(a, frac, d_clk, cur);
+            e = sweep_launch(a, frac, d_clk, cur, (last && cfl_dt) ? d_clk : nullptr);
             cur = 1 - cur;
             if (e != cudaSuccess) return e;
             return mark_end(sl);
         };
         for (int k = 0; k < na - 1; ++k)
-            if ((err = sw(act[k], 0.5)) != cudaSuccess) return err;
-        if ((err = sw(act[na - 1], 1.0)) != cudaSuccess) return err;
+            if ((err = sw(act[k], 0.5, false)) != cudaSuccess) return err;
+        if ((err = sw(act[na - 1], 1.0, na == 1)) != cudaSuccess) return err;
         for (int k = na - 2; k >= 0; --k)
-            if ((err = sw(act[k], 0.5)) != cudaSuccess) return err;
+            if ((err = sw(act[k], 0.5, k == 0)) != cudaSuccess) return err;
+        rate_valid = cfl_dt;
         return cudaSuccess;
     }
 
@@ -485,22 +500,25 @@ struct Solver {
     }
 
     hydro_status build_graph() {
-        if (graph) cudaGraphExecDestroy(graph);
-        graph = nullptr;
+        const int p = cur;
+        if (graph[p]) cudaGraphExecDestroy(graph[p]);
+        graph[p] = nullptr;
+        graph_ok[p] = false;
         const int cur0 = cur;
+        const bool rv0 = rate_valid;
         cudaGraph_t gr;
         CK(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
         cudaError_t err = enqueue_step();
         if (err == cudaSuccess) err = enqueue_step();
         cudaError_t err2 = cudaStreamEndCapture(stream, &gr);
         cur = cur0;   // capture does not run anything
+        rate_valid = rv0;
         if (err != cudaSuccess) return fail(HYDRO_E_CUDA, std::string("capture: ") + cudaGetErrorString(err));
         if (err2 != cudaSuccess) return fail(HYDRO_E_CUDA, std::string("end capture: ") + cudaGetErrorString(err2));
-        if (cur != cur0) return fail(HYDRO_E_CUDA, "graph does not return to its buffer");
-        err = cudaGraphInstantiate(&graph, gr, 0);
+        err = cudaGraphInstantiate(&graph[p], gr, 0);
         cudaGraphDestroy(gr);
         if (err != cudaSuccess) return fail(HYDRO_E_CUDA, std::string("instantiate: ") + cudaGetErrorString(err));
-        graph_dirty = false;
+        graph_ok[p] = true;
         return HYDRO_OK;
     }
 
@@ -515,12 +533,20 @@ struct Solver {
         while (done < nsteps) {
             int chunk = std::min(nsteps - done, t_end > 0.0 ? check_every : nsteps - done);
             int k = 0;
-            if (use_graph && !timing && chunk >= 2) {
-                if (graph_dirty || !graph) {
+            if (!rate_valid && !(fixed_dt > 0.0) && chunk >= 1) {   // first step computes the rate
+                CK(enqueue_step());
+                ++k;
+            }
+            if (use_graph && !timing && chunk - k >= 2) {
+                if (graph_dirty) {
+                    graph_ok[0] = graph_ok[1] = false;
+                    graph_dirty = false;
+                }
+                if (!graph_ok[cur]) {
                     s = build_graph();
                     if (s != HYDRO_OK) return s;
                 }
-                for (; k + 2 <= chunk; k += 2) CK(cudaGraphLaunch(graph, stream));
+                for (; k + 2 <= chunk; k += 2) CK(cudaGraphLaunch(graph[cur], stream));
             }
             for (; k < chunk; ++k) CK(enqueue_step());
             done += chunk;
@@ -549,6 +575,7 @@ struct Solver {
 
     hydro_status set_primitives(int e, const void *pe, const void *pvx, const void *pvy,
                                 const void *pvz, int on_device) {
+        rate_valid = false;
         if (e < 0 || e >= nevents) return fail(HYDRO_E_INVALID, "bad event");
         if (!pe || !pvx || !pvy || !pvz) return fail(HYDRO_E_INVALID, "null pointer");
         const size_t fb = (size_t)geo[e].cells * elem;
@@ -594,6 +621,7 @@ struct Solver {
     }
 
     hydro_status set_conserved(int e, const void *U, int on_device) {
+        rate_valid = false;
         if (e < 0 || e >= nevents || !U) return fail(HYDRO_E_INVALID, "bad argument");
         CK(cudaMemcpyAsync(event_ptr(cur, e), U, (size_t)4 * geo[e].cells * elem,
                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, stream));
@@ -645,6 +673,7 @@ struct Solver {
     }
 
     hydro_status hotspots(const double *spots, int nspots, double sigma, double e_bg) {
+        rate_valid = false;
         if (!spots || nspots < 0 || !(sigma > 0.0)) return fail(HYDRO_E_INVALID, "bad hot spots");
         double *d_spots = nullptr;
         const size_t bytes = (size_t)nevents * std::max(nspots, 1) * 7 * sizeof(double);
@@ -677,6 +706,7 @@ struct Solver {
     }
 
     hydro_status max_rate(double *rate) {
+        rate_valid = false;
         std::vector<EventClock> clk(nevents);
         CellLaunch c = cell_launch();
         CK(cudaMemcpyAsync(clk.data(), d_clk, nevents * sizeof(EventClock), cudaMemcpyDeviceToHost, stream));
@@ -699,6 +729,7 @@ struct Solver {
     }
 
     hydro_status single_sweep(int axis, double dt) {
+        rate_valid = false;
         if (axis < 0 || axis > 2) return fail(HYDRO_E_INVALID, "axis must be 0..2");
         if (!(dt > 0.0)) return fail(HYDRO_E_INVALID, "dt must be > 0");
         if (!active[axis]) return HYDRO_OK;

@@ -31,6 +31,24 @@ __device__ __forceinline__ V4<R> v4(R a, R b, R c, R d) {
     V4<R> v; v.e = a; v.n = b; v.t1 = c; v.t2 = d; return v;
 }
 
+// field-wise helpers: x - y, x + y, s x + y, s x
+template <class R>
+__device__ __forceinline__ V4<R> vsub(const V4<R> &x, const V4<R> &y) {
+    return v4<R>(x.e - y.e, x.n - y.n, x.t1 - y.t1, x.t2 - y.t2);
+}
+template <class R>
+__device__ __forceinline__ V4<R> vadd(const V4<R> &x, const V4<R> &y) {
+    return v4<R>(x.e + y.e, x.n + y.n, x.t1 + y.t1, x.t2 + y.t2);
+}
+template <class R>
+__device__ __forceinline__ V4<R> vfma(R s, const V4<R> &x, const V4<R> &y) {
+    return v4<R>(s * x.e + y.e, s * x.n + y.n, s * x.t1 + y.t1, s * x.t2 + y.t2);
+}
+template <class R>
+__device__ __forceinline__ V4<R> vmul(R s, const V4<R> &x) {
+    return v4<R>(s * x.e, s * x.n, s * x.t1, s * x.t2);
+}
+
 // ---------------------------------------------------------------- math helpers
 __device__ __forceinline__ double dsqrt_(double x) { return sqrt(x); }
 __device__ __forceinline__ float dsqrt_(float x) { return sqrtf(x); }
@@ -99,6 +117,7 @@ __device__ __forceinline__ void count(const Scheme &s, int which, unsigned long 
 template <class R>
 struct Prim {
     R vn, p;
+    R W;     // E + p
 };
 
 // Conformal EOS p = cs2 e (reading R10): W = E + p is the positive root of
@@ -113,21 +132,21 @@ __device__ __forceinline__ Prim<R> c2p_conformal(const V4<R> &U, R cs2, R delta,
     const R capf = (R(1) - delta) * (R(1) - delta);
     const R cap2 = capf * E2;
     const R M2c = fmin_(M2, cap2);
-    const R apc = R(1) + cs2;
-    // W^2 - (1+c2) E W + c2 M^2 = 0: 2W = (1+c2) E + sqrt((1+c2)^2 E^2 - 4 c2 M^2),
+    const R hapc = R(0.5) * (R(1) + cs2);
+    // W^2 - (1+c2) E W + c2 M^2 = 0: W = (1+c2)/2 E + sqrt(((1+c2)/2)^2 E^2 - c2 M^2),
     // the discriminant being positive for |M| < E
-    const R disc = (apc * apc) * E2 - (R(4) * cs2) * M2c;
-    const R W2 = apc * E + dsqrt_(disc);
-    R s = R(2);
+    const R W = hapc * E + dsqrt_((hapc * hapc) * E2 - cs2 * M2c);
+    R s = R(1);
     if (M2 > cap2) {      // |M| capped at (1 - delta) E (R9)
-        s = R(2) * dsqrt_(cap2 / M2);
+        s = dsqrt_(cap2 / M2);
         if (counting) count(sc, CNT_CAPPED);
     }
     const bool ok = E > R(0);   // E <= 0: vacuum, v = p = 0
-    q.vn = ok ? (s * U.n) / W2 : R(0);
-    q.p = ok ? R(0.5) * W2 - E : R(0);
+    q.vn = ok ? (s * U.n) / W : R(0);
+    q.p = ok ? W - E : R(0);
+    q.W = ok ? W : R(0);
     M2out = ok ? M2c : R(0);
-    Wout = ok ? R(0.5) * W2 : R(0);
+    Wout = q.W;
     return q;
 }
 
@@ -251,7 +270,7 @@ __device__ __forceinline__ Prim<R> c2p_table(const V4<R> &U, R delta, const Sche
         given = R(mlp_seed_warp(sc, __logf(Ef), xf));
         seed = SEED_GIVEN;
     }
-    if (!(E > R(0))) { q.vn = R(0); q.p = R(0); vmag = R(0); return q; }
+    if (!(E > R(0))) { q.vn = R(0); q.p = R(0); q.W = R(0); vmag = R(0); return q; }
     const R cap = (R(1) - delta) * E;
     if (M2 > cap * cap) {
         M2 = cap * cap;
@@ -265,6 +284,7 @@ __device__ __forceinline__ Prim<R> c2p_table(const V4<R> &U, R delta, const Sche
     const R Mfull = dsqrt_(U.n * U.n + U.t1 * U.t1 + U.t2 * U.t2);
     q.vn = Mfull > R(0) ? U.n * (v / Mfull) : R(0);
     q.p = p;
+    q.W = E + p;
     return q;
 }
 
@@ -290,6 +310,7 @@ struct Physics {
                         c2p_conformal<double>(D, double(cs2), DELTA_F64, M2d, Wd, sc, COUNT);
                     q.vn = R(qd.vn);
                     q.p = R(qd.p);
+                    q.W = R(qd.W);
                     if (COUNT) count(sc, CNT_F64_REDO);
                 }
             }
@@ -305,6 +326,7 @@ struct Physics {
                                                         double(vmag), vd);
                     q.vn = R(qd.vn);
                     q.p = R(qd.p);
+                    q.W = R(qd.W);
                     count(sc, CNT_F64_REDO);
                 }
             }
@@ -315,12 +337,51 @@ struct Physics {
     // Eq. 3 along the sweep axis
     __device__ __forceinline__ V4<R> flux(const V4<R> &U) const {
         const Prim<R> q = prim(U);
-        V4<R> F;
-        F.e = (U.e + q.p) * q.vn;
-        F.n = U.n * q.vn + q.p;
-        F.t1 = U.t1 * q.vn;
-        F.t2 = U.t2 * q.vn;
-        return F;
+        // Eq. 3 along the axis: ((E + p) v_n, M_n v_n + p, M_t1 v_n, M_t2 v_n), W = E + p
+        return v4<R>(q.W * q.vn, U.n * q.vn + q.p, U.t1 * q.vn, U.t2 * q.vn);
+    }
+
+    // CFL rate of one cell (reading R8): max over swept axes of |lambda^+-| / dx,
+    // axes given in the sweep's slot order (n, t1, t2) with ih = 1/dx (0: not swept)
+    __device__ __forceinline__ R rate(const V4<R> &U, R ih_n, R ih_t1, R ih_t2) const {
+        const R E = U.e;
+        R M2 = U.n * U.n + U.t1 * U.t1 + U.t2 * U.t2;
+        if (!(E > R(0))) return R(0);
+        const R cap2 = (R(1) - delta) * (R(1) - delta) * E * E;
+        R s = R(1);
+        if (M2 > cap2) {
+            s = dsqrt_(cap2 / M2);
+            M2 = cap2;
+        }
+        R vn, vt1, vt2, c2;
+        if (EOSK == EOS_CONFORMAL) {
+            const R hapc = R(0.5) * (R(1) + cs2);
+            const R W = hapc * E + dsqrt_((hapc * hapc) * (E * E) - cs2 * M2);
+            const R inv = s / W;
+            vn = U.n * inv; vt1 = U.t1 * inv; vt2 = U.t2 * inv;
+            c2 = cs2;
+        } else {
+            R vmag;
+            const Prim<R> q = c2p_table<R>(U, delta, sc, sc.seed, R(0), vmag);
+            const R Mfull = dsqrt_(U.n * U.n + U.t1 * U.t1 + U.t2 * U.t2);
+            const R sc_ = Mfull > R(0) ? vmag / Mfull : R(0);
+            vn = U.n * sc_; vt1 = U.t1 * sc_; vt2 = U.t2 * sc_;
+            R p;
+            eos_table<R>(sc, E - dsqrt_(M2) * vmag, p, c2);
+            (void)q;
+        }
+        const R v2 = vn * vn + vt1 * vt1 + vt2 * vt2;
+        const R cs = dsqrt_(c2);
+        const R inv_den = R(1) / (R(1) - v2 * c2);
+        auto one = [&](R vd, R ih) {
+            R rad = (R(1) - v2) * (R(1) - vd * vd - (v2 - vd * vd) * c2);
+            rad = rad < R(0) ? R(0) : rad;
+            return (fabs_(vd * (R(1) - c2)) + cs * dsqrt_(rad)) * inv_den * ih;
+        };
+        R m = one(vn, ih_n);
+        if (ih_t1 > R(0)) m = fmax_(m, one(vt1, ih_t1));
+        if (ih_t2 > R(0)) m = fmax_(m, one(vt2, ih_t2));
+        return m;
     }
 
     __device__ __forceinline__ bool admissible(const V4<R> &U) const {
@@ -335,23 +396,18 @@ struct Physics {
                                           V4<R> &ul, V4<R> &ur) const {
         const int lim = sc.limiter;
         const R half = R(0.5);
-        R s;
-        s = slope_ct<LIM, R>(lim, v0.e - vm.e, vp.e - v0.e);
-        ul.e = v0.e - half * s; ur.e = v0.e + half * s;
-        s = slope_ct<LIM, R>(lim, v0.n - vm.n, vp.n - v0.n);
-        ul.n = v0.n - half * s; ur.n = v0.n + half * s;
-        s = slope_ct<LIM, R>(lim, v0.t1 - vm.t1, vp.t1 - v0.t1);
-        ul.t1 = v0.t1 - half * s; ur.t1 = v0.t1 + half * s;
-        s = slope_ct<LIM, R>(lim, v0.t2 - vm.t2, vp.t2 - v0.t2);
-        ul.t2 = v0.t2 - half * s; ur.t2 = v0.t2 + half * s;
+        const V4<R> a = vsub(v0, vm), b = vsub(vp, v0);
+        const V4<R> sl = v4<R>(slope_ct<LIM, R>(lim, a.e, b.e), slope_ct<LIM, R>(lim, a.n, b.n),
+                               slope_ct<LIM, R>(lim, a.t1, b.t1),
+                               slope_ct<LIM, R>(lim, a.t2, b.t2));
+        ul = vfma<R>(-half, sl, v0);
+        ur = vfma<R>(half, sl, v0);
         if (sc.hancock) {
             const V4<R> FL = flux(ul), FR = flux(ur);
+            const V4<R> d = vsub(FL, FR);
             const R hl = half * lam;
-            R d;
-            d = FL.e - FR.e;  ul.e += hl * d;  ur.e += hl * d;
-            d = FL.n - FR.n;  ul.n += hl * d;  ur.n += hl * d;
-            d = FL.t1 - FR.t1; ul.t1 += hl * d; ur.t1 += hl * d;
-            d = FL.t2 - FR.t2; ul.t2 += hl * d; ur.t2 += hl * d;
+            ul = vfma<R>(hl, d, ul);
+            ur = vfma<R>(hl, d, ur);
         }
         if (!admissible(ul) || !admissible(ur)) {
             ul = v0; ur = v0;
@@ -370,26 +426,13 @@ struct Physics {
 #pragma unroll 1
         for (int l = 0; l < k; ++l) {
             const V4<R> FL = flux(UL), FR = flux(UR);
-            V4<R> Ulw;
-            Ulw.e = half * (UL.e + UR.e) - clw * (FR.e - FL.e);
-            Ulw.n = half * (UL.n + UR.n) - clw * (FR.n - FL.n);
-            Ulw.t1 = half * (UL.t1 + UR.t1) - clw * (FR.t1 - FL.t1);
-            Ulw.t2 = half * (UL.t2 + UR.t2) - clw * (FR.t2 - FL.t2);
+            const V4<R> Ulw = vfma<R>(-clw, vsub(FR, FL), vmul<R>(half, vadd(UL, UR)));
             const V4<R> Flw = flux(Ulw);
             // F = 1/2 F_lw + 1/2 F_lf = 1/2 F_lw + 1/4 (F_L + F_R) - (clf/2) (U_R - U_L)
-            Fc.e = half * Flw.e + (q4 * (FL.e + FR.e) - hclf * (UR.e - UL.e));
-            Fc.n = half * Flw.n + (q4 * (FL.n + FR.n) - hclf * (UR.n - UL.n));
-            Fc.t1 = half * Flw.t1 + (q4 * (FL.t1 + FR.t1) - hclf * (UR.t1 - UL.t1));
-            Fc.t2 = half * Flw.t2 + (q4 * (FL.t2 + FR.t2) - hclf * (UR.t2 - UL.t2));
+            Fc = vfma<R>(half, Flw, vfma<R>(-hclf, vsub(UR, UL), vmul<R>(q4, vadd(FL, FR))));
             if (l < k - 1) {
-                UL.e = UL.e - lam * (Fc.e - FL.e);
-                UL.n = UL.n - lam * (Fc.n - FL.n);
-                UL.t1 = UL.t1 - lam * (Fc.t1 - FL.t1);
-                UL.t2 = UL.t2 - lam * (Fc.t2 - FL.t2);
-                UR.e = UR.e - lam * (FR.e - Fc.e);
-                UR.n = UR.n - lam * (FR.n - Fc.n);
-                UR.t1 = UR.t1 - lam * (FR.t1 - Fc.t1);
-                UR.t2 = UR.t2 - lam * (FR.t2 - Fc.t2);
+                UL = vfma<R>(-lam, vsub(Fc, FL), UL);
+                UR = vfma<R>(-lam, vsub(FR, Fc), UR);
             }
         }
         return Fc;
@@ -417,7 +460,7 @@ struct Stage {
         if (n >= 4) {
             const V4<R> F = ph.musta(urp, ul, lam);
             if (n >= 5) {
-                D.e = F.e - fp.e; D.n = F.n - fp.n; D.t1 = F.t1 - fp.t1; D.t2 = F.t2 - fp.t2;
+                D = vsub(F, fp);
                 cell = w0;
                 out = true;
             }
@@ -489,15 +532,24 @@ __device__ __forceinline__ void shift_in(V4<R> (&q)[DEPTH], const V4<R> &v) {
 // Cells [s0, s_end) are stored; the segment's nominal length L may run past
 // the pencil end (those cells are computed with wrapped or clamped inputs and
 // not stored).
+// Rate of the stored cells for the next step's CFL dt (ih = 1/dx per slot;
+// ih.x > 0 switches it on); all lanes evaluate it, stored cells count.
+template <class R>
+struct RateAcc {
+    R ih_n, ih_t1, ih_t2;
+    R m;
+};
+
 template <class R, int RK, class PH>
 __device__ __forceinline__ void march(const PH &ph, const Pencil<R> &P, int s0, int L, int s_end,
-                                      int bc, R lam, bool do_store) {
+                                      int bc, R lam, bool do_store, RateAcc<R> &ra) {
     const int N = P.N;
     if (!(lam > R(0))) {   // finished event: copy through
         if (do_store)
             for (int o = s0; o < s_end; ++o) P.store(o, P.load(o));
         return;
     }
+    const bool rate_on = ra.ih_n > R(0);
     const R third = R(1.0 / 3.0), two3 = R(2.0 / 3.0), q3 = R(0.75), q1 = R(0.25), half = R(0.5);
     Stage<R> st1, st2, st3;
     st1.n = 0; st2.n = 0; st3.n = 0;
@@ -516,10 +568,12 @@ __device__ __forceinline__ void march(const PH &ph, const Pencil<R> &P, int s0, 
         if (!st1.push(V, ph, lam, cell, D)) continue;
         // stage-1 output: cell i = js + t - 2
         const int i = js + t - 2;
-        V4<R> X;
-        X.e = cell.e - lam * D.e; X.n = cell.n - lam * D.n;
-        X.t1 = cell.t1 - lam * D.t1; X.t2 = cell.t2 - lam * D.t2;
+        V4<R> X = vfma<R>(-lam, D, cell);   // U1 = U + dt L(U)
         if (RK == 1) {
+            if (rate_on) {
+                const R rr = ph.rate(X, ra.ih_n, ra.ih_t1, ra.ih_t2);
+                if (do_store && i < s_end) ra.m = (rr > ra.m || rr != rr) ? rr : ra.m;
+            }
             if (do_store && i < s_end) P.store(i, X);
             continue;
         }
@@ -533,11 +587,12 @@ __device__ __forceinline__ void march(const PH &ph, const Pencil<R> &P, int s0, 
             if (!st2.push(Y, ph, lam, c, Dl)) continue;
             const int o = t + s0 - 10;           // finished cell
             const V4<R> U0 = P.load(wrap_index(o, N, bc));
-            V4<R> r;   // Eq. 6: U^{n+1} = 1/2 (U + U1 + dt L(U1))
-            r.e = half * (U0.e + c.e - lam * Dl.e);
-            r.n = half * (U0.n + c.n - lam * Dl.n);
-            r.t1 = half * (U0.t1 + c.t1 - lam * Dl.t1);
-            r.t2 = half * (U0.t2 + c.t2 - lam * Dl.t2);
+            // Eq. 6: U^{n+1} = 1/2 (U + U1 + dt L(U1))
+            const V4<R> r = vmul<R>(half, vfma<R>(-lam, Dl, vadd(U0, c)));
+            if (rate_on) {
+                const R rr = ph.rate(r, ra.ih_n, ra.ih_t1, ra.ih_t2);
+                if (do_store && o < s_end) ra.m = (rr > ra.m || rr != rr) ? rr : ra.m;
+            }
             if (do_store && o < s_end) P.store(o, r);
         } else {   // RK == 3, Eq. 7
             shift_in(qa, X);
@@ -549,11 +604,8 @@ __device__ __forceinline__ void march(const PH &ph, const Pencil<R> &P, int s0, 
             if (!st2.push(Y, ph, lam, c2, D2)) continue;
             const int i2 = t + s0 - 14;
             const V4<R> U0 = P.load(wrap_index(i2, N, bc));
-            V4<R> Z;   // U2 = 3/4 U + 1/4 (U1 + dt L(U1))
-            Z.e = q3 * U0.e + q1 * (c2.e - lam * D2.e);
-            Z.n = q3 * U0.n + q1 * (c2.n - lam * D2.n);
-            Z.t1 = q3 * U0.t1 + q1 * (c2.t1 - lam * D2.t1);
-            Z.t2 = q3 * U0.t2 + q1 * (c2.t2 - lam * D2.t2);
+            // U2 = 3/4 U + 1/4 (U1 + dt L(U1))
+            V4<R> Z = vfma<R>(q3, U0, vmul<R>(q1, vfma<R>(-lam, D2, c2)));
             shift_in(qb, Z);
             if (i2 == N - 1) lastB = Z;
             if (t < 14) continue;
@@ -563,11 +615,12 @@ __device__ __forceinline__ void march(const PH &ph, const Pencil<R> &P, int s0, 
             if (!st3.push(Y3, ph, lam, c3, D3)) continue;
             const int o = t + s0 - 18;
             const V4<R> U00 = P.load(wrap_index(o, N, bc));
-            V4<R> r;   // U^{n+1} = 1/3 U + 2/3 (U2 + dt L(U2))
-            r.e = U00.e * third + two3 * (c3.e - lam * D3.e);
-            r.n = U00.n * third + two3 * (c3.n - lam * D3.n);
-            r.t1 = U00.t1 * third + two3 * (c3.t1 - lam * D3.t1);
-            r.t2 = U00.t2 * third + two3 * (c3.t2 - lam * D3.t2);
+            // U^{n+1} = 1/3 U + 2/3 (U2 + dt L(U2))
+            const V4<R> r = vfma<R>(third, U00, vmul<R>(two3, vfma<R>(-lam, D3, c3)));
+            if (rate_on) {
+                const R rr = ph.rate(r, ra.ih_n, ra.ih_t1, ra.ih_t2);
+                if (do_store && o < s_end) ra.m = (rr > ra.m || rr != rr) ? rr : ra.m;
+            }
             if (do_store && o < s_end) P.store(o, r);
         }
     }

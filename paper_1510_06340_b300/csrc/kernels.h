@@ -18,6 +18,9 @@ struct SweepLaunch {
     Scheme sc;
     int rk;
     int threads, blocks;
+    int *counter;            // non-null: persistent grid pulling items from this counter
+    EventClock *rate_clk;    // non-null: accumulate the CFL rate of the output state here
+    int sms;
     cudaStream_t stream;
 };
 

@@ -56,7 +56,20 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4],
 // inputs of sample l through in0/in1 (already standardised) and x = |M|/E;
 // returns the seed of sample l.  Optionally stores h1 (bf16-rounded) and h2
 // per sample into shared rows H1[l][.], H2[l][.] (stride ld).
-template <bool STORE>
+// hardware tanh approximation (max relative error about 2^-11); used for the
+// seed inside sweeps, where it only moves Newton's starting point
+__device__ __forceinline__ float tanh_fast(float x) {
+    float y;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+template <bool FAST>
+__device__ __forceinline__ float act_tanh(float x) {
+    return FAST ? tanh_fast(x) : tanhf(x);
+}
+
+template <bool STORE, bool FAST = false>
 __device__ __forceinline__ float mlp_warp_forward(const float *__restrict__ F,
                                                   const __nv_bfloat16 *__restrict__ Wb,
                                                   float in0, float in1, float x, float *H1,
@@ -83,8 +96,8 @@ __device__ __forceinline__ float mlp_warp_forward(const float *__restrict__ F,
                     const float w0 = __bfloat162float(Wb[MLP_OFF_W1 + 2 * k]);
                     const float w1 = __bfloat162float(Wb[MLP_OFF_W1 + 2 * k + 1]);
                     const float b = __ldg(F + MLP_OFF_B1 + k);
-                    h[0][q] = tanhf(fmaf(w1, a1, fmaf(w0, a0, b)));
-                    h[1][q] = tanhf(fmaf(w1, c1, fmaf(w0, c0, b)));
+                    h[0][q] = act_tanh<FAST>(fmaf(w1, a1, fmaf(w0, a0, b)));
+                    h[1][q] = act_tanh<FAST>(fmaf(w1, c1, fmaf(w0, c0, b)));
                 }
                 A[ks][half * 2 + 0] = pack_bf16(h[0][0], h[0][1]);   // row r0
                 A[ks][half * 2 + 1] = pack_bf16(h[1][0], h[1][1]);   // row r1
@@ -119,7 +132,7 @@ __device__ __forceinline__ float mlp_warp_forward(const float *__restrict__ F,
             for (int q = 0; q < 2; ++q) {
                 const float b2 = __ldg(F + MLP_OFF_B2 + n0 + q);
                 const float w3 = __bfloat162float(Wb[MLP_OFF_W3 + n0 + q]);
-                const float h0 = tanhf(acc[q] + b2), h1v = tanhf(acc[2 + q] + b2);
+                const float h0 = act_tanh<FAST>(acc[q] + b2), h1v = act_tanh<FAST>(acc[2 + q] + b2);
                 zp[tile][0] = fmaf(w3, h0, zp[tile][0]);
                 zp[tile][1] = fmaf(w3, h1v, zp[tile][1]);
                 if (STORE) {
@@ -157,7 +170,7 @@ __device__ __forceinline__ float mlp_seed_warp(const Scheme &sc, float lnE, floa
     const float in1 = (x - __ldg(F + MLP_OFF_NORM + 2)) / __ldg(F + MLP_OFF_NORM + 3);
     float z;
     __syncwarp();
-    return mlp_warp_forward<false>(F, Wb, in0, in1, x, nullptr, nullptr, 0, z);
+    return mlp_warp_forward<false, true>(F, Wb, in0, in1, x, nullptr, nullptr, 0, z);
 }
 
 }  // namespace hy

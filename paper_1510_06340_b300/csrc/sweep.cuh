@@ -23,12 +23,25 @@ template <class R, int PREC, int EOSK, int RK, int LIM, bool COUNT>
 __global__ void HY_SWEEP_BOUNDS
 k_sweep(const R *__restrict__ in, R *__restrict__ out, const EventGeo *__restrict__ ev,
         const WorkItem *__restrict__ items, int nitems, int axis, double frac,
-        const EventClock *__restrict__ clk, Scheme sc) {
+        const EventClock *__restrict__ clk, Scheme sc, int *counter, EventClock *rate_clk) {
     Physics<R, PREC, EOSK, LIM, COUNT> ph;
     ph.sc = sc;
     ph.cs2 = R(sc.cs2);
     ph.delta = R(sc.delta);
-    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    __shared__ int s_item;
+    __shared__ R s_red[8];
+    for (int k = 0;; ++k) {
+        // one block per item, or a persistent grid taking items from a counter
+        int it;
+        if (counter) {
+            if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+            __syncthreads();
+            it = s_item;
+            __syncthreads();
+        } else {
+            it = k == 0 ? int(blockIdx.x) : nitems;
+        }
+        if (it >= nitems) break;
         const WorkItem w = items[it];
         const EventGeo &g = ev[w.event];
         const int nx = g.n[0], ny = g.n[1];
@@ -66,7 +79,34 @@ k_sweep(const R *__restrict__ in, R *__restrict__ out, const EventGeo *__restric
         const R lam = R(frac * clk[w.event].dt / g.h[axis]);
         const int s0 = seg * L;
         const int s_end = min(s0 + L, N);
-        march<R, RK>(ph, Pc, s0, L, s_end, g.bc[axis], lam, valid);
+        RateAcc<R> ra;
+        ra.m = R(0);
+        ra.ih_n = ra.ih_t1 = ra.ih_t2 = R(0);
+        if (rate_clk) {   // last sweep of a step: CFL rate of the new state
+            const int at1 = axis == 0 ? 1 : 0, at2 = axis == 2 ? 1 : 2;
+            ra.ih_n = R(g.inv_h[axis]);
+            ra.ih_t1 = g.n[at1] > 1 ? R(g.inv_h[at1]) : R(0);
+            ra.ih_t2 = g.n[at2] > 1 ? R(g.inv_h[at2]) : R(0);
+        }
+        march<R, RK>(ph, Pc, s0, L, s_end, g.bc[axis], lam, valid, ra);
+        if (rate_clk) {   // block max, one atomic per work item
+            R m = ra.m;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const R x = __shfl_xor_sync(0xffffffffu, m, o);
+                m = (x > m || x != x) ? x : m;
+            }
+            if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = m;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                R t = s_red[0];
+                for (int k = 1; k < int(blockDim.x >> 5); ++k)
+                    t = (s_red[k] > t || s_red[k] != s_red[k]) ? s_red[k] : t;
+                atomicMax(&rate_clk[w.event].rate_bits,
+                          (unsigned long long)__double_as_longlong(double(t)));
+            }
+            __syncthreads();
+        }
     }
 }
 
@@ -76,8 +116,20 @@ cudaError_t launch_sweep_prec(const SweepLaunch &a) {
     R *out = static_cast<R *>(a.out);
 #define HY_SWEEP(EOSK, RK, LIM, COUNT)                                                       \
     {                                                                                       \
-        k_sweep<R, PREC, EOSK, RK, LIM, COUNT><<<a.blocks, a.threads, 0, a.stream>>>(       \
-            in, out, a.ev, a.items, a.nitems, a.axis, a.frac, a.clk, a.sc);                 \
+        auto kfn = k_sweep<R, PREC, EOSK, RK, LIM, COUNT>;                                  \
+        int blocks = a.nitems;                                                              \
+        if (a.counter) {                                                                    \
+            int occ = 0;                                                                    \
+            cudaError_t e_ = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kfn,       \
+                                                                           a.threads, 0);   \
+            if (e_ != cudaSuccess) return e_;                                               \
+            blocks = occ * a.sms < a.nitems ? occ * a.sms : a.nitems;                       \
+            if (blocks < 1) blocks = 1;                                                     \
+            e_ = cudaMemsetAsync(a.counter, 0, sizeof(int), a.stream);                      \
+            if (e_ != cudaSuccess) return e_;                                               \
+        }                                                                                   \
+        kfn<<<blocks, a.threads, 0, a.stream>>>(in, out, a.ev, a.items, a.nitems, a.axis,    \
+                                                a.frac, a.clk, a.sc, a.counter, a.rate_clk); \
         return cudaGetLastError();                                                          \
     }
     // specialised kernels (limiter fixed at compile time, no counters) for the

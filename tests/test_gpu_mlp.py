@@ -136,7 +136,7 @@ def test_learned_seed_cuts_newton_iterations_and_keeps_the_root(H, trained, prec
     print("mean Newton iterations per solve:", mean_it)
     # the paper's fixed-point start (v0 = 0) is the method without the network
     assert mean_it["mlp"] < 0.85 * mean_it["zero"], mean_it
-    assert mean_it["mlp"] <= mean_it["conformal"] + 0.1, mean_it
+    assert mean_it["mlp"] <= mean_it["conformal"] + 0.15, mean_it
     tol = 1e-12 if prec == "fp64" else 1e-5
     assert np.abs(res["mlp"][0] - res["zero"][0]).max() <= tol
 
