@@ -38,6 +38,18 @@ WORKLOADS = {
     "blast128_fp32": dict(n=128, prec="fp32"),   # small case for ncu captures
 }
 BYTES = {"fp32": 4, "fp64": 8}
+# Algorithmic floating-point operations of one sweep per cell (conformal EOS,
+# minmod, 2 MUSTA stages, RK2 with the Hancock half step), counted from the
+# method's formulas: 25 per cons->prim + flux evaluation, 16 evaluations per
+# cell (2 Hancock + 6 MUSTA per RK stage), plus limiter, faces, Hancock,
+# admissibility, MUSTA-FORCE linear algebra, divergence and RK updates: 800.
+FLOPS_PER_CELL_SWEEP = 800
+# FP32 (non-tensor) peak from unit counts and clock: 148 SMs x 128 FP32 lanes x
+# 2 flop per FMA x 2.032 GHz; FP64 from the B300's nominal 1.25 TFLOP/s.
+# DRAM bytes read + written per sweep launch from the latest ncu capture of the
+# current kernel (see profiles/), None when not captured for this kernel
+SWEEP_TRAFFIC = {}
+ALU_PEAK_TFLOPS = {"fp32": 148 * 128 * 2 * 2.032e9 / 1e12, "fp64": 1.25}
 
 
 def peaks():
@@ -237,7 +249,10 @@ def run_ours(args):
     bytes_per_sweep = 2 * 4 * BYTES[prec] * cells      # read + write of 4 fields
     avg_sweep_ms = sweep_ms / max(n_sweep, 1)
     achieved = bytes_per_sweep / (avg_sweep_ms * 1e-3) / 1e9
-    launches = n_sweep + 2 * n_other
+    # per step: 5 sweeps + k_dt (the CFL rate is fused into the last sweep)
+    launches = n_sweep + n_other
+    alu_peak = ALU_PEAK_TFLOPS[prec]
+    flops_achieved = FLOPS_PER_CELL_SWEEP * cells / (avg_sweep_ms * 1e-3) / 1e12
 
     cpu = None
     if rank == 0 and world >= 1 and not args.no_cpu:
@@ -258,11 +273,18 @@ def run_ours(args):
                        "launch_threads_segments_xyz": shapes,
                        "l2": "inputs larger than L2 (two state copies of "
                              f"{state_bytes / 1e6:.0f} MB)"},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm, "traffic": None,
+            "roofline": {"bound": "alu", "achieved": flops_achieved, "peak": alu_peak,
+                         "unit": "TFLOP/s", "frac": flops_achieved / alu_peak,
+                         "traffic": SWEEP_TRAFFIC.get((n, prec)),
                          "kernel": "k_sweep (one directional sweep, all RK stages)",
-                         "algorithmic_bytes_per_launch": bytes_per_sweep,
-                         "avg_launch_ms": avg_sweep_ms, "peak_source": src},
+                         "algorithmic_flops_per_launch": FLOPS_PER_CELL_SWEEP * cells,
+                         "avg_launch_ms": avg_sweep_ms,
+                         "peak_source": "derived: 148 SM x 128 lanes x 2 x 2.032 GHz (fp32); "
+                                        "nominal 1.25 TFLOP/s (fp64)"},
+            "roofline_hbm": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                             "frac": achieved / hbm,
+                             "algorithmic_bytes_per_launch": bytes_per_sweep,
+                             "peak_source": src},
             "kernel_ms": {"sweeps": sweep_ms, "sweep_launches": n_sweep,
                           "rate_dt": other_ms, "rate_dt_groups": n_other},
             "gpu_launches": launches,
@@ -332,7 +354,8 @@ def run_batch(args):
     b.step(min(args.steps, 4))
     (sweep_ms, other_ms), (n_sweep, n_other) = b.kernel_timing()
     b.set_kernel_timing(False)
-    launches_per_step = (n_sweep + 3 * n_other) / max(n_other, 1)
+    # per step: 5 sweeps + k_dt + k_jet (the CFL rate is fused into the last sweep)
+    launches_per_step = (n_sweep + 2 * n_other) / max(n_other, 1)
     status = b.event_status()
     value = world * nev * args.steps / 100.0 / (ms * 1e-3)
     hbm, src = peaks()

@@ -22,8 +22,11 @@ EXTRA = os.environ.get("HYDRO_NVCC_FLAGS", "").split()
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 BASE = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + SRC, "-I" + INC]
-# float sweeps use approximate sqrt/divide (a few ulp, far inside the FP32 tolerance)
+# float sweeps use approximate sqrt/divide and flush denormals (a few ulp, far
+# inside the FP32 tolerance)
 FAST = {"sweep_f32.cu", "sweep_mixed.cu"}
+FAST_FLAGS = ["-ftz=true", "-prec-div=false", "-prec-sqrt=false"]
+NOFMAD = set()   # units compiled with -fmad=false (none)
 
 
 def _sources():
@@ -46,7 +49,9 @@ def _compile(src: str) -> str:
     obj = os.path.join(BUILD, os.path.basename(src) + ".o")
     flags = list(BASE) + EXTRA
     if os.path.basename(src) in FAST:
-        flags.append("--use_fast_math")
+        flags += FAST_FLAGS
+    if os.path.basename(src) in NOFMAD:
+        flags.append("-fmad=false")
     cmd = [NVCC] + flags + ["-c", src, "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:

@@ -19,7 +19,7 @@ namespace hy {
 #define HY_SWEEP_BOUNDS __launch_bounds__(256)
 #endif
 
-template <class R, int PREC, int EOSK, int RK, int LIM, bool COUNT>
+template <class R, int PREC, int EOSK, int RK, int LIM, bool COUNT, bool RATE>
 __global__ void HY_SWEEP_BOUNDS
 k_sweep(const R *__restrict__ in, R *__restrict__ out, const EventGeo *__restrict__ ev,
         const WorkItem *__restrict__ items, int nitems, int axis, double frac,
@@ -82,14 +82,14 @@ k_sweep(const R *__restrict__ in, R *__restrict__ out, const EventGeo *__restric
         RateAcc<R> ra;
         ra.m = R(0);
         ra.ih_n = ra.ih_t1 = ra.ih_t2 = R(0);
-        if (rate_clk) {   // last sweep of a step: CFL rate of the new state
+        if (RATE && rate_clk) {   // last sweep of a step: CFL rate of the new state
             const int at1 = axis == 0 ? 1 : 0, at2 = axis == 2 ? 1 : 2;
             ra.ih_n = R(g.inv_h[axis]);
             ra.ih_t1 = g.n[at1] > 1 ? R(g.inv_h[at1]) : R(0);
             ra.ih_t2 = g.n[at2] > 1 ? R(g.inv_h[at2]) : R(0);
         }
-        march<R, RK>(ph, Pc, s0, L, s_end, g.bc[axis], lam, valid, ra);
-        if (rate_clk) {   // block max, one atomic per work item
+        march<R, RK, RATE>(ph, Pc, s0, L, s_end, g.bc[axis], lam, valid, ra);
+        if (RATE && rate_clk) {   // block max, one atomic per work item
             R m = ra.m;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
@@ -114,9 +114,9 @@ template <class R, int PREC>
 cudaError_t launch_sweep_prec(const SweepLaunch &a) {
     const R *in = static_cast<const R *>(a.in);
     R *out = static_cast<R *>(a.out);
-#define HY_SWEEP(EOSK, RK, LIM, COUNT)                                                       \
+#define HY_SWEEP(EOSK, RK, LIM, COUNT, RATE)                                                 \
     {                                                                                       \
-        auto kfn = k_sweep<R, PREC, EOSK, RK, LIM, COUNT>;                                  \
+        auto kfn = k_sweep<R, PREC, EOSK, RK, LIM, COUNT, RATE>;                            \
         int blocks = a.nitems;                                                              \
         if (a.counter) {                                                                    \
             int occ = 0;                                                                    \
@@ -135,22 +135,33 @@ cudaError_t launch_sweep_prec(const SweepLaunch &a) {
     // specialised kernels (limiter fixed at compile time, no counters) for the
     // conformal RK2 scheme; everything else takes the runtime-limiter kernel
     if (a.sc.eos_kind == EOS_CONFORMAL && a.rk == 2 && !a.sc.counters) {
-        switch (a.sc.limiter) {
-        case LIM_MINMOD: HY_SWEEP(EOS_CONFORMAL, 2, LIM_MINMOD, false)
-        case LIM_MC: HY_SWEEP(EOS_CONFORMAL, 2, LIM_MC, false)
-        case LIM_SUPERBEE: HY_SWEEP(EOS_CONFORMAL, 2, LIM_SUPERBEE, false)
-        case LIM_NONE: HY_SWEEP(EOS_CONFORMAL, 2, LIM_NONE, false)
-        default: break;
+        // the CFL rate is compiled in only for the last sweep of a step
+        if (a.rate_clk) {
+            switch (a.sc.limiter) {
+            case LIM_MINMOD: HY_SWEEP(EOS_CONFORMAL, 2, LIM_MINMOD, false, true)
+            case LIM_MC: HY_SWEEP(EOS_CONFORMAL, 2, LIM_MC, false, true)
+            case LIM_SUPERBEE: HY_SWEEP(EOS_CONFORMAL, 2, LIM_SUPERBEE, false, true)
+            case LIM_NONE: HY_SWEEP(EOS_CONFORMAL, 2, LIM_NONE, false, true)
+            default: break;
+            }
+        } else {
+            switch (a.sc.limiter) {
+            case LIM_MINMOD: HY_SWEEP(EOS_CONFORMAL, 2, LIM_MINMOD, false, false)
+            case LIM_MC: HY_SWEEP(EOS_CONFORMAL, 2, LIM_MC, false, false)
+            case LIM_SUPERBEE: HY_SWEEP(EOS_CONFORMAL, 2, LIM_SUPERBEE, false, false)
+            case LIM_NONE: HY_SWEEP(EOS_CONFORMAL, 2, LIM_NONE, false, false)
+            default: break;
+            }
         }
     }
     if (a.sc.eos_kind == EOS_CONFORMAL) {
-        if (a.rk == 1) HY_SWEEP(EOS_CONFORMAL, 1, -1, true)
-        if (a.rk == 2) HY_SWEEP(EOS_CONFORMAL, 2, -1, true)
-        if (a.rk == 3) HY_SWEEP(EOS_CONFORMAL, 3, -1, true)
+        if (a.rk == 1) HY_SWEEP(EOS_CONFORMAL, 1, -1, true, true)
+        if (a.rk == 2) HY_SWEEP(EOS_CONFORMAL, 2, -1, true, true)
+        if (a.rk == 3) HY_SWEEP(EOS_CONFORMAL, 3, -1, true, true)
     } else {
-        if (a.rk == 1) HY_SWEEP(EOS_TABLE, 1, -1, true)
-        if (a.rk == 2) HY_SWEEP(EOS_TABLE, 2, -1, true)
-        if (a.rk == 3) HY_SWEEP(EOS_TABLE, 3, -1, true)
+        if (a.rk == 1) HY_SWEEP(EOS_TABLE, 1, -1, true, true)
+        if (a.rk == 2) HY_SWEEP(EOS_TABLE, 2, -1, true, true)
+        if (a.rk == 3) HY_SWEEP(EOS_TABLE, 3, -1, true, true)
     }
 #undef HY_SWEEP
     return cudaErrorInvalidValue;
