@@ -31,9 +31,8 @@ __device__ __forceinline__ V4<R> v4(R a, R b, R c, R d) {
     V4<R> v; v.e = a; v.n = b; v.t1 = c; v.t2 = d; return v;
 }
 
-// Multiply-adds are written out as fma_: the sweep units compile with
-// -fmad=false, so the compiler fuses nothing on its own and every code path
-// (prologue or steady loop, any launch shape) rounds identically.
+// Multiply-adds of the formulas are written out as fma_, so they are fused
+// whatever the compiler's contraction setting.
 __device__ __forceinline__ float fma_(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ double fma_(double a, double b, double c) { return fma(a, b, c); }
 
@@ -684,6 +683,172 @@ __device__ __forceinline__ void march(const PH &ph, const Pencil<R> &P, int s0, 
             if (do_store && o < s_end) P.store(o, r);
         }
     }
+}
+
+// ---------------------------------------------------------------- staged x sweep
+// Along x each thread marches its own row, so a warp touches 32 rows at once.
+// Loading each row cell by cell leaves every 32-byte sector to be assembled
+// from 8 separate requests spread over 8 steps; L1 cannot hold the 32 rows x 4
+// fields of all resident warps that long, so sectors were fetched from DRAM
+// several times and written back in pieces.  Instead each warp stages its 32
+// rows through shared memory in whole sectors: every 8 steps the lanes copy
+// the next 8 cells of all 32 rows (4 rows x 8 cells per instruction, with
+// cp.async, so the copy overlaps the following two steps of arithmetic) into
+// a 16-cell ring per row and field, and finished cells go back 8 at a time
+// from an output ring.  In step space (slot = step & 15) the ring holds steps
+// [t - 6, t + 2) and, once a copy lands, up to t + 10: the input of step t
+// and the cell 6 steps behind it that the RK combination reloads.  Fills and
+// flushes are placed so that rows whose start is 8-cell aligned move whole
+// sectors.
+constexpr int XR = 16;        // input ring: steps per row
+constexpr int XRS = XR + 1;   // row stride (odd: conflict-free column reads)
+constexpr int XO = 8;         // output ring: steps per row
+constexpr int XOS = XO + 1;
+
+template <class R>
+__host__ __device__ constexpr int xstage_floats_per_warp() {
+    return 4 * 32 * XRS + 4 * 32 * XOS;
+}
+
+template <class R>
+__device__ __forceinline__ void cp_async_elem(R *dst, const R *src) {
+    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(d), "l"(src),
+                 "n"(int(sizeof(R))) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
+template <class R>
+struct XStage {
+    R *ring;            // [4][32][XRS]
+    R *oring;           // [4][32][XOS]
+    const R *in;        // event base (field 0, cell 0) of the input state
+    R *out;
+    int fo1, fo2, fo3;  // field offsets (E at 0)
+    int N, bc, lane;
+    int js;             // this lane's position at step 0
+    int rowN;           // this lane's row start: row (pencil) index * N
+
+    // start copying steps t0 .. t0 + 7 of all 32 rows into the ring
+    __device__ __forceinline__ void fill(int t0) {
+        const int c = lane & 7;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int r = (lane >> 3) + 4 * k;
+            const int rn = __shfl_sync(0xffffffffu, rowN, r);
+            const int jr = __shfl_sync(0xffffffffu, js, r);
+            const R *p = in + rn + wrap_index(jr + t0 + c, N, bc);
+            R *q = ring + r * XRS + ((t0 + c) & (XR - 1));
+            cp_async_elem(q, p);
+            cp_async_elem(q + 32 * XRS, p + fo1);
+            cp_async_elem(q + 2 * 32 * XRS, p + fo2);
+            cp_async_elem(q + 3 * 32 * XRS, p + fo3);
+        }
+        cp_async_commit();
+    }
+    __device__ __forceinline__ V4<R> get(int t) const {
+        const R *q = ring + lane * XRS + (t & (XR - 1));
+        return v4<R>(q[0], q[32 * XRS], q[2 * 32 * XRS], q[3 * 32 * XRS]);
+    }
+    __device__ __forceinline__ void put(int t, const V4<R> &v) {
+        R *q = oring + lane * XOS + (t & (XO - 1));
+        q[0] = v.e; q[32 * XOS] = v.n; q[2 * 32 * XOS] = v.t1; q[3 * 32 * XOS] = v.t2;
+    }
+    // write the results of steps t1 - 7 .. t1 (position js + step - 6) whose
+    // keep bits (bit step & 7, per row) are set
+    __device__ __forceinline__ void flush(int t1, unsigned keep) {
+        const int c = lane & 7;
+        const int st = t1 - 7 + c;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int r = (lane >> 3) + 4 * k;
+            const int rn = __shfl_sync(0xffffffffu, rowN, r);
+            const int jr = __shfl_sync(0xffffffffu, js, r);
+            const unsigned kr = __shfl_sync(0xffffffffu, keep, r);
+            if ((kr >> (st & 7)) & 1u) {
+                R *p = out + rn + (jr + st - 6);
+                const R *q = oring + r * XOS + (st & (XO - 1));
+                p[0] = q[0];
+                p[fo1] = q[32 * XOS];
+                p[fo2] = q[2 * 32 * XOS];
+                p[fo3] = q[3 * 32 * XOS];
+            }
+        }
+    }
+};
+
+// RK2 march of x-rows through the warp's shared-memory rings; the same
+// arithmetic, schedule and zero start as march() (Eq. 6), so stored cells
+// are bit-identical to it.  The whole warp must call it together.
+template <class R, bool RATE, class PH>
+__device__ __forceinline__ void march_x_rk2(const PH &ph, XStage<R> &X, int s0, int L, int s_end,
+                                            R lam, bool do_store, RateAcc<R> &ra) {
+    const int N = X.N, bc = X.bc;
+    const bool rate_on = RATE && ra.ih_n > R(0);
+    const R half = R(0.5);
+    const int T = L + 10;
+    const int js = s0 - 4;
+    X.js = js;
+    // fills at steps t = phi (mod 8), t >= 1, each for steps t + 2 .. t + 9,
+    // so that lane 0's row moves 8-aligned cells; flushes at t = psi (mod 8)
+    const int js0 = __shfl_sync(0xffffffffu, js, 0);
+    const int phi = (6 - js0) & 7;
+    const int psi = (13 - js0) & 7;
+    const int tf = phi == 0 ? 8 : phi;   // first fill step
+    Stage<R> st1, st2;
+    const V4<R> zero = v4<R>(R(0), R(0), R(0), R(0));
+    st1.w0 = st1.w1 = st1.w2 = st1.urp = st1.fp = zero;
+    st2.w0 = st2.w1 = st2.w2 = st2.urp = st2.fp = zero;
+    V4<R> qa[3] = {zero, zero, zero};
+    V4<R> lastA = zero, cell, D;
+    __syncwarp();
+    X.fill(tf - 14);
+    X.fill(tf - 6);   // steps [tf - 14, tf + 2) cover [-6, tf + 2)
+    cp_async_wait_all();
+    __syncwarp();
+    unsigned keep = 0u;
+#pragma unroll 1
+    for (int t = 0; t < T; ++t) {
+        if (t >= tf && ((t - phi) & 7) == 0) {   // slots of steps < t - 6 are free
+            __syncwarp();
+            X.fill(t + 2);
+        } else if (t >= tf + 2 && ((t - 2 - phi) & 7) == 0) {   // the copy is needed now
+            cp_async_wait_all();
+            __syncwarp();
+        }
+        const V4<R> V = X.get(t);
+        st1.push_full(V, ph, lam, cell, D);
+        const int i = js + t - 2;
+        const V4<R> Xv = vfma<R>(-lam, D, cell);   // U1 = U + dt L(U)
+        shift_in(qa, Xv);
+        if (i == N - 1) lastA = Xv;
+        const V4<R> Y = pick(qa, i, t + s0 - 8, N, bc, lastA);
+        V4<R> c, Dl;
+        st2.push_full(Y, ph, lam, c, Dl);
+        const int o = t + s0 - 10;
+        const V4<R> U0 = X.get(t - 6);
+        const V4<R> r = vmul<R>(half, vfma<R>(-lam, Dl, vadd(U0, c)));
+        const bool kp = do_store && o >= s0 && o < s_end;
+        if (rate_on) {
+            const R rr = ph.rate(r, ra.ih_n, ra.ih_t1, ra.ih_t2);
+            if (kp) ra.m = (rr > ra.m || rr != rr) ? rr : ra.m;
+        }
+        X.put(t, r);
+        keep |= (kp ? 1u : 0u) << (t & 7);
+        if (((t - psi) & 7) == 0 || t == T - 1) {
+            __syncwarp();
+            X.flush(t, keep);
+            __syncwarp();
+            keep = 0u;
+        }
+    }
+    cp_async_wait_all();   // a last copy may still be in flight
+    __syncwarp();
 }
 
 }  // namespace hy

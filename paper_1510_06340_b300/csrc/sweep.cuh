@@ -1,6 +1,8 @@
 // sweep.cuh -- the directional sweep kernel (all RK stages of one sweep of
 // Sec. 2.3 over every pencil along one axis, for any number of events).
 #pragma once
+#include <atomic>
+
 #include "device.cuh"
 #include "kernels.h"
 
@@ -88,7 +90,29 @@ k_sweep(const R *__restrict__ in, R *__restrict__ out, const EventGeo *__restric
             ra.ih_t1 = g.n[at1] > 1 ? R(g.inv_h[at1]) : R(0);
             ra.ih_t2 = g.n[at2] > 1 ? R(g.inv_h[at2]) : R(0);
         }
-        march<R, RK, RATE>(ph, Pc, s0, L, s_end, g.bc[axis], lam, valid, ra);
+        if (RK == 2 && axis == 0) {   // rows through the warp's shared-memory rings
+            extern __shared__ __align__(16) unsigned char xs_raw[];
+            R *base = reinterpret_cast<R *>(xs_raw) +
+                      (threadIdx.x >> 5) * xstage_floats_per_warp<R>();
+            XStage<R> X;
+            X.ring = base;
+            X.oring = base + 4 * 32 * XRS;
+            X.in = in + g.off;
+            X.out = out + g.off;
+            X.fo1 = Pc.fo1; X.fo2 = Pc.fo2; X.fo3 = Pc.fo3;
+            X.N = N;
+            X.bc = g.bc[0];
+            X.lane = threadIdx.x & 31;
+            X.rowN = int(pencil) * N;   // < cells < 2^31
+            X.js = s0 - 4;
+            if (lam > R(0)) {
+                march_x_rk2<R, RATE>(ph, X, s0, L, s_end, lam, valid, ra);
+            } else if (valid) {   // finished event: copy through
+                for (int o = s0; o < s_end; ++o) Pc.store(o, Pc.load(o));
+            }
+        } else {
+            march<R, RK, RATE>(ph, Pc, s0, L, s_end, g.bc[axis], lam, valid, ra);
+        }
         if (RATE && rate_clk) {   // block max, one atomic per work item
             R m = ra.m;
 #pragma unroll
@@ -117,18 +141,33 @@ cudaError_t launch_sweep_prec(const SweepLaunch &a) {
 #define HY_SWEEP(EOSK, RK, LIM, COUNT, RATE)                                                 \
     {                                                                                       \
         auto kfn = k_sweep<R, PREC, EOSK, RK, LIM, COUNT, RATE>;                            \
+        const size_t smem = (RK == 2 && a.axis == 0)                                        \
+            ? size_t(a.threads / 32) * xstage_floats_per_warp<R>() * sizeof(R) : 0;          \
+        if (smem > 0) {   /* opt in once per device, for 256 threads */                 \
+            static std::atomic<unsigned long long> opted{0};                                \
+            int dev_ = 0;                                                                   \
+            cudaError_t e_ = cudaGetDevice(&dev_);                                          \
+            if (e_ != cudaSuccess) return e_;                                               \
+            const unsigned long long bit_ = 1ull << (dev_ & 63);                            \
+            if (!(opted.load() & bit_)) {                                                   \
+                e_ = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                          int(8 * xstage_floats_per_warp<R>() * sizeof(R)));\
+                if (e_ != cudaSuccess) return e_;                                           \
+                opted.fetch_or(bit_);                                                       \
+            }                                                                               \
+        }                                                                                   \
         int blocks = a.nitems;                                                              \
         if (a.counter) {                                                                    \
             int occ = 0;                                                                    \
             cudaError_t e_ = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kfn,       \
-                                                                           a.threads, 0);   \
+                                                                           a.threads, smem);\
             if (e_ != cudaSuccess) return e_;                                               \
             blocks = occ * a.sms < a.nitems ? occ * a.sms : a.nitems;                       \
             if (blocks < 1) blocks = 1;                                                     \
             e_ = cudaMemsetAsync(a.counter, 0, sizeof(int), a.stream);                      \
             if (e_ != cudaSuccess) return e_;                                               \
         }                                                                                   \
-        kfn<<<blocks, a.threads, 0, a.stream>>>(in, out, a.ev, a.items, a.nitems, a.axis,    \
+        kfn<<<blocks, a.threads, smem, a.stream>>>(in, out, a.ev, a.items, a.nitems, a.axis, \
                                                 a.frac, a.clk, a.sc, a.counter, a.rate_clk); \
         return cudaGetLastError();                                                          \
     }
