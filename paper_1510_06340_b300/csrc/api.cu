@@ -43,6 +43,20 @@ struct LaunchShape {
     int seg_len = 0;      // target segment length; 0 = whole pencils
 };
 
+// the derived constants, in the arithmetic of R itself
+template <class R>
+static void set_consts(SchemeConsts<R> &k, R alpha, R delta, R cs2) {
+    k.alpha = alpha;
+    k.delta = delta;
+    k.omd = R(1) - delta;
+    k.capf = k.omd * k.omd;
+    k.cs2 = cs2;
+    k.cs = std::sqrt(cs2);
+    k.k1 = R(1) - cs2;
+    k.hapc = R(0.5) * (R(1) + cs2);
+    k.hapc2 = k.hapc * k.hapc;
+}
+
 struct Solver {
     int nevents = 0;
     int prec = HYDRO_FP64;
@@ -217,6 +231,8 @@ struct Solver {
         sc.cs2 = eos->cs2;
         sc.seed = eos->seed;
         sc.tol = eos->newton_tol > 0.0 ? eos->newton_tol : (prec == HYDRO_FP64 ? 1e-13 : 2e-6);
+        set_consts(sc.c64, sc.alpha, DELTA_F64, sc.cs2);
+        set_consts(sc.c32, float(sc.alpha), float(DELTA_F32), float(sc.cs2));
         if (eos->kind == HYDRO_EOS_CONFORMAL) {
             if (!(eos->cs2 >= 0.0 && eos->cs2 < 1.0)) return fail(HYDRO_E_INVALID, "cs2 must be in [0,1)");
         } else if (eos->kind == HYDRO_EOS_TABLE) {
@@ -309,7 +325,10 @@ struct Solver {
             int S = 1;
             if (s.seg_len > 0 && N > s.seg_len) S = (N + s.seg_len / 2) / s.seg_len;
             S = std::max(1, S);
-            const int L = (N + S - 1) / S;
+            int L = (N + S - 1) / S;
+            // x rows are staged 8 cells at a time: 8-aligned segment starts
+            // keep every copy on whole 32-byte sectors
+            if (axis == 0 && S > 1) L = std::min(N, (L + 7) / 8 * 8);
             S = (N + L - 1) / L;
             g.seg[axis] = S;
             g.segL[axis] = L;

@@ -65,6 +65,21 @@ struct WorkItem {
 };
 
 // Scheme constants of one launch (uniform over its threads).
+// Per-run constants of the scheme in one precision, derived once on the host
+// so that the sweeps read them as kernel-parameter operands
+template <class R>
+struct SchemeConsts {
+    R alpha;   // FORCE coefficient
+    R delta;   // admissibility margin (R9)
+    R omd;     // 1 - delta
+    R capf;    // (1 - delta)^2
+    R cs2;     // conformal c^2
+    R cs;      // c
+    R k1;      // 1 - c^2
+    R hapc;    // (1 + c^2) / 2
+    R hapc2;   // ((1 + c^2) / 2)^2
+};
+
 struct Scheme {
     int limiter, stages, hancock;
     double alpha;
@@ -80,6 +95,8 @@ struct Scheme {
     const void *mlp_w;            // bf16 W1 [32][2], W2 [32][32], W3 [32]
     const float *mlp_f;           // fp32 copy of the full parameter vector
     unsigned long long *counters; // [NCOUNTERS] or null
+    SchemeConsts<double> c64;     // FP64 values, delta of FP64
+    SchemeConsts<float> c32;      // FP32 values computed in FP32, delta of FP32
 };
 
 }  // namespace hy

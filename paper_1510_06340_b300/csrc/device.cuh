@@ -57,8 +57,14 @@ __device__ __forceinline__ V4<R> vmul(R s, const V4<R> &x) {
 // ---------------------------------------------------------------- math helpers
 __device__ __forceinline__ double dsqrt_(double x) { return sqrt(x); }
 __device__ __forceinline__ float dsqrt_(float x) { return sqrtf(x); }
+// 1/x: exact in FP64; in FP32 the hardware approximation (rcp.approx, within
+// about one ulp), the accuracy class of the FP32 sweep's fast division
 __device__ __forceinline__ double rcp_(double x) { return 1.0 / x; }
-__device__ __forceinline__ float rcp_(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ float rcp_(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
 __device__ __forceinline__ double fmax_(double a, double b) { return fmax(a, b); }
 __device__ __forceinline__ float fmax_(float a, float b) { return fmaxf(a, b); }
 __device__ __forceinline__ double fmin_(double a, double b) { return fmin(a, b); }
@@ -117,41 +123,59 @@ __device__ __forceinline__ void count(const Scheme &s, int which, unsigned long 
     if (s.counters) atomicAdd(s.counters + which, v);
 }
 
+// the scheme's constants in precision R
+template <class R>
+__device__ __forceinline__ const SchemeConsts<R> &consts(const Scheme &s);
+template <>
+__device__ __forceinline__ const SchemeConsts<double> &consts<double>(const Scheme &s) {
+    return s.c64;
+}
+template <>
+__device__ __forceinline__ const SchemeConsts<float> &consts<float>(const Scheme &s) {
+    return s.c32;
+}
+
 // ---------------------------------------------------------------- cons -> prim
 // What a flux evaluation needs from Eq. 23: velocity along the sweep axis and p.
 template <class R>
 struct Prim {
     R vn, p;
     R W;     // E + p
+    R fe;    // energy flux (E + p) v_n
 };
 
 // Conformal EOS p = cs2 e (reading R10): W = E + p is the positive root of
 // W^2 - (1+cs2) E W + cs2 M^2 = 0; |M| is capped at (1 - delta) E (R9).
 template <class R>
-__device__ __forceinline__ Prim<R> c2p_conformal(const V4<R> &U, R cs2, R delta, R &M2out,
-                                                 R &Wout, const Scheme &sc, bool counting) {
+__device__ __forceinline__ Prim<R> c2p_conformal(const V4<R> &U, const SchemeConsts<R> &k,
+                                                 R &M2out, R &Wout, const Scheme &sc,
+                                                 bool counting) {
     Prim<R> q;
-    const R E = U.e;
+    // E <= 0 is vacuum (v = p = 0): with E clamped to 0 the cap forces M2c = 0,
+    // so W = p = 0 follow from the same formulas and only 1/W needs a guard
+    const R E = fmax_(U.e, R(0));
     const R M2 = fma_(U.t2, U.t2, fma_(U.t1, U.t1, U.n * U.n));
     const R E2 = E * E;
-    const R capf = (R(1) - delta) * (R(1) - delta);
-    const R cap2 = capf * E2;
+    const R cap2 = k.capf * E2;
     const R M2c = fmin_(M2, cap2);
-    const R hapc = R(0.5) * (R(1) + cs2);
     // W^2 - (1+c2) E W + c2 M^2 = 0: W = (1+c2)/2 E + sqrt(((1+c2)/2)^2 E^2 - c2 M^2),
     // the discriminant being positive for |M| < E
-    const R W = fma_(hapc, E, dsqrt_(fma_(-cs2, M2c, (hapc * hapc) * E2)));
-    R s = R(1);
-    if (M2 > cap2) {      // |M| capped at (1 - delta) E (R9)
-        s = dsqrt_(cap2 / M2);
+    const R W = fma_(k.hapc, E, dsqrt_(fma_(-k.cs2, M2c, k.hapc2 * E2)));
+    R inv = W > R(0) ? rcp_(W) : R(0);
+    // energy flux (E + p) v_n = W (s M_n / W) = s M_n
+    R fe = U.n;
+    if (M2 > cap2) {      // |M| capped at (1 - delta) E (R9): v = s M / W
+        const R s = dsqrt_(cap2 / M2);
+        inv *= s;
+        fe *= s;
         if (counting) count(sc, CNT_CAPPED);
     }
-    const bool ok = E > R(0);   // E <= 0: vacuum, v = p = 0
-    q.vn = ok ? (s * U.n) / W : R(0);
-    q.p = ok ? W - E : R(0);
-    q.W = ok ? W : R(0);
-    M2out = ok ? M2c : R(0);
-    Wout = q.W;
+    q.vn = U.n * inv;
+    q.fe = fe;
+    q.p = W - E;
+    q.W = W;
+    M2out = M2c;
+    Wout = W;
     return q;
 }
 
@@ -275,7 +299,7 @@ __device__ __forceinline__ Prim<R> c2p_table(const V4<R> &U, R delta, const Sche
         given = R(mlp_seed_warp(sc, __logf(Ef), xf));
         seed = SEED_GIVEN;
     }
-    if (!(E > R(0))) { q.vn = R(0); q.p = R(0); q.W = R(0); vmag = R(0); return q; }
+    if (!(E > R(0))) { q.vn = R(0); q.p = R(0); q.W = R(0); q.fe = R(0); vmag = R(0); return q; }
     const R cap = (R(1) - delta) * E;
     if (M2 > cap * cap) {
         M2 = cap * cap;
@@ -290,6 +314,7 @@ __device__ __forceinline__ Prim<R> c2p_table(const V4<R> &U, R delta, const Sche
     q.vn = Mfull > R(0) ? U.n * (v / Mfull) : R(0);
     q.p = p;
     q.W = E + p;
+    q.fe = q.W * q.vn;
     return q;
 }
 
@@ -299,30 +324,39 @@ enum { PREC_F64 = 0, PREC_F32 = 1, PREC_MIXED = 2 };
 template <class R, int PREC, int EOSK, int LIM = -1, bool COUNT = true>
 struct Physics {
     Scheme sc;
-    R cs2, delta;
+    R al_, hclf_;   // alpha dt/dx and 1 / (4 alpha dt/dx) of the current sweep
+
+    __device__ __forceinline__ const SchemeConsts<R> &K() const { return consts<R>(sc); }
+
+    // per-event constants of a sweep with lam = dt / dx
+    __device__ __forceinline__ void set_lam(R lam) {
+        al_ = K().alpha * lam;
+        hclf_ = R(0.25) / al_;
+    }
 
     // cons -> prim for a flux evaluation (Eq. 23)
     __device__ __forceinline__ Prim<R> prim(const V4<R> &U) const {
         if (EOSK == EOS_CONFORMAL) {
             R M2, W;
-            Prim<R> q = c2p_conformal<R>(U, cs2, delta, M2, W, sc, COUNT);
+            Prim<R> q = c2p_conformal<R>(U, K(), M2, W, sc, COUNT);
             if (PREC == PREC_MIXED) {
                 // |v|^2 = M2 / W^2 > 0.99^2: redo in double (cancellation in W - E)
                 if (M2 > R(0.9801) * W * W) {
                     V4<double> D = v4<double>(U.e, U.n, U.t1, U.t2);
                     double M2d, Wd;
                     Prim<double> qd =
-                        c2p_conformal<double>(D, double(cs2), DELTA_F64, M2d, Wd, sc, COUNT);
+                        c2p_conformal<double>(D, sc.c64, M2d, Wd, sc, COUNT);
                     q.vn = R(qd.vn);
                     q.p = R(qd.p);
                     q.W = R(qd.W);
+                    q.fe = R(qd.fe);
                     if (COUNT) count(sc, CNT_F64_REDO);
                 }
             }
             return q;
         } else {
             R vmag;
-            Prim<R> q = c2p_table<R>(U, delta, sc, sc.seed, R(0), vmag);
+            Prim<R> q = c2p_table<R>(U, K().delta, sc, sc.seed, R(0), vmag);
             if (PREC == PREC_MIXED) {
                 if (vmag > R(0.99)) {   // redo in double, seeded by the float root
                     V4<double> D = v4<double>(U.e, U.n, U.t1, U.t2);
@@ -332,6 +366,7 @@ struct Physics {
                     q.vn = R(qd.vn);
                     q.p = R(qd.p);
                     q.W = R(qd.W);
+                    q.fe = R(qd.fe);
                     count(sc, CNT_F64_REDO);
                 }
             }
@@ -342,17 +377,43 @@ struct Physics {
     // Eq. 3 along the sweep axis
     __device__ __forceinline__ V4<R> flux(const V4<R> &U) const {
         const Prim<R> q = prim(U);
-        // Eq. 3 along the axis: ((E + p) v_n, M_n v_n + p, M_t1 v_n, M_t2 v_n), W = E + p
-        return v4<R>(q.W * q.vn, fma_(U.n, q.vn, q.p), U.t1 * q.vn, U.t2 * q.vn);
+        // Eq. 3 along the axis: ((E + p) v_n, M_n v_n + p, M_t1 v_n, M_t2 v_n)
+        return v4<R>(q.fe, fma_(U.n, q.vn, q.p), U.t1 * q.vn, U.t2 * q.vn);
     }
 
     // CFL rate of one cell (reading R8): max over swept axes of |lambda^+-| / dx,
-    // axes given in the sweep's slot order (n, t1, t2) with ih = 1/dx (0: not swept)
-    __device__ __forceinline__ R rate(const V4<R> &U, R ih_n, R ih_t1, R ih_t2) const {
+    // axes given in the sweep's slot order (n, t1, t2) with ih = 1/dx (0: not swept);
+    // iso: every swept axis has spacing 1 / ih_n
+    __device__ __forceinline__ R rate(const V4<R> &U, R ih_n, R ih_t1, R ih_t2, bool iso) const {
+        if (EOSK == EOS_CONFORMAL && iso) {
+            // At fixed |v| the speed grows with |v_d| (its derivative in |v_d| has
+            // the sign of 1 - v_d^2), so the axis of largest |v_d| gives the max;
+            // with k = c2 and D = 1 - |v|^2 k:
+            //   lambda = (|v_d| (1 - k) + c sqrt((1 - |v|^2) (D - v_d^2 (1 - k)))) / D
+            const R E = fmax_(U.e, R(0));
+            const R M2 = fma_(U.t2, U.t2, fma_(U.t1, U.t1, U.n * U.n));
+            const SchemeConsts<R> &k = K();
+            const R E2 = E * E;
+            const R cap2 = k.capf * E2;
+            const R M2c = fmin_(M2, cap2);
+            const R W = fma_(k.hapc, E, dsqrt_(fma_(-k.cs2, M2c, k.hapc2 * E2)));
+            const R inv = W > R(0) ? rcp_(W) : R(0);
+            R am = fabs_(U.n);
+            if (ih_t1 > R(0)) am = fmax_(am, fabs_(U.t1));
+            if (ih_t2 > R(0)) am = fmax_(am, fabs_(U.t2));
+            R a = am * inv;                       // largest |v_d|
+            if (M2 > cap2) a *= dsqrt_(cap2 / M2);   // capped |M| (R9)
+            const R v2 = (M2c * inv) * inv;
+            const R D = fma_(-v2, k.cs2, R(1));
+            const R rad = fmax_((R(1) - v2) * fma_(-a * a, k.k1, D), R(0));
+            const R lam = fma_(k.cs, dsqrt_(rad), a * k.k1) * rcp_(D);
+            return U.e > R(0) ? lam * ih_n : R(0);
+        }
         const R E = U.e;
+        const R cs2 = K().cs2;
         R M2 = U.n * U.n + U.t1 * U.t1 + U.t2 * U.t2;
         if (!(E > R(0))) return R(0);
-        const R cap2 = (R(1) - delta) * (R(1) - delta) * E * E;
+        const R cap2 = K().capf * E * E;
         R s = R(1);
         if (M2 > cap2) {
             s = dsqrt_(cap2 / M2);
@@ -367,7 +428,7 @@ struct Physics {
             c2 = cs2;
         } else {
             R vmag;
-            const Prim<R> q = c2p_table<R>(U, delta, sc, sc.seed, R(0), vmag);
+            const Prim<R> q = c2p_table<R>(U, K().delta, sc, sc.seed, R(0), vmag);
             const R Mfull = dsqrt_(U.n * U.n + U.t1 * U.t1 + U.t2 * U.t2);
             const R sc_ = Mfull > R(0) ? vmag / Mfull : R(0);
             vn = U.n * sc_; vt1 = U.t1 * sc_; vt2 = U.t2 * sc_;
@@ -383,6 +444,14 @@ struct Physics {
             rad = rad < R(0) ? R(0) : rad;
             return (fabs_(vd * (R(1) - c2)) + cs * dsqrt_(rad)) * inv_den * ih;
         };
+        if (iso) {
+            // at fixed |v| the speed grows with |v_d| (its derivative in |v_d|
+            // has the sign of 1 - v_d^2), so the axis of largest |v_d| gives the max
+            R a = fabs_(vn);
+            if (ih_t1 > R(0)) a = fmax_(a, fabs_(vt1));
+            if (ih_t2 > R(0)) a = fmax_(a, fabs_(vt2));
+            return one(a, ih_n);
+        }
         R m = one(vn, ih_n);
         if (ih_t1 > R(0)) m = fmax_(m, one(vt1, ih_t1));
         if (ih_t2 > R(0)) m = fmax_(m, one(vt2, ih_t2));
@@ -391,7 +460,7 @@ struct Physics {
 
     __device__ __forceinline__ bool admissible(const V4<R> &U) const {
         const R M2 = fma_(U.t2, U.t2, fma_(U.t1, U.t1, U.n * U.n));
-        const R cap = (R(1) - delta) * U.e;
+        const R cap = K().omd * U.e;
         return U.e > R(0) && M2 < cap * cap;
     }
 
@@ -422,19 +491,25 @@ struct Physics {
 
     // MUSTA-FORCE interface flux (Sec. 2.4 steps 1-5, Eq. 8-11; R1, R2, R4)
     __device__ __forceinline__ V4<R> musta(V4<R> UL, V4<R> UR, R lam) const {
-        const R al = R(sc.alpha) * lam;
+        const R al = al_;
         const R clw = R(0.5) * al;
-        const R clf = R(0.5) / al;
-        const R half = R(0.5), q4 = R(0.25), hclf = R(0.5) * clf;
+        const R half = R(0.5), q4 = R(0.25), hclf = hclf_;
         V4<R> Fc;
         const int k = sc.stages;
 #pragma unroll 1
         for (int l = 0; l < k; ++l) {
             const V4<R> FL = flux(UL), FR = flux(UR);
-            const V4<R> Ulw = vfma<R>(-clw, vsub(FR, FL), vmul<R>(half, vadd(UL, UR)));
-            const V4<R> Flw = flux(Ulw);
             // F = 1/2 F_lw + 1/2 F_lf = 1/2 F_lw + 1/4 (F_L + F_R) - (clf/2) (U_R - U_L)
-            Fc = vfma<R>(half, Flw, vfma<R>(-hclf, vsub(UR, UL), vmul<R>(q4, vadd(FL, FR))));
+            const V4<R> Flf = vfma<R>(-hclf, vsub(UR, UL), vmul<R>(q4, vadd(FL, FR)));
+            if (EOSK == EOS_CONFORMAL) {
+                // p = c2 e makes the flux homogeneous of degree 1, F(2U) = 2 F(U),
+                // and doubling is exact: take F(2 U_lw) / 4 for F_lw / 2
+                const V4<R> Ulw2 = vfma<R>(-al, vsub(FR, FL), vadd(UL, UR));
+                Fc = vfma<R>(q4, flux(Ulw2), Flf);
+            } else {
+                const V4<R> Ulw = vfma<R>(-clw, vsub(FR, FL), vmul<R>(half, vadd(UL, UR)));
+                Fc = vfma<R>(half, flux(Ulw), Flf);
+            }
             if (l < k - 1) {
                 UL = vfma<R>(-lam, vsub(Fc, FL), UL);
                 UR = vfma<R>(-lam, vsub(FR, Fc), UR);
@@ -557,6 +632,7 @@ template <class R>
 struct RateAcc {
     R ih_n, ih_t1, ih_t2;
     R m;
+    bool iso;   // the swept axes share one spacing
 };
 
 template <class R, int RK, bool RATE, class PH>
@@ -612,9 +688,9 @@ __device__ __forceinline__ void march(const PH &ph, const Pencil<R> &P, int s0, 
             // Eq. 6: U^{n+1} = 1/2 (U + U1 + dt L(U1))
             const V4<R> r = vmul<R>(half, vfma<R>(-lam, Dl, vadd(U0, c)));
             const bool keep = do_store && o >= s0 && o < s_end;
-            if (rate_on) {
-                const R rr = ph.rate(r, ra.ih_n, ra.ih_t1, ra.ih_t2);
-                if (keep) ra.m = (rr > ra.m || rr != rr) ? rr : ra.m;
+            if (rate_on && keep) {
+                const R rr = ph.rate(r, ra.ih_n, ra.ih_t1, ra.ih_t2, ra.iso);
+                ra.m = (rr > ra.m || rr != rr) ? rr : ra.m;
             }
             if (keep) P.store(o, r);
         }
@@ -630,7 +706,7 @@ __device__ __forceinline__ void march(const PH &ph, const Pencil<R> &P, int s0, 
         V4<R> X = vfma<R>(-lam, D, cell);   // U1 = U + dt L(U)
         if (RK == 1) {
             if (rate_on) {
-                const R rr = ph.rate(X, ra.ih_n, ra.ih_t1, ra.ih_t2);
+                const R rr = ph.rate(X, ra.ih_n, ra.ih_t1, ra.ih_t2, ra.iso);
                 if (do_store && i < s_end) ra.m = (rr > ra.m || rr != rr) ? rr : ra.m;
             }
             if (do_store && i < s_end) P.store(i, X);
@@ -649,7 +725,7 @@ __device__ __forceinline__ void march(const PH &ph, const Pencil<R> &P, int s0, 
             // Eq. 6: U^{n+1} = 1/2 (U + U1 + dt L(U1))
             const V4<R> r = vmul<R>(half, vfma<R>(-lam, Dl, vadd(U0, c)));
             if (rate_on) {
-                const R rr = ph.rate(r, ra.ih_n, ra.ih_t1, ra.ih_t2);
+                const R rr = ph.rate(r, ra.ih_n, ra.ih_t1, ra.ih_t2, ra.iso);
                 if (do_store && o < s_end) ra.m = (rr > ra.m || rr != rr) ? rr : ra.m;
             }
             if (do_store && o < s_end) P.store(o, r);
@@ -677,7 +753,7 @@ __device__ __forceinline__ void march(const PH &ph, const Pencil<R> &P, int s0, 
             // U^{n+1} = 1/3 U + 2/3 (U2 + dt L(U2))
             const V4<R> r = vfma<R>(third, U00, vmul<R>(two3, vfma<R>(-lam, D3, c3)));
             if (rate_on) {
-                const R rr = ph.rate(r, ra.ih_n, ra.ih_t1, ra.ih_t2);
+                const R rr = ph.rate(r, ra.ih_n, ra.ih_t1, ra.ih_t2, ra.iso);
                 if (do_store && o < s_end) ra.m = (rr > ra.m || rr != rr) ? rr : ra.m;
             }
             if (do_store && o < s_end) P.store(o, r);
@@ -760,8 +836,11 @@ struct XStage {
         q[0] = v.e; q[32 * XOS] = v.n; q[2 * 32 * XOS] = v.t1; q[3 * 32 * XOS] = v.t2;
     }
     // write the results of steps t1 - 7 .. t1 (position js + step - 6) whose
-    // keep bits (bit step & 7, per row) are set
-    __device__ __forceinline__ void flush(int t1, unsigned keep) {
+    // keep bits (bit step & 7, per row) are set; with RATE also fold their CFL
+    // rates into ra (8 independent evaluations per lane)
+    template <bool RATE, class PH>
+    __device__ __forceinline__ void flush(int t1, unsigned keep, const PH &ph, RateAcc<R> &ra,
+                                          bool rate_on) {
         const int c = lane & 7;
         const int st = t1 - 7 + c;
 #pragma unroll
@@ -773,10 +852,15 @@ struct XStage {
             if ((kr >> (st & 7)) & 1u) {
                 R *p = out + rn + (jr + st - 6);
                 const R *q = oring + r * XOS + (st & (XO - 1));
-                p[0] = q[0];
-                p[fo1] = q[32 * XOS];
-                p[fo2] = q[2 * 32 * XOS];
-                p[fo3] = q[3 * 32 * XOS];
+                const V4<R> v = v4<R>(q[0], q[32 * XOS], q[2 * 32 * XOS], q[3 * 32 * XOS]);
+                p[0] = v.e;
+                p[fo1] = v.n;
+                p[fo2] = v.t1;
+                p[fo3] = v.t2;
+                if (RATE && rate_on) {
+                    const R rr = ph.rate(v, ra.ih_n, ra.ih_t1, ra.ih_t2, ra.iso);
+                    ra.m = (rr > ra.m || rr != rr) ? rr : ra.m;
+                }
             }
         }
     }
@@ -834,15 +918,11 @@ __device__ __forceinline__ void march_x_rk2(const PH &ph, XStage<R> &X, int s0, 
         const V4<R> U0 = X.get(t - 6);
         const V4<R> r = vmul<R>(half, vfma<R>(-lam, Dl, vadd(U0, c)));
         const bool kp = do_store && o >= s0 && o < s_end;
-        if (rate_on) {
-            const R rr = ph.rate(r, ra.ih_n, ra.ih_t1, ra.ih_t2);
-            if (kp) ra.m = (rr > ra.m || rr != rr) ? rr : ra.m;
-        }
         X.put(t, r);
         keep |= (kp ? 1u : 0u) << (t & 7);
         if (((t - psi) & 7) == 0 || t == T - 1) {
             __syncwarp();
-            X.flush(t, keep);
+            X.flush<RATE>(t, keep, ph, ra, rate_on);
             __syncwarp();
             keep = 0u;
         }

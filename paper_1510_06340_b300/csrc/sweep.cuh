@@ -28,8 +28,6 @@ k_sweep(const R *__restrict__ in, R *__restrict__ out, const EventGeo *__restric
         const EventClock *__restrict__ clk, Scheme sc, int *counter, EventClock *rate_clk) {
     Physics<R, PREC, EOSK, LIM, COUNT> ph;
     ph.sc = sc;
-    ph.cs2 = R(sc.cs2);
-    ph.delta = R(sc.delta);
     __shared__ int s_item;
     __shared__ R s_red[8];
     for (int k = 0;; ++k) {
@@ -79,16 +77,20 @@ k_sweep(const R *__restrict__ in, R *__restrict__ out, const EventGeo *__restric
         Pc.stride = int(stride);
         Pc.N = N;
         const R lam = R(frac * clk[w.event].dt / g.h[axis]);
+        ph.set_lam(lam);
         const int s0 = seg * L;
         const int s_end = min(s0 + L, N);
         RateAcc<R> ra;
         ra.m = R(0);
         ra.ih_n = ra.ih_t1 = ra.ih_t2 = R(0);
+        ra.iso = false;
         if (RATE && rate_clk) {   // last sweep of a step: CFL rate of the new state
             const int at1 = axis == 0 ? 1 : 0, at2 = axis == 2 ? 1 : 2;
             ra.ih_n = R(g.inv_h[axis]);
             ra.ih_t1 = g.n[at1] > 1 ? R(g.inv_h[at1]) : R(0);
             ra.ih_t2 = g.n[at2] > 1 ? R(g.inv_h[at2]) : R(0);
+            ra.iso = (ra.ih_t1 == R(0) || ra.ih_t1 == ra.ih_n) &&
+                     (ra.ih_t2 == R(0) || ra.ih_t2 == ra.ih_n);
         }
         if (RK == 2 && axis == 0) {   // rows through the warp's shared-memory rings
             extern __shared__ __align__(16) unsigned char xs_raw[];
