@@ -669,12 +669,22 @@ __device__ __forceinline__ void march(const PH &ph, const Pencil<R> &P, int s0, 
         qa[0] = qa[1] = qa[2] = zero;
         int jn = wrap_index(js + 1, N, bc);
         int jc = js + 1;
+        // the cell reloaded for the RK combination, one step ahead like the input
+        int on = wrap_index(s0 - 9, N, bc);
+        int oc = s0 - 9;
+        V4<R> U0n = P.load(wrap_index(s0 - 10, N, bc));
 #pragma unroll 1
         for (int t = 0; t < T; ++t) {
             const V4<R> V = nxt;
-            if (t + 1 < T) nxt = P.load(jn);
+            const V4<R> U0 = U0n;
+            if (t + 1 < T) {
+                nxt = P.load(jn);
+                U0n = P.load(on);
+            }
             ++jc;
             jn = (bc == BC_OUTFLOW) ? min(max(jc, 0), N - 1) : (jn + 1 == N ? 0 : jn + 1);
+            ++oc;
+            on = (bc == BC_OUTFLOW) ? min(max(oc, 0), N - 1) : (on + 1 == N ? 0 : on + 1);
             st1.push_full(V, ph, lam, cell, D);
             const int i = js + t - 2;                 // stage-1 output cell
             const V4<R> X = vfma<R>(-lam, D, cell);   // U1 = U + dt L(U)
@@ -684,7 +694,6 @@ __device__ __forceinline__ void march(const PH &ph, const Pencil<R> &P, int s0, 
             V4<R> c, Dl;
             st2.push_full(Y, ph, lam, c, Dl);
             const int o = t + s0 - 10;                // finished cell
-            const V4<R> U0 = P.load(wrap_index(o, N, bc));
             // Eq. 6: U^{n+1} = 1/2 (U + U1 + dt L(U1))
             const V4<R> r = vmul<R>(half, vfma<R>(-lam, Dl, vadd(U0, c)));
             const bool keep = do_store && o >= s0 && o < s_end;
@@ -809,10 +818,31 @@ struct XStage {
     int N, bc, lane;
     int js;             // this lane's position at step 0
     int rowN;           // this lane's row start: row (pencil) index * N
+    // uni: the warp's rows are consecutive (row start rowN0 + lane N), all
+    // stored, with one segment (start js0), so addresses and keep bits are
+    // the same arithmetic on every lane and need no exchange
+    bool uni;
+    int js0, rowN0;
 
     // start copying steps t0 .. t0 + 7 of all 32 rows into the ring
     __device__ __forceinline__ void fill(int t0) {
         const int c = lane & 7;
+        if (uni) {
+            const R *p0 = in + rowN0 + wrap_index(js0 + t0 + c, N, bc);
+            R *q0 = ring + ((t0 + c) & (XR - 1));
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int r = (lane >> 3) + 4 * k;
+                const R *p = p0 + r * N;
+                R *q = q0 + r * XRS;
+                cp_async_elem(q, p);
+                cp_async_elem(q + 32 * XRS, p + fo1);
+                cp_async_elem(q + 2 * 32 * XRS, p + fo2);
+                cp_async_elem(q + 3 * 32 * XRS, p + fo3);
+            }
+            cp_async_commit();
+            return;
+        }
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
             const int r = (lane >> 3) + 4 * k;
@@ -843,6 +873,29 @@ struct XStage {
                                           bool rate_on) {
         const int c = lane & 7;
         const int st = t1 - 7 + c;
+        if (uni) {
+            if ((keep >> (st & 7)) & 1u) {
+                R *p0 = out + rowN0 + (js0 + st - 6);
+                const R *q0 = oring + (st & (XO - 1));
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const int r = (lane >> 3) + 4 * k;
+                    R *p = p0 + r * N;
+                    const R *q = q0 + r * XOS;
+                    const V4<R> v =
+                        v4<R>(q[0], q[32 * XOS], q[2 * 32 * XOS], q[3 * 32 * XOS]);
+                    p[0] = v.e;
+                    p[fo1] = v.n;
+                    p[fo2] = v.t1;
+                    p[fo3] = v.t2;
+                    if (RATE && rate_on) {
+                        const R rr = ph.rate(v, ra.ih_n, ra.ih_t1, ra.ih_t2, ra.iso);
+                        ra.m = (rr > ra.m || rr != rr) ? rr : ra.m;
+                    }
+                }
+            }
+            return;
+        }
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
             const int r = (lane >> 3) + 4 * k;
@@ -881,6 +934,9 @@ __device__ __forceinline__ void march_x_rk2(const PH &ph, XStage<R> &X, int s0, 
     // fills at steps t = phi (mod 8), t >= 1, each for steps t + 2 .. t + 9,
     // so that lane 0's row moves 8-aligned cells; flushes at t = psi (mod 8)
     const int js0 = __shfl_sync(0xffffffffu, js, 0);
+    X.js0 = js0;
+    X.rowN0 = __shfl_sync(0xffffffffu, X.rowN, 0);
+    X.uni = __all_sync(0xffffffffu, do_store && js == js0 && X.rowN == X.rowN0 + X.lane * N);
     const int phi = (6 - js0) & 7;
     const int psi = (13 - js0) & 7;
     const int tf = phi == 0 ? 8 : phi;   // first fill step

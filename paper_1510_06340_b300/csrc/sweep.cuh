@@ -21,7 +21,8 @@ namespace hy {
 #define HY_SWEEP_BOUNDS __launch_bounds__(256)
 #endif
 
-template <class R, int PREC, int EOSK, int RK, int LIM, bool COUNT, bool RATE>
+// XS: RK2 x sweep through the shared-memory row rings (march_x_rk2)
+template <class R, int PREC, int EOSK, int RK, int LIM, bool COUNT, bool RATE, bool XS>
 __global__ void HY_SWEEP_BOUNDS
 k_sweep(const R *__restrict__ in, R *__restrict__ out, const EventGeo *__restrict__ ev,
         const WorkItem *__restrict__ items, int nitems, int axis, double frac,
@@ -92,7 +93,7 @@ k_sweep(const R *__restrict__ in, R *__restrict__ out, const EventGeo *__restric
             ra.iso = (ra.ih_t1 == R(0) || ra.ih_t1 == ra.ih_n) &&
                      (ra.ih_t2 == R(0) || ra.ih_t2 == ra.ih_n);
         }
-        if (RK == 2 && axis == 0) {   // rows through the warp's shared-memory rings
+        if (XS) {   // rows through the warp's shared-memory rings
             extern __shared__ __align__(16) unsigned char xs_raw[];
             R *base = reinterpret_cast<R *>(xs_raw) +
                       (threadIdx.x >> 5) * xstage_floats_per_warp<R>();
@@ -142,8 +143,13 @@ cudaError_t launch_sweep_prec(const SweepLaunch &a) {
     R *out = static_cast<R *>(a.out);
 #define HY_SWEEP(EOSK, RK, LIM, COUNT, RATE)                                                 \
     {                                                                                       \
-        auto kfn = k_sweep<R, PREC, EOSK, RK, LIM, COUNT, RATE>;                            \
-        const size_t smem = (RK == 2 && a.axis == 0)                                        \
+        if (RK == 2 && a.axis == 0) HY_SWEEP_XS(EOSK, RK, LIM, COUNT, RATE, RK == 2)         \
+        else HY_SWEEP_XS(EOSK, RK, LIM, COUNT, RATE, false)                                 \
+    }
+#define HY_SWEEP_XS(EOSK, RK, LIM, COUNT, RATE, XS)                                          \
+    {                                                                                       \
+        auto kfn = k_sweep<R, PREC, EOSK, RK, LIM, COUNT, RATE, XS>;                        \
+        const size_t smem = XS                                                              \
             ? size_t(a.threads / 32) * xstage_floats_per_warp<R>() * sizeof(R) : 0;          \
         if (smem > 0) {   /* opt in once per device, for 256 threads */                 \
             static std::atomic<unsigned long long> opted{0};                                \
@@ -205,6 +211,7 @@ cudaError_t launch_sweep_prec(const SweepLaunch &a) {
         if (a.rk == 3) HY_SWEEP(EOS_TABLE, 3, -1, true, true)
     }
 #undef HY_SWEEP
+#undef HY_SWEEP_XS
     return cudaErrorInvalidValue;
 }
 
