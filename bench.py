@@ -46,9 +46,10 @@ BYTES = {"fp32": 4, "fp64": 8}
 FLOPS_PER_CELL_SWEEP = 800
 # FP32 (non-tensor) peak from unit counts and clock: 148 SMs x 128 FP32 lanes x
 # 2 flop per FMA x 2.032 GHz; FP64 from the B300's nominal 1.25 TFLOP/s.
-# DRAM bytes read + written per sweep launch from the latest ncu capture of the
-# current kernel (see profiles/), None when not captured for this kernel
-SWEEP_TRAFFIC = {}
+# DRAM bytes read + written per sweep launch, mean over the five sweeps of one
+# step, from an ncu capture of the current kernels (profiles/
+# sweep_blast256_fp32_step.md); None where no capture of the current kernels exists
+SWEEP_TRAFFIC = {(256, "fp32"): 597.3e6}
 ALU_PEAK_TFLOPS = {"fp32": 148 * 128 * 2 * 2.032e9 / 1e12, "fp64": 1.25}
 
 
@@ -234,13 +235,14 @@ def run_ours(args):
     e2e_value = None
     if not args.no_e2e:
         pinned = [torch.from_numpy(a).pin_memory() for a in prim]
+        result = [torch.empty(a.shape, dtype=pinned[0].dtype).pin_memory() for a in prim]
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         h.set_primitives(*[p.numpy() for p in pinned])
         for _ in range(args.steps):
             h.step(1)
             h.conservation_sums()
-        h.get_primitives()
+        h.get_primitives(out=result)
         torch.cuda.synchronize()
         e2e_value = world * cells * args.steps / (time.perf_counter() - t0)
     state_bytes = 4 * cells * BYTES[prec]

@@ -274,6 +274,12 @@ struct Solver {
         } else {
             return fail(HYDRO_E_INVALID, "unknown EOS kind");
         }
+        sc.c64.lne_min = sc.lne_min;
+        sc.c64.inv_h = sc.inv_h;
+        sc.c64.e_max = sc.e_max;
+        sc.c32.lne_min = float(sc.lne_min);
+        sc.c32.inv_h = float(sc.inv_h);
+        sc.c32.e_max = float(sc.e_max);
         // device memory
         const size_t bytes = (size_t)4 * total_cells * elem;
         CK(cudaMalloc(&d_state[0], bytes));

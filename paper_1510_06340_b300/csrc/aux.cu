@@ -275,23 +275,46 @@ __global__ void k_sums(const EventGeo *__restrict__ ev, const WorkItem *__restri
     }
 }
 
-// one thread per (event, field): items of an event are consecutive
-__global__ void k_sums_final(const WorkItem *__restrict__ items, int nitems,
-                             const double *__restrict__ partial, const EventGeo *__restrict__ ev,
-                             double *__restrict__ out, int nevents) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= 4 * nevents) return;
-    const int e = i / 4, q = i % 4;
-    // binary search for the first item of event e
-    int lo = 0, hi = nitems;
-    while (lo < hi) {
-        const int mid = (lo + hi) / 2;
-        if (items[mid].event < e) lo = mid + 1; else hi = mid;
+// one block per event (items of an event are consecutive): each thread sums a
+// fixed strided subset of the event's block partials, then a fixed-shape tree
+// adds the threads' sums, so the result does not depend on timing
+constexpr int SUMS_FINAL_THREADS = 256;
+
+__global__ void __launch_bounds__(SUMS_FINAL_THREADS)
+k_sums_final(const WorkItem *__restrict__ items, int nitems, const double *__restrict__ partial,
+             const EventGeo *__restrict__ ev, double *__restrict__ out, int nevents) {
+    __shared__ double red[4][SUMS_FINAL_THREADS];
+    __shared__ int range[2];
+    const int e = blockIdx.x;
+    if (threadIdx.x < 2) {   // first item of event e (t = 0) and of event e + 1 (t = 1)
+        const int key = e + int(threadIdx.x);
+        int lo = 0, hi = nitems;
+        while (lo < hi) {
+            const int mid = (lo + hi) / 2;
+            if (items[mid].event < key) lo = mid + 1; else hi = mid;
+        }
+        range[threadIdx.x] = lo;
     }
-    double s = 0.0;
-    for (int it = lo; it < nitems && items[it].event == e; ++it) s += partial[4LL * it + q];
-    const EventGeo &g = ev[e];
-    out[i] = s * (g.h[0] * g.h[1] * g.h[2]);
+    __syncthreads();
+    double s[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int it = range[0] + int(threadIdx.x); it < range[1]; it += SUMS_FINAL_THREADS) {
+        const double *p = partial + 4LL * it;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) s[q] += p[q];
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) red[q][threadIdx.x] = s[q];
+    __syncthreads();
+    for (int w = SUMS_FINAL_THREADS / 2; w > 0; w >>= 1) {
+        if (int(threadIdx.x) < w)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x < 4) {
+        const EventGeo &g = ev[e];
+        out[4 * e + threadIdx.x] = red[threadIdx.x][0] * (g.h[0] * g.h[1] * g.h[2]);
+    }
 }
 
 // ------------------------------------------------------------------ hot spots
@@ -447,8 +470,7 @@ cudaError_t launch_sums(const CellLaunch &c, const void *U, double *partial) {
 
 cudaError_t launch_sums_final(const WorkItem *items, int nitems, const double *partial,
                               const EventGeo *ev, double *out, int nevents, cudaStream_t s) {
-    k_sums_final<<<(4 * nevents + 127) / 128, 128, 0, s>>>(items, nitems, partial, ev, out,
-                                                           nevents);
+    k_sums_final<<<nevents, SUMS_FINAL_THREADS, 0, s>>>(items, nitems, partial, ev, out, nevents);
     return cudaGetLastError();
 }
 

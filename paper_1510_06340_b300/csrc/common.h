@@ -8,6 +8,10 @@ enum { LIM_NONE = 0, LIM_MINMOD = 1, LIM_MC = 2, LIM_SUPERBEE = 3, LIM_VANLEER =
        LIM_VANALBADA = 5 };
 enum { BC_PERIODIC = 0, BC_OUTFLOW = 1 };
 enum { EOS_CONFORMAL = 0, EOS_TABLE = 1 };
+// kernel specialisation only (never stored in Scheme::eos_kind): the tabulated
+// EOS with the MLP Newton seed, whose warp-wide forward pass needs registers
+// the plain Newton kernels should not carry
+enum { EOS_TABLE_MLP = 2 };
 enum { SEED_ZERO = 0, SEED_CONFORMAL = 1, SEED_MLP = 2 };
 enum { CNT_CAPPED = 0, CNT_FACE_FALLBACK = 1, CNT_NEWTON_CALLS = 2, CNT_NEWTON_ITERS = 3,
        CNT_NEWTON_FAIL = 4, CNT_F64_REDO = 5, NCOUNTERS = 6 };
@@ -78,6 +82,7 @@ struct SchemeConsts {
     R k1;      // 1 - c^2
     R hapc;    // (1 + c^2) / 2
     R hapc2;   // ((1 + c^2) / 2)^2
+    R lne_min, inv_h, e_max;   // tabulated EOS: first node, 1 / node spacing, last e
 };
 
 struct Scheme {

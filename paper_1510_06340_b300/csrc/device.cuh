@@ -179,49 +179,48 @@ __device__ __forceinline__ Prim<R> c2p_conformal(const V4<R> &U, const SchemeCon
     return q;
 }
 
-// Tabulated EOS (reading R11): linear interpolation in ln e.
+// Tabulated EOS (reading R11): linear interpolation in ln e.  The node
+// constants come from the scheme's constants in precision R.
 template <class R>
-__device__ __forceinline__ void eos_table(const Scheme &sc, R e, R &p, R &c2);
-
+__device__ __forceinline__ R log_(R x);
 template <>
-__device__ __forceinline__ void eos_table<double>(const Scheme &sc, double e, double &p,
-                                                  double &c2) {
-    if (!(e > 0.0)) { p = 0.0; c2 = 1.0 / 3.0; return; }
-    const double lne = log(e);
-    if (lne < sc.lne_min) { p = e / 3.0; c2 = 1.0 / 3.0; return; }
-    const double u = (lne - sc.lne_min) * sc.inv_h;
+__device__ __forceinline__ double log_<double>(double x) { return log(x); }
+template <>
+__device__ __forceinline__ float log_<float>(float x) { return __logf(x); }
+
+template <class R>
+__device__ __forceinline__ const R *p_tab(const Scheme &sc);
+template <>
+__device__ __forceinline__ const double *p_tab<double>(const Scheme &sc) { return sc.p_tab64; }
+template <>
+__device__ __forceinline__ const float *p_tab<float>(const Scheme &sc) { return sc.p_tab32; }
+template <class R>
+__device__ __forceinline__ const R *c2_tab(const Scheme &sc);
+template <>
+__device__ __forceinline__ const double *c2_tab<double>(const Scheme &sc) { return sc.c2_tab64; }
+template <>
+__device__ __forceinline__ const float *c2_tab<float>(const Scheme &sc) { return sc.c2_tab32; }
+
+template <class R>
+__device__ __forceinline__ void eos_table(const Scheme &sc, R e, R &p, R &c2) {
+    const SchemeConsts<R> &k = consts<R>(sc);
+    if (!(e > R(0))) { p = R(0); c2 = R(1.0 / 3.0); return; }
+    const R lne = log_<R>(e);
+    if (lne < k.lne_min) { p = e * R(1.0 / 3.0); c2 = R(1.0 / 3.0); return; }
+    const R u = (lne - k.lne_min) * k.inv_h;
     const int n = sc.tab_n;
-    if (u >= double(n - 1)) {
-        p = __ldg(sc.p_tab64 + n - 1) + __ldg(sc.c2_tab64 + n - 1) * (e - sc.e_max);
-        c2 = __ldg(sc.c2_tab64 + n - 1);
+    const R *pt = p_tab<R>(sc), *ct = c2_tab<R>(sc);
+    if (u >= R(n - 1)) {
+        c2 = __ldg(ct + n - 1);
+        p = fma_(c2, e - k.e_max, __ldg(pt + n - 1));
         return;
     }
-    const int i = int(floor(u));
-    const double f = u - double(i);
-    const double p0 = __ldg(sc.p_tab64 + i), p1 = __ldg(sc.p_tab64 + i + 1);
-    const double c0 = __ldg(sc.c2_tab64 + i), c1 = __ldg(sc.c2_tab64 + i + 1);
-    p = fma(f, p1 - p0, p0);
-    c2 = fma(f, c1 - c0, c0);
-}
-
-template <>
-__device__ __forceinline__ void eos_table<float>(const Scheme &sc, float e, float &p, float &c2) {
-    if (!(e > 0.0f)) { p = 0.0f; c2 = 1.0f / 3.0f; return; }
-    const float lne = __logf(e);
-    if (lne < float(sc.lne_min)) { p = e * (1.0f / 3.0f); c2 = 1.0f / 3.0f; return; }
-    const float u = (lne - float(sc.lne_min)) * float(sc.inv_h);
-    const int n = sc.tab_n;
-    if (u >= float(n - 1)) {
-        p = __ldg(sc.p_tab32 + n - 1) + __ldg(sc.c2_tab32 + n - 1) * (e - float(sc.e_max));
-        c2 = __ldg(sc.c2_tab32 + n - 1);
-        return;
-    }
-    const int i = int(floorf(u));
-    const float f = u - float(i);
-    const float p0 = __ldg(sc.p_tab32 + i), p1 = __ldg(sc.p_tab32 + i + 1);
-    const float c0 = __ldg(sc.c2_tab32 + i), c1 = __ldg(sc.c2_tab32 + i + 1);
-    p = fmaf(f, p1 - p0, p0);
-    c2 = fmaf(f, c1 - c0, c0);
+    const int i = int(u);   // u >= 0 here
+    const R f = u - R(i);
+    const R p0 = __ldg(pt + i), p1 = __ldg(pt + i + 1);
+    const R c0 = __ldg(ct + i), c1 = __ldg(ct + i + 1);
+    p = fma_(f, p1 - p0, p0);
+    c2 = fma_(f, c1 - c0, c0);
 }
 
 }  // namespace hy
@@ -232,7 +231,9 @@ namespace hy {
 // Returns |v|; iters receives the iteration count.
 enum { SEED_GIVEN = 100 };   // internal: start from the value passed in
 
-template <class R>
+// RCP: take 1/W and 1/f' as one reciprocal each (the FP32 sweeps) instead of
+// three divisions
+template <class R, bool RCP = false>
 __device__ __forceinline__ R newton_speed(const Scheme &sc, R E, R M, R M2, int seed, R given,
                                           R &p_out, int &iters) {
     R lo = R(0), hi = M / E;
@@ -261,11 +262,12 @@ __device__ __forceinline__ R newton_speed(const Scheme &sc, R E, R M, R M2, int 
         for (it = 1; it <= NEWTON_MAX_IT; ++it) {
             eos_table<R>(sc, E - M * v, p, c2);
             const R W = E + p;
-            const R f = v - M / W;
+            const R iw = RCP ? rcp_(W) : R(1);
+            const R f = RCP ? v - M * iw : v - M / W;
             if (f == R(0)) { conv = true; break; }
             if (f > R(0)) hi = v; else lo = v;
-            const R fp = R(1) - c2 * M2 / (W * W);
-            R vn = v - f / fp;
+            const R fp = RCP ? R(1) - (c2 * M2) * (iw * iw) : R(1) - c2 * M2 / (W * W);
+            R vn = RCP ? v - f * rcp_(fp) : v - f / fp;
             if (!(vn > lo && vn < hi)) vn = R(0.5) * (lo + hi);
             const R dv = vn - v;
             v = vn;
@@ -284,33 +286,35 @@ __device__ __forceinline__ R newton_speed(const Scheme &sc, R E, R M, R M2, int 
     return v;
 }
 
-template <class R>
+// MLP: seed from the warp-wide tensor-core MLP (the whole warp must be
+// converged here); otherwise `seed` is SEED_ZERO, SEED_CONFORMAL or SEED_GIVEN
+template <class R, bool MLP, bool RCP = false>
 __device__ __forceinline__ Prim<R> c2p_table(const V4<R> &U, R delta, const Scheme &sc,
                                              int seed, R given, R &vmag) {
-    // seed == SEED_MLP requires the whole warp to be converged here
     Prim<R> q;
     const R E = U.e;
-    R M2 = U.n * U.n + U.t1 * U.t1 + U.t2 * U.t2;
-    if (seed == SEED_MLP) {
-        // warp-wide tensor-core seed, taken before any lane-dependent branch
+    const R M2f = fma_(U.t2, U.t2, fma_(U.t1, U.t1, U.n * U.n));
+    if (MLP) {
+        // taken before any lane-dependent branch
         const float Ef = E > R(0) ? float(E) : 1.0f;
-        float xf = E > R(0) ? float(dsqrt_(M2) / E) : 0.0f;
+        float xf = E > R(0) ? float(dsqrt_(M2f) / E) : 0.0f;
         xf = fminf(xf, 1.0f - float(delta));
         given = R(mlp_seed_warp(sc, __logf(Ef), xf));
         seed = SEED_GIVEN;
     }
     if (!(E > R(0))) { q.vn = R(0); q.p = R(0); q.W = R(0); q.fe = R(0); vmag = R(0); return q; }
     const R cap = (R(1) - delta) * E;
-    if (M2 > cap * cap) {
+    const R Mfull = dsqrt_(M2f);
+    R M2 = M2f, M = Mfull;
+    if (M2f > cap * cap) {
         M2 = cap * cap;
+        M = cap;
         count(sc, CNT_CAPPED);
     }
-    const R M = dsqrt_(M2);
     R p;
     int it;
-    const R v = newton_speed<R>(sc, E, M, M2, seed, given, p, it);
+    const R v = newton_speed<R, RCP>(sc, E, M, M2, seed, given, p, it);
     vmag = v;
-    const R Mfull = dsqrt_(U.n * U.n + U.t1 * U.t1 + U.t2 * U.t2);
     q.vn = Mfull > R(0) ? U.n * (v / Mfull) : R(0);
     q.p = p;
     q.W = E + p;
@@ -356,12 +360,14 @@ struct Physics {
             return q;
         } else {
             R vmag;
-            Prim<R> q = c2p_table<R>(U, K().delta, sc, sc.seed, R(0), vmag);
+            constexpr bool F32 = sizeof(R) == 4;
+            Prim<R> q = c2p_table<R, EOSK == EOS_TABLE_MLP, F32>(U, K().delta, sc, sc.seed, R(0),
+                                                                 vmag);
             if (PREC == PREC_MIXED) {
                 if (vmag > R(0.99)) {   // redo in double, seeded by the float root
                     V4<double> D = v4<double>(U.e, U.n, U.t1, U.t2);
                     double vd;
-                    Prim<double> qd = c2p_table<double>(D, DELTA_F64, sc, SEED_GIVEN,
+                    Prim<double> qd = c2p_table<double, false>(D, DELTA_F64, sc, SEED_GIVEN,
                                                         double(vmag), vd);
                     q.vn = R(qd.vn);
                     q.p = R(qd.p);
@@ -428,7 +434,9 @@ struct Physics {
             c2 = cs2;
         } else {
             R vmag;
-            const Prim<R> q = c2p_table<R>(U, K().delta, sc, sc.seed, R(0), vmag);
+            // lane-wise: no warp-wide MLP seed here (the rate may run in divergent code)
+            const int seed = sc.seed == SEED_MLP ? SEED_CONFORMAL : sc.seed;
+            const Prim<R> q = c2p_table<R, false>(U, K().delta, sc, seed, R(0), vmag);
             const R Mfull = dsqrt_(U.n * U.n + U.t1 * U.t1 + U.t2 * U.t2);
             const R sc_ = Mfull > R(0) ? vmag / Mfull : R(0);
             vn = U.n * sc_; vt1 = U.t1 * sc_; vt2 = U.t2 * sc_;

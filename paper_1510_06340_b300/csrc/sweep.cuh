@@ -201,10 +201,26 @@ cudaError_t launch_sweep_prec(const SweepLaunch &a) {
             }
         }
     }
+    // tabulated EOS: Minbee RK2 specialised (plain Newton seeds, or the MLP seed)
+    const bool mlp = a.sc.eos_kind == EOS_TABLE && a.sc.seed == SEED_MLP;
+    if (a.sc.eos_kind == EOS_TABLE && a.rk == 2 && !a.sc.counters &&
+        a.sc.limiter == LIM_MINMOD) {
+        if (mlp) {
+            if (a.rate_clk) HY_SWEEP(EOS_TABLE_MLP, 2, LIM_MINMOD, false, true)
+            else HY_SWEEP(EOS_TABLE_MLP, 2, LIM_MINMOD, false, false)
+        } else {
+            if (a.rate_clk) HY_SWEEP(EOS_TABLE, 2, LIM_MINMOD, false, true)
+            else HY_SWEEP(EOS_TABLE, 2, LIM_MINMOD, false, false)
+        }
+    }
     if (a.sc.eos_kind == EOS_CONFORMAL) {
         if (a.rk == 1) HY_SWEEP(EOS_CONFORMAL, 1, -1, true, true)
         if (a.rk == 2) HY_SWEEP(EOS_CONFORMAL, 2, -1, true, true)
         if (a.rk == 3) HY_SWEEP(EOS_CONFORMAL, 3, -1, true, true)
+    } else if (mlp) {
+        if (a.rk == 1) HY_SWEEP(EOS_TABLE_MLP, 1, -1, true, true)
+        if (a.rk == 2) HY_SWEEP(EOS_TABLE_MLP, 2, -1, true, true)
+        if (a.rk == 3) HY_SWEEP(EOS_TABLE_MLP, 3, -1, true, true)
     } else {
         if (a.rk == 1) HY_SWEEP(EOS_TABLE, 1, -1, true, true)
         if (a.rk == 2) HY_SWEEP(EOS_TABLE, 2, -1, true, true)

@@ -143,6 +143,16 @@ def _arg(a, dtype):
     return arr.ctypes.data_as(C.c_void_p), 0, arr
 
 
+def _out_arg(o, dtype):
+    """_arg for an output: a host output must be written in place."""
+    p, dev, keep = _arg(o, dtype)
+    if not dev:
+        base = o.numpy() if _is_tensor(o) else o
+        if not (isinstance(base, np.ndarray) and np.shares_memory(keep, base)):
+            raise ValueError("host output must be a contiguous array of the handle's dtype")
+    return p, dev, keep
+
+
 def _stream_ptr(stream):
     if stream is None:
         return None
@@ -247,10 +257,17 @@ class Hydro(_Base):
         _check(lib().hydro_get_conserved(self.h, p, dev))
         return out
 
-    def get_primitives(self):
-        outs = [np.empty(self.shape[1:], dtype=self._dtype) for _ in range(4)]
-        _check(lib().hydro_get_primitives(self.h, *[o.ctypes.data_as(C.c_void_p) for o in outs], 0))
-        return outs
+    def get_primitives(self, out=None):
+        """(e, vx, vy, vz) as new host arrays, or written into `out`: four
+        contiguous host arrays / CPU tensors (pinned ones copy at full speed) or
+        four CUDA tensors, of the handle's dtype."""
+        if out is None:
+            out = [np.empty(self.shape[1:], dtype=self._dtype) for _ in range(4)]
+        args = [_out_arg(o, self._dtype) for o in out]
+        if len({a[1] for a in args}) != 1:
+            raise ValueError("outputs must be all on the host or all on the device")
+        _check(lib().hydro_get_primitives(self.h, *[a[0] for a in args], args[0][1]))
+        return out
 
     def init_hotspots(self, spots, sigma, e_bg):
         s = np.ascontiguousarray(spots, dtype=np.float64)

@@ -358,3 +358,24 @@ def test_hubble_expansion_paper_settings(H, limiter):
     err = (np.abs(Ug - U)[:, live] / U[0][live][None]).max()
     assert err <= F64_TOL, err
     assert np.abs(Ug[:, ~live] - U[:, ~live]).max() <= 1e-12 * U[0].max()
+
+
+def test_get_primitives_into_pinned_and_device_buffers(H):
+    """The same primitives land in new arrays, pinned host tensors and CUDA
+    tensors; a host output that cannot be written in place is refused."""
+    import torch
+    g, prim = I.spherical_blast(24)
+    grid = H.make_grid(24, 24, 24, dx=g["dx"], x0=-1.0, y0=-1.0, z0=-1.0, prec="fp32")
+    h = H.Hydro(grid)
+    h.set_primitives(*[a.astype(np.float32) for a in prim])
+    h.step(2)
+    ref = h.get_primitives()
+    pinned = [torch.empty(a.shape, dtype=torch.float32).pin_memory() for a in ref]
+    dev = [torch.empty(a.shape, dtype=torch.float32, device="cuda") for a in ref]
+    h.get_primitives(out=pinned)
+    h.get_primitives(out=dev)
+    for r, p, d in zip(ref, pinned, dev):
+        assert np.array_equal(r, p.numpy())
+        assert np.array_equal(r, d.cpu().numpy())
+    with pytest.raises(ValueError):
+        h.get_primitives(out=[np.empty(a.shape, dtype=np.float64) for a in ref])
