@@ -36,6 +36,8 @@ WORKLOADS = {
     "blast256_fp32": dict(n=256, prec="fp32"),
     "blast256_fp64": dict(n=256, prec="fp64"),
     "blast128_fp32": dict(n=128, prec="fp32"),   # small case for ncu captures
+    # the paper's production settings (Sec. 3.2): RK3 and 4 MUSTA stages
+    "blast256_paper": dict(n=256, prec="fp32", rk=3, stages=4),
 }
 BYTES = {"fp32": 4, "fp64": 8}
 # Algorithmic floating-point operations of one sweep per cell (conformal EOS,
@@ -44,12 +46,23 @@ BYTES = {"fp32": 4, "fp64": 8}
 # cell (2 Hancock + 6 MUSTA per RK stage), plus limiter, faces, Hancock,
 # admissibility, MUSTA-FORCE linear algebra, divergence and RK updates: 800.
 FLOPS_PER_CELL_SWEEP = 800
+
+
+def flops_per_cell_sweep(rk=2, stages=2):
+    """The same count for any RK order and MUSTA stage number k: per RK stage
+    (2 + 3k) cons->prim + flux evaluations of 25 flops, 61 for slopes, faces,
+    Hancock and admissibility, 48 per MUSTA stage and 24 per predictor update
+    plus 3, and 4 for the divergence; RK combinations 24 (RK2) or 48 (RK3),
+    8 for RK1.  (rk, k) = (2, 2) gives 800."""
+    per_stage = (2 + 3 * stages) * 25 + 61 + 48 * stages + 24 * (stages - 1) + 3 + 4
+    combine = {1: 8, 2: 24, 3: 48}[rk]
+    return rk * per_stage + combine
 # FP32 (non-tensor) peak from unit counts and clock: 148 SMs x 128 FP32 lanes x
 # 2 flop per FMA x 2.032 GHz; FP64 from the B300's nominal 1.25 TFLOP/s.
 # DRAM bytes read + written per sweep launch, mean over the five sweeps of one
 # step, from an ncu capture of the current kernels (profiles/
 # sweep_blast256_fp32_step.md); None where no capture of the current kernels exists
-SWEEP_TRAFFIC = {(256, "fp32"): 597.3e6}
+SWEEP_TRAFFIC = {(256, "fp32", 2, 2): 597.3e6}
 ALU_PEAK_TFLOPS = {"fp32": 148 * 128 * 2 * 2.032e9 / 1e12, "fp64": 1.25}
 
 
@@ -127,13 +140,13 @@ def dist_setup():
     return world, rank, local
 
 
-def cpu_baseline_oracle(n=96, steps=1):
+def cpu_baseline_oracle(n=96, steps=1, rk=2, stages=2):
     """The oracle, as it stands, on a bounded sample: the blast recipe on n^3."""
     from oracle import oracle as O
     from paper_1510_06340_b300 import inputs as I
     g, prim = I.spherical_blast(n)
     o = O.Oracle(n, n, n, dx=g["dx"], x0=-1.0, y0=-1.0, z0=-1.0, bc="periodic",
-                 limiter="minmod", stages=2, cfl=0.4)
+                 limiter="minmod", stages=stages, rk_order=rk, cfl=0.4)
     U = o.prim2cons_field(*prim)
     t0 = time.perf_counter()
     o.run(U, steps)
@@ -186,13 +199,15 @@ def run_ours(args):
         dist.barrier()
     wl = WORKLOADS[args.workload]
     n, prec = wl["n"], wl["prec"]
+    rk, stages = wl.get("rk", 2), wl.get("stages", 2)
+    flops_cell_sweep = flops_per_cell_sweep(rk, stages)
     dt_np = np.float64 if prec == "fp64" else np.float32
     g, prim = I.spherical_blast(n)
     prim = [np.ascontiguousarray(a, dtype=dt_np) for a in prim]
     stream = torch.cuda.Stream()
     grid = hydro.make_grid(n, n, n, dx=g["dx"], x0=-1.0, y0=-1.0, z0=-1.0, bc="periodic",
-                           prec=prec, cfl=0.4)
-    h = hydro.Hydro(grid, limiter="minmod", stages=2, stream=stream)
+                           prec=prec, cfl=0.4, rk_order=rk)
+    h = hydro.Hydro(grid, limiter="minmod", stages=stages, stream=stream)
     h.set_primitives(*prim)
     cells = n ** 3
     if args.launch:
@@ -254,11 +269,12 @@ def run_ours(args):
     # per step: 5 sweeps + k_dt (the CFL rate is fused into the last sweep)
     launches = n_sweep + n_other
     alu_peak = ALU_PEAK_TFLOPS[prec]
-    flops_achieved = FLOPS_PER_CELL_SWEEP * cells / (avg_sweep_ms * 1e-3) / 1e12
+    flops_achieved = flops_cell_sweep * cells / (avg_sweep_ms * 1e-3) / 1e12
 
     cpu = None
     if rank == 0 and world >= 1 and not args.no_cpu:
-        v, el, sample = cpu_baseline_oracle(96, 1)
+        nb = 96 if (rk, stages) == (2, 2) else 64   # about the same seconds of CPU work
+        v, el, sample = cpu_baseline_oracle(nb, 1, rk, stages)
         cpu = {"value": v, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
                "sample": sample + f", {el:.1f} s"}
     if rank == 0:
@@ -269,17 +285,17 @@ def run_ours(args):
             "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "f64",
             "data": "synthetic",
             "config": {"workload": f"3D spherical blast {n}^3 on [-1,1]^3, p=e/3, "
-                                   f"{prec.upper()}, minmod, 2 MUSTA stages, RK2+Hancock, "
-                                   "Strang, periodic, CFL 0.4",
+                                   f"{prec.upper()}, minmod, {stages} MUSTA stages, "
+                                   f"RK{rk}+Hancock, Strang, periodic, CFL 0.4",
                        "cells": cells, "parallelism": f"replicas x{world}",
                        "launch_threads_segments_xyz": shapes,
                        "l2": "inputs larger than L2 (two state copies of "
                              f"{state_bytes / 1e6:.0f} MB)"},
             "roofline": {"bound": "alu", "achieved": flops_achieved, "peak": alu_peak,
                          "unit": "TFLOP/s", "frac": flops_achieved / alu_peak,
-                         "traffic": SWEEP_TRAFFIC.get((n, prec)),
+                         "traffic": SWEEP_TRAFFIC.get((n, prec, rk, stages)),
                          "kernel": "k_sweep (one directional sweep, all RK stages)",
-                         "algorithmic_flops_per_launch": FLOPS_PER_CELL_SWEEP * cells,
+                         "algorithmic_flops_per_launch": flops_cell_sweep * cells,
                          "avg_launch_ms": avg_sweep_ms,
                          "peak_source": "derived: 148 SM x 128 lanes x 2 x 2.032 GHz (fp32); "
                                         "nominal 1.25 TFLOP/s (fp64)"},

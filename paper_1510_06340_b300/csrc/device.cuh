@@ -628,7 +628,7 @@ __device__ __forceinline__ void shift_in(V4<R> (&q)[DEPTH], const V4<R> &v) {
 }
 
 // March one segment of a pencil: the RK stages of Eq. 5-7 fused in registers.
-// Every thread runs the same schedule (T = L + 4, L + 10 or L + 18 steps for
+// Every thread runs the same schedule (T = L + 4, L + 10 or L + 16 steps for
 // RK1/2/3), so a warp stays converged; stage k+1 starts a fixed number of
 // steps after stage k, reading stage k's outputs from a short register queue.
 // Cells [s0, s_end) are stored; the segment's nominal length L may run past
@@ -653,15 +653,15 @@ __device__ __forceinline__ void march(const PH &ph, const Pencil<R> &P, int s0, 
         return;
     }
     const bool rate_on = RATE && ra.ih_n > R(0);
-    const R third = R(1.0 / 3.0), two3 = R(2.0 / 3.0), q3 = R(0.75), q1 = R(0.25), half = R(0.5);
+    const R third = R(1.0 / 3.0), two3 = R(2.0 / 3.0), q3 = R(0.75), q1c = R(0.25), half = R(0.5);
     Stage<R> st1, st2, st3;
     st1.n = 0; st2.n = 0; st3.n = 0;
     V4<R> cell, D;
     constexpr int H = 2 * RK;                 // halo of the stage-1 input
-    constexpr int T_EXTRA = RK == 1 ? 4 : (RK == 2 ? 10 : 18);
+    constexpr int T_EXTRA = RK == 1 ? 4 : (RK == 2 ? 10 : 16);
     const int T = L + T_EXTRA;
     const int js = s0 - H;
-    V4<R> qa[RK == 3 ? 5 : 3], qb[3];
+    V4<R> qa[3];
     V4<R> lastA = v4<R>(0, 0, 0, 0), lastB = lastA;
     V4<R> nxt = P.load(wrap_index(js, N, bc));
     if (RK == 2) {
@@ -713,68 +713,80 @@ __device__ __forceinline__ void march(const PH &ph, const Pencil<R> &P, int s0, 
         }
         return;
     }
+    if (RK == 3) {
+        // The same uniform loop for Eq. 7: three engines push from step 0 on
+        // zero-initialised windows; each stage reads the previous stage's
+        // output two cells behind its newest (the 2 ghost cells of a stage).
+        // Stage 1 outputs cell t+s0-8, stage 2 cell t+s0-12, stage 3 t+s0-16.
+        const V4<R> zero = v4<R>(R(0), R(0), R(0), R(0));
+        st1.w0 = st1.w1 = st1.w2 = st1.urp = st1.fp = zero;
+        st2.w0 = st2.w1 = st2.w2 = st2.urp = st2.fp = zero;
+        st3.w0 = st3.w1 = st3.w2 = st3.urp = st3.fp = zero;
+        V4<R> q1[3] = {zero, zero, zero}, q2[3] = {zero, zero, zero};
+        const int T3 = L + 16;
+        int jn = wrap_index(js + 1, N, bc), jc = js + 1;
+        // U^n of the stage-2 and stage-3 output cells, one step ahead
+        int an = wrap_index(s0 - 11, N, bc), ac = s0 - 11;
+        int bn = wrap_index(s0 - 15, N, bc), bcn = s0 - 15;
+        V4<R> Ua = P.load(wrap_index(s0 - 12, N, bc));
+        V4<R> Ub = P.load(wrap_index(s0 - 16, N, bc));
+#pragma unroll 1
+        for (int t = 0; t < T3; ++t) {
+            const V4<R> V = nxt, U0 = Ua, U00 = Ub;
+            if (t + 1 < T3) {
+                nxt = P.load(jn);
+                Ua = P.load(an);
+                Ub = P.load(bn);
+            }
+            ++jc; ++ac; ++bcn;
+            if (bc == BC_OUTFLOW) {
+                jn = min(max(jc, 0), N - 1);
+                an = min(max(ac, 0), N - 1);
+                bn = min(max(bcn, 0), N - 1);
+            } else {
+                jn = jn + 1 == N ? 0 : jn + 1;
+                an = an + 1 == N ? 0 : an + 1;
+                bn = bn + 1 == N ? 0 : bn + 1;
+            }
+            st1.push_full(V, ph, lam, cell, D);
+            const int i = t + s0 - 8;                  // stage-1 output cell
+            const V4<R> X = vfma<R>(-lam, D, cell);    // U1 = U + dt L(U)
+            shift_in(q1, X);
+            if (i == N - 1) lastA = X;
+            V4<R> c2, D2;
+            st2.push_full(pick(q1, i, t + s0 - 10, N, bc, lastA), ph, lam, c2, D2);
+            const int i2 = t + s0 - 12;                // stage-2 output cell
+            // U2 = 3/4 U + 1/4 (U1 + dt L(U1))
+            const V4<R> Z = vfma<R>(q3, U0, vmul<R>(q1c, vfma<R>(-lam, D2, c2)));
+            shift_in(q2, Z);
+            if (i2 == N - 1) lastB = Z;
+            V4<R> c3, D3;
+            st3.push_full(pick(q2, i2, t + s0 - 14, N, bc, lastB), ph, lam, c3, D3);
+            const int o = t + s0 - 16;                 // finished cell
+            // U^{n+1} = 1/3 U + 2/3 (U2 + dt L(U2))
+            const V4<R> r = vfma<R>(third, U00, vmul<R>(two3, vfma<R>(-lam, D3, c3)));
+            const bool keep = do_store && o >= s0 && o < s_end;
+            if (rate_on && keep) {
+                const R rr = ph.rate(r, ra.ih_n, ra.ih_t1, ra.ih_t2, ra.iso);
+                ra.m = (rr > ra.m || rr != rr) ? rr : ra.m;
+            }
+            if (keep) P.store(o, r);
+        }
+        return;
+    }
+    // RK1 (plain MUSCL-Hancock with MUSTA-FORCE fluxes)
 #pragma unroll 1
     for (int t = 0; t < T; ++t) {
         const V4<R> V = nxt;
         if (t + 1 < T) nxt = P.load(wrap_index(js + t + 1, N, bc));
         if (!st1.push(V, ph, lam, cell, D)) continue;
-        // stage-1 output: cell i = js + t - 2
-        const int i = js + t - 2;
-        V4<R> X = vfma<R>(-lam, D, cell);   // U1 = U + dt L(U)
-        if (RK == 1) {
-            if (rate_on) {
-                const R rr = ph.rate(X, ra.ih_n, ra.ih_t1, ra.ih_t2, ra.iso);
-                if (do_store && i < s_end) ra.m = (rr > ra.m || rr != rr) ? rr : ra.m;
-            }
-            if (do_store && i < s_end) P.store(i, X);
-            continue;
+        const int i = js + t - 2;   // output cell
+        const V4<R> X = vfma<R>(-lam, D, cell);   // U + dt L(U)
+        if (rate_on) {
+            const R rr = ph.rate(X, ra.ih_n, ra.ih_t1, ra.ih_t2, ra.iso);
+            if (do_store && i < s_end) ra.m = (rr > ra.m || rr != rr) ? rr : ra.m;
         }
-        if (RK == 2) {
-            shift_in(qa, X);
-            if (i == N - 1) lastA = X;
-            if (t < 6) continue;
-            const int p = t + s0 - 8;            // stage-2 input position
-            const V4<R> Y = pick(qa, i, p, N, bc, lastA);
-            V4<R> c, Dl;
-            if (!st2.push(Y, ph, lam, c, Dl)) continue;
-            const int o = t + s0 - 10;           // finished cell
-            const V4<R> U0 = P.load(wrap_index(o, N, bc));
-            // Eq. 6: U^{n+1} = 1/2 (U + U1 + dt L(U1))
-            const V4<R> r = vmul<R>(half, vfma<R>(-lam, Dl, vadd(U0, c)));
-            if (rate_on) {
-                const R rr = ph.rate(r, ra.ih_n, ra.ih_t1, ra.ih_t2, ra.iso);
-                if (do_store && o < s_end) ra.m = (rr > ra.m || rr != rr) ? rr : ra.m;
-            }
-            if (do_store && o < s_end) P.store(o, r);
-        } else {   // RK == 3, Eq. 7
-            shift_in(qa, X);
-            if (i == N - 1) lastA = X;
-            if (t < 8) continue;
-            const int p2 = t + s0 - 12;
-            const V4<R> Y = pick(qa, i, p2, N, bc, lastA);
-            V4<R> c2, D2;
-            if (!st2.push(Y, ph, lam, c2, D2)) continue;
-            const int i2 = t + s0 - 14;
-            const V4<R> U0 = P.load(wrap_index(i2, N, bc));
-            // U2 = 3/4 U + 1/4 (U1 + dt L(U1))
-            V4<R> Z = vfma<R>(q3, U0, vmul<R>(q1, vfma<R>(-lam, D2, c2)));
-            shift_in(qb, Z);
-            if (i2 == N - 1) lastB = Z;
-            if (t < 14) continue;
-            const int p3 = t + s0 - 16;
-            const V4<R> Y3 = pick(qb, i2, p3, N, bc, lastB);
-            V4<R> c3, D3;
-            if (!st3.push(Y3, ph, lam, c3, D3)) continue;
-            const int o = t + s0 - 18;
-            const V4<R> U00 = P.load(wrap_index(o, N, bc));
-            // U^{n+1} = 1/3 U + 2/3 (U2 + dt L(U2))
-            const V4<R> r = vfma<R>(third, U00, vmul<R>(two3, vfma<R>(-lam, D3, c3)));
-            if (rate_on) {
-                const R rr = ph.rate(r, ra.ih_n, ra.ih_t1, ra.ih_t2, ra.iso);
-                if (do_store && o < s_end) ra.m = (rr > ra.m || rr != rr) ? rr : ra.m;
-            }
-            if (do_store && o < s_end) P.store(o, r);
-        }
+        if (do_store && i < s_end) P.store(i, X);
     }
 }
 
