@@ -47,6 +47,15 @@
  *      f(v) = v - |M|/(E + p(E - |M| v)) in the bracket [0, |M|/E].
  *  R12 Jet source: S^{0mu} = dEdx (1, n) g(x - x0 - n t), g a normalised
  *      3-D Gaussian; added once per step as U += dt S(t_n) before the sweeps.
+ *  R16 Unsplit scheme (unsplit = 1; the paper's multi-D MUSCL-Hancock of
+ *      Eq. 13 with FORCE alpha, 3 in 3-D): (a) each flux term of the half
+ *      step uses the faces of its own axis, h = 1/2 sum_d dt/dx_d
+ *      (F_d(U^L_d) - F_d(U^R_d)), and every face of the cell is advanced by
+ *      the same h; (b) R9's fallback: if any evolved face is not admissible,
+ *      all faces of the cell are its cell average; (c) dt = cfl / max over
+ *      cells of sum_d max|lam_d| / dx_d over the axes with more than one cell;
+ *      (d) the RK stages of Eq. 6-7 act on the whole field, with
+ *      dt L(U) = - sum_d dt/dx_d (F_d,i+1/2 - F_d,i-1/2).
  */
 #include <math.h>
 #include <stdlib.h>
@@ -77,6 +86,7 @@ typedef struct {
     double newton_tol;         /* |dv| tolerance */
     int jet_on;
     double jet[8];             /* x0,y0,z0, nx,ny,nz, dEdx, sigma */
+    int unsplit;               /* 1: unsplit multi-D scheme (R16) instead of Strang sweeps */
 } or_config;
 
 /* diagnostics counters (reset by or_reset_counters) */
@@ -587,15 +597,172 @@ void or_jet_source(const or_config *c, double *U, double t, double dt) {
             }
 }
 
+
+/* -------------------------------------------------------- unsplit (R16) */
+/* cell index of the logical position (i, j, k), ghosts mapped by the BCs */
+static long grid_index(const or_config *c, int i, int j, int k) {
+    int n[3] = {c->nx, c->ny, c->nz};
+    int x[3] = {i, j, k};
+    for (int d = 0; d < 3; d++) {
+        if (c->bc[d] == 0) x[d] = ((x[d] % n[d]) + n[d]) % n[d];
+        else x[d] = x[d] < 0 ? 0 : (x[d] >= n[d] ? n[d] - 1 : x[d]);
+    }
+    return x[0] + (long)c->nx * (x[1] + (long)c->ny * x[2]);
+}
+
+static void grid_load(const or_config *c, const double *U, int i, int j, int k, double u[4]) {
+    long cells = (long)c->nx * c->ny * c->nz;
+    long g = grid_index(c, i, j, k);
+    for (int q = 0; q < 4; q++) u[q] = U[q * cells + g];
+}
+
+/*
+ * dt L(U) of the unsplit scheme for every cell (R16): D[q][cell] receives
+ * sum_d dt/dx_d (F_d,i+1/2 - F_d,i-1/2).  Faces are evolved for the cells of
+ * the box grown by one cell along every active axis; fluxes are taken at the
+ * interfaces of the real cells.
+ */
+static void unsplit_L(const or_config *c, const double *U, double dt, double *D) {
+    int n[3] = {c->nx, c->ny, c->nz};
+    double h[3] = {c->dx, c->dy, c->dz};
+    int act[3], g[3];
+    for (int d = 0; d < 3; d++) { act[d] = n[d] > 1; g[d] = act[d] ? 1 : 0; }
+    int m[3] = {n[0] + 2 * g[0], n[1] + 2 * g[1], n[2] + 2 * g[2]};
+    long mcells = (long)m[0] * m[1] * m[2];
+    long cells = (long)n[0] * n[1] * n[2];
+    /* evolved faces: FL[d][cell of the grown box][q], FR likewise */
+    double *FLf = malloc(sizeof(double) * 3 * mcells * 4);
+    double *FRf = malloc(sizeof(double) * 3 * mcells * 4);
+    for (int k = -g[2]; k < n[2] + g[2]; k++)
+        for (int j = -g[1]; j < n[1] + g[1]; j++)
+            for (int i = -g[0]; i < n[0] + g[0]; i++) {
+                long mi = (i + g[0]) + (long)m[0] * ((j + g[1]) + (long)m[1] * (k + g[2]));
+                double V0[4], UL[3][4], UR[3][4], hq[4] = {0.0, 0.0, 0.0, 0.0};
+                grid_load(c, U, i, j, k, V0);
+                for (int d = 0; d < 3; d++) {
+                    if (!act[d]) continue;
+                    double Vm[4], Vp[4];
+                    int o[3] = {0, 0, 0};
+                    o[d] = 1;
+                    grid_load(c, U, i - o[0], j - o[1], k - o[2], Vm);
+                    grid_load(c, U, i + o[0], j + o[1], k + o[2], Vp);
+                    /* Eq. 15-17 along axis d */
+                    for (int q = 0; q < 4; q++) {
+                        double sl = or_limiter(c->limiter, V0[q] - Vm[q], Vp[q] - V0[q]);
+                        UL[d][q] = V0[q] - 0.5 * sl;
+                        UR[d][q] = V0[q] + 0.5 * sl;
+                    }
+                    if (c->hancock) {   /* Eq. 13: the axis-d term of the half step */
+                        double FLd[4], FRd[4];
+                        or_flux(c, d, UL[d], FLd);
+                        or_flux(c, d, UR[d], FRd);
+                        for (int q = 0; q < 4; q++)
+                            hq[q] += 0.5 * (dt / h[d]) * (FLd[q] - FRd[q]);
+                    }
+                }
+                int ok = 1;
+                for (int d = 0; d < 3; d++) {
+                    if (!act[d]) continue;
+                    for (int q = 0; q < 4; q++) {
+                        UL[d][q] += hq[q];
+                        UR[d][q] += hq[q];
+                    }
+                    if (!admissible(c, UL[d]) || !admissible(c, UR[d])) ok = 0;
+                }
+                if (!ok) g_face_fallback++;
+                for (int d = 0; d < 3; d++) {
+                    if (!act[d]) continue;
+                    for (int q = 0; q < 4; q++) {
+                        FLf[((long)d * mcells + mi) * 4 + q] = ok ? UL[d][q] : V0[q];
+                        FRf[((long)d * mcells + mi) * 4 + q] = ok ? UR[d][q] : V0[q];
+                    }
+                }
+            }
+    for (long x = 0; x < 4 * cells; x++) D[x] = 0.0;
+    /* MUSTA-FORCE fluxes at both interfaces of every real cell, axis by axis */
+    for (int d = 0; d < 3; d++) {
+        if (!act[d]) continue;
+        double lam = dt / h[d];
+        for (int k = 0; k < n[2]; k++)
+            for (int j = 0; j < n[1]; j++)
+                for (int i = 0; i < n[0]; i++) {
+                    int o[3] = {0, 0, 0};
+                    o[d] = 1;
+                    long mc = (i + g[0]) + (long)m[0] * ((j + g[1]) + (long)m[1] * (k + g[2]));
+                    long mm = (i - o[0] + g[0]) +
+                              (long)m[0] * ((j - o[1] + g[1]) + (long)m[1] * (k - o[2] + g[2]));
+                    long mp = (i + o[0] + g[0]) +
+                              (long)m[0] * ((j + o[1] + g[1]) + (long)m[1] * (k + o[2] + g[2]));
+                    double Fm[4], Fp[4];
+                    /* interface i-1/2: right face of cell i-1, left face of cell i (R3) */
+                    or_musta_force(c, d, lam, &FRf[((long)d * mcells + mm) * 4],
+                                   &FLf[((long)d * mcells + mc) * 4], Fm);
+                    or_musta_force(c, d, lam, &FRf[((long)d * mcells + mc) * 4],
+                                   &FLf[((long)d * mcells + mp) * 4], Fp);
+                    long cidx = i + (long)n[0] * (j + (long)n[1] * k);
+                    for (int q = 0; q < 4; q++) D[q * cells + cidx] += lam * (Fp[q] - Fm[q]);
+                }
+    }
+    free(FLf);
+    free(FRf);
+}
+
+/* one unsplit step of length dt: the RK stages of Eq. 5-7 on the whole field */
+static void unsplit_rk(const or_config *c, double *U, double dt) {
+    long cells = (long)c->nx * c->ny * c->nz;
+    long nv = 4 * cells;
+    double *D = malloc(sizeof(double) * nv);
+    double *U1 = malloc(sizeof(double) * nv);
+    double *U2 = malloc(sizeof(double) * nv);
+    unsplit_L(c, U, dt, D);
+    if (c->rk_order == 1) {
+        for (long x = 0; x < nv; x++) U[x] = U[x] - D[x];
+    } else {
+        for (long x = 0; x < nv; x++) U1[x] = U[x] - D[x];   /* U1 = U + dt L(U) */
+        unsplit_L(c, U1, dt, D);
+        if (c->rk_order == 3) {
+            for (long x = 0; x < nv; x++) U2[x] = 0.75 * U[x] + 0.25 * (U1[x] - D[x]);
+            unsplit_L(c, U2, dt, D);
+            for (long x = 0; x < nv; x++) U[x] = U[x] / 3.0 + (2.0 / 3.0) * (U2[x] - D[x]);
+        } else {
+            for (long x = 0; x < nv; x++) U[x] = 0.5 * (U[x] + U1[x] - D[x]);
+        }
+    }
+    free(D);
+    free(U1);
+    free(U2);
+}
+
+/* R16c: max over cells of sum over active axes of speed/dx */
+double or_max_rate_unsplit(const or_config *c, const double *U) {
+    long cells = (long)c->nx * c->ny * c->nz;
+    int n[3] = {c->nx, c->ny, c->nz};
+    double h[3] = {c->dx, c->dy, c->dz};
+    double m = 0.0;
+    for (long i = 0; i < cells; i++) {
+        double u[4] = {U[i], U[cells + i], U[2 * cells + i], U[3 * cells + i]};
+        double r = 0.0;
+        for (int d = 0; d < 3; d++)
+            if (n[d] > 1) r += or_signal_speed(c, u, d) / h[d];
+        if (r > m) m = r;
+    }
+    return m;
+}
+
 /* ----------------------------------------------------------------- step */
-/* one full step: dt (R8), source (R12), Strang sweeps (R7).  Returns dt. */
+/* one full step: dt (R8 or R16c), source (R12), Strang sweeps (R7) or the
+   unsplit scheme (R16).  Returns dt. */
 double or_step(const or_config *c, double *U, double t, double t_end) {
     double dt;
     if (c->fixed_dt > 0.0) dt = c->fixed_dt;
-    else dt = c->cfl / or_max_rate(c, U);
+    else dt = c->cfl / (c->unsplit ? or_max_rate_unsplit(c, U) : or_max_rate(c, U));
     if (t_end > 0.0 && t + dt > t_end) dt = t_end - t;
     if (!(dt > 0.0)) return 0.0;
     if (c->jet_on) or_jet_source(c, U, t, dt);
+    if (c->unsplit) {
+        unsplit_rk(c, U, dt);
+        return dt;
+    }
     int n[3] = {c->nx, c->ny, c->nz};
     int act[3], na = 0;
     for (int d = 0; d < 3; d++) if (n[d] > 1) act[na++] = d;

@@ -50,6 +50,7 @@ class _Cfg(C.Structure):
         ("seed_kind", C.c_int), ("mlp", C.POINTER(C.c_double)), ("mlp_quantize", C.c_int),
         ("newton_tol", C.c_double),
         ("jet_on", C.c_int), ("jet", C.c_double * 8),
+        ("unsplit", C.c_int),
     ]
 
 
@@ -75,6 +76,8 @@ def lib():
         L.or_signal_speed.argtypes = [P, _dp, C.c_int]
         L.or_max_rate.restype = C.c_double
         L.or_max_rate.argtypes = [P, _dp]
+        L.or_max_rate_unsplit.restype = C.c_double
+        L.or_max_rate_unsplit.argtypes = [P, _dp]
         L.or_jet_source.argtypes = [P, _dp, C.c_double, C.c_double]
         L.or_step.restype = C.c_double
         L.or_step.argtypes = [P, _dp, C.c_double, C.c_double]
@@ -111,7 +114,7 @@ class Oracle:
                  bc=("periodic", "periodic", "periodic"), limiter="minmod", stages=2,
                  rk_order=2, hancock=1, alpha=1.0, cfl=0.4, fixed_dt=0.0, delta=1e-12, eos=None,
                  cs2=1.0 / 3.0, seed_kind=0, mlp=None, mlp_quantize=0, newton_tol=1e-13,
-                 jet=None):
+                 jet=None, unsplit=0):
         self.keep = []
         c = _Cfg()
         c.nx, c.ny, c.nz = nx, ny, nz
@@ -148,6 +151,7 @@ class Oracle:
             c.jet_on = 1
             for i in range(8):
                 c.jet[i] = float(jet[i])
+        c.unsplit = int(unsplit)
         self.c = c
         self.shape = (4, nz, ny, nx)
 
@@ -218,6 +222,10 @@ class Oracle:
         lib().or_sweep(C.byref(self.c), _ptr(U), d, dt)
 
     def max_rate(self, U):
+        """The rate whose inverse times cfl is dt: max over axes (split) or the
+        sum over axes (unsplit, R16c)."""
+        if self.c.unsplit:
+            return lib().or_max_rate_unsplit(C.byref(self.c), _ptr(U))
         return lib().or_max_rate(C.byref(self.c), _ptr(U))
 
     def jet_source(self, U, t, dt):

@@ -318,7 +318,7 @@ def test_axis_embedding_equals_1d_run(axis):
     assert not got[others].any()
 
 
-def hubble_error(n, dx, dt, nsteps, t0=2.0):
+def hubble_error(n, dx, dt, nsteps, t0=2.0, **kw):
     lo = -0.5 * n * dx
     c = I.cell_centres(n, lo, dx)
     zz, yy, xx = np.meshgrid(c, c, c, indexing="ij")
@@ -328,7 +328,7 @@ def hubble_error(n, dx, dt, nsteps, t0=2.0):
     e = np.where(inside, e, 0.0)
     vr = np.where(inside, vr, 0.0)
     rs = np.where(r > 0, r, 1.0)
-    o = O.Oracle(n, n, n, dx=dx, x0=lo, y0=lo, z0=lo, bc="outflow", fixed_dt=dt)
+    o = O.Oracle(n, n, n, dx=dx, x0=lo, y0=lo, z0=lo, bc="outflow", fixed_dt=dt, **kw)
     U = o.prim2cons_field(e, vr * xx / rs, vr * yy / rs, vr * zz / rs)
     o.run(U, nsteps)
     ee, vx, vy, vz, _ = o.cons2prim_field(U)
@@ -471,3 +471,119 @@ def test_jet_source_deposits_dedx_per_unit_time():
     # the Gaussian's tail beyond the box edge (6 sigma away) is ~1e-9 of its mass
     assert abs(ds[0] - want) < 1e-8 * want
     np.testing.assert_allclose(ds[1:], want * jet[3:6], atol=1e-8 * want)
+
+
+# ----------------------------------------------- unsplit multi-D scheme (R16)
+def test_unsplit_on_a_line_equals_the_1d_sweep():
+    """With one active axis the unsplit scheme (Eq. 13 with only the F term)
+    is the 1-D MUSCL-Hancock MUSTA-FORCE step: same faces, fluxes, RK stages
+    and CFL dt (sum over one axis = max over one axis)."""
+    for rk in (1, 2, 3):
+        g, prim = I.shock_tube(200)
+        kw = dict(dx=g["dx"], x0=-1.0, bc="outflow", alpha=3.0, rk_order=rk, cfl=0.4)
+        a, b = O.Oracle(200, **kw), O.Oracle(200, unsplit=1, **kw)
+        Ua = a.prim2cons_field(*prim)
+        Ub = Ua.copy()
+        a.run(Ua, 40)
+        b.run(Ub, 40)
+        assert np.array_equal(Ua, Ub), rk
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_unsplit_plane_wave_equals_1d_unsplit(axis):
+    """Data varying along one axis only of a 3-D grid: the transverse half-step
+    terms vanish (zero slopes give equal faces) and so do the transverse flux
+    differences, so every line equals the 1-D unsplit run."""
+    n = 48
+    g, prim = I.shock_tube(n)
+    dt = 0.1 * g["dx"]
+    ref = O.Oracle(n, dx=g["dx"], x0=-1.0, bc="outflow", alpha=3.0, unsplit=1, fixed_dt=dt)
+    U1 = ref.prim2cons_field(*prim)
+    ref.run(U1, 12)
+    shape = [5, 5, 5]
+    shape[2 - axis] = n
+    bc = ["periodic"] * 3
+    bc[axis] = "outflow"
+    o = O.Oracle(shape[2], shape[1], shape[0], dx=g["dx"], bc=tuple(bc), alpha=3.0, unsplit=1,
+                 fixed_dt=dt)
+    sl = [None, None, None]
+    sl[2 - axis] = slice(None)
+    e = np.broadcast_to(prim[0].ravel()[tuple(sl)], shape).copy()
+    z = np.zeros(shape)
+    U3 = o.prim2cons_field(e, z, z, z)
+    o.run(U3, 12)
+    line = [slice(None), 2, 2, 2]
+    line[1 + (2 - axis)] = slice(None)
+    got = U3[tuple(line)]
+    assert np.array_equal(got[0], U1[0].ravel())
+    assert np.array_equal(got[1 + axis], U1[1].ravel())
+    others = [q for q in (1, 2, 3) if q != 1 + axis]
+    assert not got[others].any()
+
+
+def unsplit_blast(n, steps, limiter="minmod"):
+    g, prim = I.spherical_blast(n)
+    o = O.Oracle(n, n, n, dx=g["dx"], x0=-1.0, y0=-1.0, z0=-1.0, bc="periodic",
+                 limiter=limiter, cfl=0.4, alpha=3.0, unsplit=1)
+    U = o.prim2cons_field(*prim)
+    s0 = o.conservation_sums(U)
+    o.run(U, steps)
+    return o, U, s0
+
+
+def test_unsplit_blast_conserves_and_is_symmetric():
+    """Periodic flux form conserves E and M to roundoff; the blast stays
+    symmetric under each reflection (M_d odd) and under exchange of two axes
+    (the scheme treats the axes alike; only the order of the axis sums differs)."""
+    o, U, s0 = unsplit_blast(16, 6)
+    s1 = o.conservation_sums(U)
+    assert abs(s1[0] - s0[0]) <= 1e-13 * s0[0]
+    assert np.abs(s1[1:]).max() <= 1e-13 * s0[0]
+    scale = U[0].max()
+    for ax in range(3):
+        R = np.flip(U, axis=3 - ax).copy()
+        R[1 + ax] *= -1.0
+        assert np.abs(R - U).max() <= 1e-14 * scale
+    # exchange x and y: array axes 3 and 2, momentum components 1 and 2
+    T = np.swapaxes(U, 2, 3)[[0, 2, 1, 3]]
+    assert np.abs(T - U).max() <= 1e-13 * scale
+
+
+def test_unsplit_and_strang_agree_on_the_blast():
+    """Two consistent discretisations of the same flow: after the same physical
+    time their energy densities differ by discretisation error only (small
+    against the blast's jump of 9), and both keep E positive."""
+    n = 24
+    g, prim = I.spherical_blast(n)
+    kw = dict(dx=g["dx"], x0=-1.0, y0=-1.0, z0=-1.0, bc="periodic", cfl=0.4)
+    a = O.Oracle(n, n, n, **kw)
+    b = O.Oracle(n, n, n, alpha=3.0, unsplit=1, **kw)
+    Ua = a.prim2cons_field(*prim)
+    Ub = Ua.copy()
+    _, ta = a.run(Ua, 10)
+    _, tb = b.run(Ub, 200, t_end=ta)
+    assert tb == ta
+    assert Ua[0].min() > 0 and Ub[0].min() > 0
+    assert np.abs(Ua[0] - Ub[0]).mean() <= 0.05 * np.abs(Ua[0] - 1.0).mean() + 0.02
+
+
+def test_unsplit_cfl_rate_sums_the_axes():
+    """R16c: the rate is the sum over active axes of speed/dx; at rest with
+    c_s^2 = 1/3 each axis contributes c_s/dx."""
+    n = 8
+    o = O.Oracle(n, n, n, dx=0.25, unsplit=1)
+    U = o.prim2cons_field(np.ones((n, n, n)), *[np.zeros((n, n, n))] * 3)
+    assert o.max_rate(U) == pytest.approx(3 * math.sqrt(1 / 3) / 0.25, rel=1e-14)
+    o2 = O.Oracle(n, n, n, dx=0.25)
+    assert o2.max_rate(U) == pytest.approx(math.sqrt(1 / 3) / 0.25, rel=1e-14)
+
+
+@pytest.mark.slow
+def test_unsplit_hubble_expansion_interior_converges():
+    """The unsplit scheme (alpha = 3) on the same 3-D Hubble flow: the core
+    follows the exact solution and the error falls under refinement at a fixed
+    Courant number small enough for the unsplit stability limit."""
+    e1, v1 = hubble_error(32, 0.1, 0.02, 15, alpha=3.0, unsplit=1)
+    e2, v2 = hubble_error(64, 0.05, 0.01, 30, alpha=3.0, unsplit=1)
+    assert e1 < 0.04 and v1 < 0.01
+    assert e2 < e1 / 2 and v2 < v1 / 2
