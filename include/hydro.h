@@ -83,7 +83,11 @@ typedef struct {
     int hancock;              /* 1: Hancock half step of Eq. 13 inside each stage (paper); 0: off */
     double cfl;               /* Courant number of the CFL time step */
     double fixed_dt;          /* > 0: use this time step instead of the CFL step */
-    double alpha;             /* FORCE alpha of Eq. 10-11 (1 for split sweeps) */
+    double alpha;             /* FORCE alpha of Eq. 10-11 (1 for split sweeps, 3 for unsplit 3-D) */
+    int unsplit;              /* 0: Strang-split sweeps X(1/2) Y(1/2) Z(1) Y(1/2) X(1/2);
+                                 1: the unsplit MUSCL-Hancock step of Eq. 13 with every flux
+                                 term, one RK update of the whole field per stage, CFL rate
+                                 summed over the axes; all events of a batch must agree */
 } hydro_grid_t;
 
 /* Equation of state p(e) of Eq. 2 (no charge). */

@@ -24,7 +24,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 BASE = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + SRC, "-I" + INC]
 # float sweeps use approximate sqrt/divide and flush denormals (a few ulp, far
 # inside the FP32 tolerance)
-FAST = {"sweep_f32.cu", "sweep_mixed.cu"}
+FAST = {"sweep_f32.cu", "sweep_mixed.cu", "unsplit_f32.cu", "unsplit_mixed.cu"}
 FAST_FLAGS = ["-ftz=true", "-prec-div=false", "-prec-sqrt=false"]
 NOFMAD = set()   # units compiled with -fmad=false (none)
 

@@ -77,6 +77,14 @@ struct Solver {
     size_t sweep_cap[3] = {0, 0, 0};
     double *d_partial = nullptr, *d_sums = nullptr;
     int *d_work_counter = nullptr;     // persistent sweeps of a batch
+    // unsplit scheme (R16): scratch faces and fluxes, RK stage states, work lists
+    bool unsplit = false;
+    std::vector<UnsplitGeo> ugeo;
+    UnsplitGeo *d_ugeo = nullptr;
+    void *d_faces = nullptr, *d_fluxes = nullptr;
+    void *d_stage[2] = {nullptr, nullptr};
+    std::vector<WorkItem> us_face_items, us_flux_items[3];
+    WorkItem *d_us_face_items = nullptr, *d_us_flux_items[3] = {nullptr, nullptr, nullptr};
     // scheme
     Scheme sc{};
     double *d_p64 = nullptr, *d_c64 = nullptr;
@@ -126,7 +134,9 @@ struct Solver {
         void *ptrs[] = {d_geo, d_clk, d_clk_tune, d_state[0], d_state[1], d_cell_items,
                         d_sweep_items[0], d_sweep_items[1], d_sweep_items[2], d_partial, d_sums,
                         d_p64, d_c64, d_p32, d_c32, d_mlp_f, d_mlp_w, d_counters,
-                        d_work_counter};
+                        d_work_counter, d_ugeo, d_faces, d_fluxes, d_stage[0], d_stage[1],
+                        d_us_face_items, d_us_flux_items[0], d_us_flux_items[1],
+                        d_us_flux_items[2]};
         for (void *p : ptrs)
             if (p) cudaFree(p);
         d_geo = nullptr;
@@ -141,6 +151,11 @@ struct Solver {
         d_mlp_w = nullptr;
         d_counters = nullptr;
         d_work_counter = nullptr;
+        d_ugeo = nullptr;
+        d_faces = d_fluxes = nullptr;
+        d_stage[0] = d_stage[1] = nullptr;
+        d_us_face_items = nullptr;
+        for (int a = 0; a < 3; ++a) d_us_flux_items[a] = nullptr;
     }
 
     Scheme scheme() const {
@@ -160,6 +175,7 @@ struct Solver {
         c.prec = prec == HYDRO_FP64 ? 0 : 1;
         c.mixed = prec == HYDRO_MIXED ? 1 : 0;
         c.sc = scheme();
+        c.rate_sum = unsplit ? 1 : 0;
         return c;
     }
 
@@ -178,6 +194,10 @@ struct Solver {
         nevents = n;
         prec = g0.prec;
         rk = g0.rk_order;
+        unsplit = g0.unsplit != 0;
+        for (int e = 1; e < n; ++e)
+            if ((grids[e].unsplit != 0) != unsplit)
+                return fail(HYDRO_E_INVALID, "all events of a batch use the same scheme (unsplit)");
         cfl = g0.cfl;
         fixed_dt = g0.fixed_dt;
         elem = prec == HYDRO_FP64 ? 8 : 4;
@@ -318,7 +338,106 @@ struct Solver {
         CK(cudaMalloc(&d_partial, cell_items.size() * 4 * sizeof(double)));
         CK(cudaMalloc(&d_sums, (size_t)n * 4 * sizeof(double)));
         if (n > 1) CK(cudaMalloc(&d_work_counter, sizeof(int)));
+        if (unsplit) {
+            hydro_status st = init_unsplit();
+            if (st != HYDRO_OK) return st;
+        }
         return HYDRO_OK;
+    }
+
+    // scratch and work lists of the unsplit scheme (R16)
+    hydro_status init_unsplit() {
+        ugeo.resize(nevents);
+        long long fo = 0, xo = 0;
+        for (int e = 0; e < nevents; ++e) {
+            const EventGeo &g = geo[e];
+            UnsplitGeo &u = ugeo[e];
+            memset(&u, 0, sizeof u);
+            for (int a = 0; a < 3; ++a) {
+                u.g[a] = g.n[a] > 1 ? 1 : 0;
+                u.m[a] = g.n[a] + 2 * u.g[a];
+            }
+            u.gcells = (long long)u.m[0] * u.m[1] * u.m[2];
+            u.fo = fo;
+            fo += 24 * u.gcells;
+            for (int a = 0; a < 3; ++a) {
+                u.nint[a] = u.g[a] ? (g.cells / g.n[a]) * (long long)(g.n[a] + 1) : 0;
+                u.xo[a] = xo;
+                xo += 4 * u.nint[a];
+            }
+            for (long long c = 0; c < u.gcells; c += US_ITEM) us_face_items.push_back(item(e, c, u.gcells));
+            for (int a = 0; a < 3; ++a)
+                for (long long c = 0; c < u.nint[a]; c += US_ITEM)
+                    us_flux_items[a].push_back(item(e, c, u.nint[a]));
+        }
+        CK(cudaMalloc(&d_ugeo, nevents * sizeof(UnsplitGeo)));
+        CK(cudaMemcpy(d_ugeo, ugeo.data(), nevents * sizeof(UnsplitGeo), cudaMemcpyHostToDevice));
+        CK(cudaMalloc(&d_faces, (size_t)fo * elem));
+        CK(cudaMalloc(&d_fluxes, (size_t)std::max(xo, 1LL) * elem));
+        const size_t bytes = (size_t)4 * total_cells * elem;
+        CK(cudaMalloc(&d_stage[0], bytes));
+        if (rk == 3) CK(cudaMalloc(&d_stage[1], bytes));
+        auto upload = [&](const std::vector<WorkItem> &v, WorkItem **d) -> cudaError_t {
+            if (v.empty()) return cudaSuccess;
+            cudaError_t err = cudaMalloc(d, v.size() * sizeof(WorkItem));
+            if (err != cudaSuccess) return err;
+            return cudaMemcpy(*d, v.data(), v.size() * sizeof(WorkItem), cudaMemcpyHostToDevice);
+        };
+        CK(upload(us_face_items, &d_us_face_items));
+        for (int a = 0; a < 3; ++a) CK(upload(us_flux_items[a], &d_us_flux_items[a]));
+        return HYDRO_OK;
+    }
+
+    static constexpr int US_ITEM = 256;   // units per unsplit work item (one per thread)
+    static WorkItem item(int e, long long first, long long total) {
+        WorkItem w;
+        w.event = e;
+        w.first = first;
+        w.count = (int)std::min<long long>(US_ITEM, total - first);
+        return w;
+    }
+
+    // one step of the unsplit scheme after dt and the source: RK stages of
+    // faces, fluxes and update; the last stage writes the spare buffer
+    cudaError_t enqueue_unsplit(bool cfl_dt) {
+        UnsplitLaunch a;
+        a.faces = d_faces;
+        a.fluxes = d_fluxes;
+        a.ev = d_geo;
+        a.ug = d_ugeo;
+        a.face_items = d_us_face_items;
+        a.n_face_items = (int)us_face_items.size();
+        for (int d = 0; d < 3; ++d) {
+            a.flux_items[d] = d_us_flux_items[d];
+            a.n_flux_items[d] = (int)us_flux_items[d].size();
+        }
+        a.cell_items = d_cell_items;
+        a.n_cell_items = (int)cell_items.size();
+        a.clk = d_clk;
+        a.sc = scheme();
+        a.rk = rk;
+        a.sms = sms;
+        a.stream = stream;
+        a.u0 = d_state[cur];
+        for (int st = 1; st <= rk; ++st) {
+            const bool last = st == rk;
+            // stage inputs: U^n, then U1 (d_stage[0]), then U2 (d_stage[1])
+            a.in = st == 1 ? d_state[cur] : d_stage[st - 2];
+            a.u1 = st == 1 ? nullptr : d_stage[st - 2];
+            a.out = last ? d_state[1 - cur] : d_stage[st - 1];
+            a.stage = st;
+            a.rate_clk = (last && cfl_dt) ? d_clk : nullptr;
+            size_t sl = 0;
+            cudaError_t e = mark_begin(0, sl);
+            if (e != cudaSuccess) return e;
+            if (prec == HYDRO_FP64) e = launch_unsplit_f64(a);
+            else if (prec == HYDRO_FP32) e = launch_unsplit_f32(a);
+            else e = launch_unsplit_mixed(a);
+            if (e != cudaSuccess) return e;
+            if ((e = mark_end(sl)) != cudaSuccess) return e;
+        }
+        cur = 1 - cur;
+        return cudaSuccess;
     }
 
     // ---------------------------------------------------------------- launch shapes
@@ -436,6 +555,7 @@ struct Solver {
                 hydro_status s = build_sweep_items(a, shape[a]);
                 if (s != HYDRO_OK) return s;
             }
+            if (unsplit) continue;   // the unsplit scheme launches no sweeps
             hydro_status s = tune(a);
             if (s != HYDRO_OK) return s;
         }
@@ -488,6 +608,12 @@ struct Solver {
         if ((err = launch_dt(d_clk, cf, nevents, stream)) != cudaSuccess) return err;
         if (any_jet && (err = launch_jet(c, d_state[cur], d_clk)) != cudaSuccess) return err;
         if ((err = mark_end(slot)) != cudaSuccess) return err;
+        if (unsplit) {
+            bool any = active[0] || active[1] || active[2];
+            if (any && (err = enqueue_unsplit(cfl_dt)) != cudaSuccess) return err;
+            rate_valid = cfl_dt && any;
+            return cudaSuccess;
+        }
         int act[3], na = 0;
         for (int a = 0; a < 3; ++a)
             if (active[a]) act[na++] = a;

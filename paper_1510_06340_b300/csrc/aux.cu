@@ -132,7 +132,7 @@ __device__ __forceinline__ void flush_rate(R m, int event, EventClock *clk, R *r
 template <class R>
 __global__ void k_rate(const EventGeo *__restrict__ ev, const WorkItem *__restrict__ items,
                        int nitems, const R *__restrict__ U, EventClock *__restrict__ clk,
-                       Scheme sc) {
+                       Scheme sc, int sum_axes) {
     __shared__ R red[32];
     R m = R(0);
     int cur_event = -1;
@@ -165,14 +165,18 @@ __global__ void k_rate(const EventGeo *__restrict__ ev, const WorkItem *__restri
             const R cs = dsqrt_(c2);
             const R inv_den = R(1) / (R(1) - v2 * c2);
             const R vd[3] = {vx, vy, vz};
+            R sum = R(0);   // the unsplit scheme's rate: sum over axes (R16c)
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
                 if (!act[d]) continue;
                 R rad = (R(1) - v2) * (R(1) - vd[d] * vd[d] - (v2 - vd[d] * vd[d]) * c2);
                 rad = rad < R(0) ? R(0) : rad;
                 const R a = vd[d] * (R(1) - c2);
-                m = max_nan(m, (fabs_(a) + cs * dsqrt_(rad)) * inv_den * invh[d]);
+                const R r = (fabs_(a) + cs * dsqrt_(rad)) * inv_den * invh[d];
+                if (sum_axes) sum += r;
+                else m = max_nan(m, r);
             }
+            if (sum_axes) m = max_nan(m, sum);
         }
     }
     if (cur_event >= 0) flush_rate<R>(m, cur_event, clk, red);
@@ -439,9 +443,9 @@ cudaError_t launch_cons2prim(const CellLaunch &c, const void *U, void *e, void *
 cudaError_t launch_rate(const CellLaunch &c, const void *U, EventClock *clk, double) {
     HY_DISPATCH(c.prec,
         (k_rate<double><<<c.blocks, c.threads, 0, c.stream>>>(c.ev, c.items, c.nitems,
-            (const double *)U, clk, c.sc)),
+            (const double *)U, clk, c.sc, c.rate_sum)),
         (k_rate<float><<<c.blocks, c.threads, 0, c.stream>>>(c.ev, c.items, c.nitems,
-            (const float *)U, clk, c.sc)));
+            (const float *)U, clk, c.sc, c.rate_sum)));
     return cudaGetLastError();
 }
 

@@ -60,6 +60,19 @@ struct EventClock {
     int pad;
 };
 
+// Per-event layout of the scratch of the unsplit scheme: evolved faces on the
+// box grown by one cell along each active axis, interface fluxes per axis.
+struct UnsplitGeo {
+    long long fo;        // element offset of the event's faces: face (d, side, q) of
+                         // grown cell gi at fo + ((2 d + side) 4 + q) gcells + gi
+    long long gcells;    // cells of the grown box
+    long long xo[3];     // element offset of the axis-d interface fluxes:
+                         // field q of interface ii at xo[d] + q nint[d] + ii
+    long long nint[3];   // interfaces along axis d, (n_d + 1) cells / n_d (0: inactive)
+    int g[3];            // 1 on active axes, else 0
+    int m[3];            // grown box: n + 2 g
+};
+
 // A block's share of a launch: `count` consecutive units of one event
 // starting at `first` (pencil-segment tasks for sweeps, cells otherwise).
 struct WorkItem {

@@ -28,6 +28,31 @@ cudaError_t launch_sweep_f64(const SweepLaunch &a);
 cudaError_t launch_sweep_f32(const SweepLaunch &a);
 cudaError_t launch_sweep_mixed(const SweepLaunch &a);
 
+// One RK stage of the unsplit scheme (Eq. 13 with all flux terms, reading
+// R16): evolved faces, MUSTA-FORCE fluxes per active axis, then the
+// divergence and the stage combination of Eq. 5-7.
+struct UnsplitLaunch {
+    const void *in;          // state the stage differentiates (U^n, U1 or U2)
+    const void *u0;          // U^n
+    const void *u1;          // U1 (stages 2-3), U2 (stage 3 of RK3)
+    void *out;               // the stage result
+    void *faces, *fluxes;    // scratch laid out by UnsplitGeo
+    const EventGeo *ev;
+    const UnsplitGeo *ug;
+    const WorkItem *face_items, *flux_items[3], *cell_items;
+    int n_face_items, n_flux_items[3], n_cell_items;
+    const EventClock *clk;
+    Scheme sc;
+    int rk, stage;           // stage 1..rk
+    EventClock *rate_clk;    // non-null on the last stage: CFL rate (sum over axes) of out
+    int sms;
+    cudaStream_t stream;
+};
+
+cudaError_t launch_unsplit_f64(const UnsplitLaunch &a);
+cudaError_t launch_unsplit_f32(const UnsplitLaunch &a);
+cudaError_t launch_unsplit_mixed(const UnsplitLaunch &a);
+
 // Cell-wise kernels over work items of cells (prec: 0 double, 1/2 float).
 struct CellLaunch {
     const EventGeo *ev;
@@ -38,13 +63,15 @@ struct CellLaunch {
     int prec;             // 0 double, 1 float
     int mixed;            // float state, cons->prim redone in double where |v| > 0.99
     Scheme sc;
+    int rate_sum = 0;     // launch_rate: sum over axes (unsplit scheme) instead of max
 };
 
 cudaError_t launch_prim2cons(const CellLaunch &c, const void *e, const void *vx, const void *vy,
                              const void *vz, void *U);
 cudaError_t launch_cons2prim(const CellLaunch &c, const void *U, void *e, void *vx, void *vy,
                              void *vz);
-// max over cells and swept axes of speed/dx into clk[event].rate_bits (atomic max)
+// max over cells of speed/dx, maximised (or with rate_sum summed) over the swept
+// axes, into clk[event].rate_bits (atomic max)
 cudaError_t launch_rate(const CellLaunch &c, const void *U, EventClock *clk, double cfl_unused);
 // per-event dt from rate_bits (resets it), t_step = t, t += dt
 cudaError_t launch_dt(EventClock *clk, const double *cfl_fixed, int nevents, cudaStream_t s);

@@ -36,7 +36,7 @@ class GridT(C.Structure):
                 ("x0", C.c_double), ("y0", C.c_double), ("z0", C.c_double),
                 ("bc", C.c_int * 3), ("prec", C.c_int), ("rk_order", C.c_int),
                 ("hancock", C.c_int), ("cfl", C.c_double), ("fixed_dt", C.c_double),
-                ("alpha", C.c_double)]
+                ("alpha", C.c_double), ("unsplit", C.c_int)]
 
 
 class EosT(C.Structure):
@@ -163,7 +163,9 @@ def _stream_ptr(stream):
 
 def make_grid(nx, ny=1, nz=1, dx=1.0, dy=None, dz=None, x0=0.0, y0=0.0, z0=0.0,
               bc="periodic", prec="fp64", rk_order=2, hancock=1, cfl=0.4, fixed_dt=0.0,
-              alpha=1.0):
+              alpha=None, unsplit=False):
+    """hydro_grid_t; alpha defaults to 1 for split sweeps and 3 for the
+    unsplit scheme (the paper's 3-D value)."""
     g = GridT()
     g.nx, g.ny, g.nz = nx, ny, nz
     g.dx = dx
@@ -176,7 +178,9 @@ def make_grid(nx, ny=1, nz=1, dx=1.0, dy=None, dz=None, x0=0.0, y0=0.0, z0=0.0,
         g.bc[k] = BCS[bc[k]] if isinstance(bc[k], str) else int(bc[k])
     g.prec = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
     g.rk_order, g.hancock = rk_order, hancock
-    g.cfl, g.fixed_dt, g.alpha = cfl, fixed_dt, alpha
+    g.cfl, g.fixed_dt = cfl, fixed_dt
+    g.alpha = (3.0 if unsplit else 1.0) if alpha is None else alpha
+    g.unsplit = 1 if unsplit else 0
     return g
 
 
