@@ -38,6 +38,8 @@ WORKLOADS = {
     "blast128_fp32": dict(n=128, prec="fp32"),   # small case for ncu captures
     # the paper's production settings (Sec. 3.2): RK3 and 4 MUSTA stages
     "blast256_paper": dict(n=256, prec="fp32", rk=3, stages=4),
+    # the unsplit multi-D scheme (Eq. 13 with every flux term, alpha = 3)
+    "blast256_unsplit": dict(n=256, prec="fp32", unsplit=True),
 }
 BYTES = {"fp32": 4, "fp64": 8}
 # Algorithmic floating-point operations of one sweep per cell (conformal EOS,
@@ -62,7 +64,24 @@ def flops_per_cell_sweep(rk=2, stages=2):
 # DRAM bytes read + written per sweep launch, mean over the five sweeps of one
 # step, from an ncu capture of the current kernels (profiles/
 # sweep_blast256_fp32_step.md); None where no capture of the current kernels exists
-SWEEP_TRAFFIC = {(256, "fp32", 2, 2): 597.3e6}
+SWEEP_TRAFFIC = {(256, "fp32", 2, 2, False): 597.3e6}
+
+
+def flops_per_cell_stage_unsplit(stages=2):
+    """Algorithmic flops of one RK stage of the unsplit scheme per cell, counted
+    like flops_per_cell_sweep: per axis 16 (slopes) + 12 (faces) + 2 x 25
+    (Hancock fluxes) + 8 (their difference); 24 to add the increment to the 6
+    faces and 48 for their admissibility; per axis one interface with
+    3k x 25 + 48k + 24(k-1) + 3; 12 per axis for the divergence."""
+    return 3 * (16 + 12 + 50 + 8) + 24 + 48 + 3 * (75 * stages + 48 * stages +
+                                                   24 * (stages - 1) + 3) + 36
+
+
+def bytes_per_cell_stage_unsplit(elem):
+    """Algorithmic HBM bytes of one unsplit RK stage per cell: 6 faces written
+    and read, 3 interface fluxes written and read, the input state read, the
+    RK inputs read and the result written (4 fields each)."""
+    return (2 * 24 + 2 * 12 + 4 + 8 + 4) * elem
 ALU_PEAK_TFLOPS = {"fp32": 148 * 128 * 2 * 2.032e9 / 1e12, "fp64": 1.25}
 
 
@@ -140,13 +159,14 @@ def dist_setup():
     return world, rank, local
 
 
-def cpu_baseline_oracle(n=96, steps=1, rk=2, stages=2):
+def cpu_baseline_oracle(n=96, steps=1, rk=2, stages=2, unsplit=False):
     """The oracle, as it stands, on a bounded sample: the blast recipe on n^3."""
     from oracle import oracle as O
     from paper_1510_06340_b300 import inputs as I
     g, prim = I.spherical_blast(n)
     o = O.Oracle(n, n, n, dx=g["dx"], x0=-1.0, y0=-1.0, z0=-1.0, bc="periodic",
-                 limiter="minmod", stages=stages, rk_order=rk, cfl=0.4)
+                 limiter="minmod", stages=stages, rk_order=rk, cfl=0.4,
+                 alpha=3.0 if unsplit else 1.0, unsplit=int(unsplit))
     U = o.prim2cons_field(*prim)
     t0 = time.perf_counter()
     o.run(U, steps)
@@ -200,13 +220,14 @@ def run_ours(args):
     wl = WORKLOADS[args.workload]
     n, prec = wl["n"], wl["prec"]
     rk, stages = wl.get("rk", 2), wl.get("stages", 2)
+    unsplit = wl.get("unsplit", False)
     flops_cell_sweep = flops_per_cell_sweep(rk, stages)
     dt_np = np.float64 if prec == "fp64" else np.float32
     g, prim = I.spherical_blast(n)
     prim = [np.ascontiguousarray(a, dtype=dt_np) for a in prim]
     stream = torch.cuda.Stream()
     grid = hydro.make_grid(n, n, n, dx=g["dx"], x0=-1.0, y0=-1.0, z0=-1.0, bc="periodic",
-                           prec=prec, cfl=0.4, rk_order=rk)
+                           prec=prec, cfl=0.4, rk_order=rk, unsplit=unsplit)
     h = hydro.Hydro(grid, limiter="minmod", stages=stages, stream=stream)
     h.set_primitives(*prim)
     cells = n ** 3
@@ -224,6 +245,7 @@ def run_ours(args):
     h.kernel_timing()   # reset
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    t_sim0 = h.time()
     with Clocks(local) as clk:
         if world > 1:
             dist.barrier()
@@ -235,6 +257,7 @@ def run_ours(args):
         if world > 1:
             dist.barrier()
     ms = e0.elapsed_time(e1)
+    t_sim = h.time() - t_sim0
     (sweep_ms, other_ms), (n_sweep, n_other) = h.kernel_timing()
     shapes = [h.get_launch(ax) for ax in range(3)]
     h.set_kernel_timing(False)
@@ -263,18 +286,27 @@ def run_ours(args):
     state_bytes = 4 * cells * BYTES[prec]
 
     hbm, src = peaks()
-    bytes_per_sweep = 2 * 4 * BYTES[prec] * cells      # read + write of 4 fields
     avg_sweep_ms = sweep_ms / max(n_sweep, 1)
+    if unsplit:
+        # a timed group is one RK stage: faces, 3 flux launches, update
+        bytes_per_sweep = bytes_per_cell_stage_unsplit(BYTES[prec]) * cells
+        flops_per_group = flops_per_cell_stage_unsplit(stages) * cells
+        launches = 5 * n_sweep + n_other
+        kernel_name = "unsplit RK stage (k_us_faces, 3 x k_us_flux, k_us_update)"
+    else:
+        bytes_per_sweep = 2 * 4 * BYTES[prec] * cells      # read + write of 4 fields
+        flops_per_group = flops_cell_sweep * cells
+        # per step: 5 sweeps + k_dt (the CFL rate is fused into the last sweep)
+        launches = n_sweep + n_other
+        kernel_name = "k_sweep (one directional sweep, all RK stages)"
     achieved = bytes_per_sweep / (avg_sweep_ms * 1e-3) / 1e9
-    # per step: 5 sweeps + k_dt (the CFL rate is fused into the last sweep)
-    launches = n_sweep + n_other
     alu_peak = ALU_PEAK_TFLOPS[prec]
-    flops_achieved = flops_cell_sweep * cells / (avg_sweep_ms * 1e-3) / 1e12
+    flops_achieved = flops_per_group / (avg_sweep_ms * 1e-3) / 1e12
 
     cpu = None
     if rank == 0 and world >= 1 and not args.no_cpu:
         nb = 96 if (rk, stages) == (2, 2) else 64   # about the same seconds of CPU work
-        v, el, sample = cpu_baseline_oracle(nb, 1, rk, stages)
+        v, el, sample = cpu_baseline_oracle(nb, 1, rk, stages, unsplit)
         cpu = {"value": v, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
                "sample": sample + f", {el:.1f} s"}
     if rank == 0:
@@ -286,16 +318,18 @@ def run_ours(args):
             "data": "synthetic",
             "config": {"workload": f"3D spherical blast {n}^3 on [-1,1]^3, p=e/3, "
                                    f"{prec.upper()}, minmod, {stages} MUSTA stages, "
-                                   f"RK{rk}+Hancock, Strang, periodic, CFL 0.4",
+                                   f"RK{rk}+Hancock, "
+                                   f"{'unsplit, alpha 3' if unsplit else 'Strang'}, periodic, "
+                                   "CFL 0.4",
                        "cells": cells, "parallelism": f"replicas x{world}",
                        "launch_threads_segments_xyz": shapes,
                        "l2": "inputs larger than L2 (two state copies of "
                              f"{state_bytes / 1e6:.0f} MB)"},
             "roofline": {"bound": "alu", "achieved": flops_achieved, "peak": alu_peak,
                          "unit": "TFLOP/s", "frac": flops_achieved / alu_peak,
-                         "traffic": SWEEP_TRAFFIC.get((n, prec, rk, stages)),
-                         "kernel": "k_sweep (one directional sweep, all RK stages)",
-                         "algorithmic_flops_per_launch": flops_cell_sweep * cells,
+                         "traffic": SWEEP_TRAFFIC.get((n, prec, rk, stages, unsplit)),
+                         "kernel": kernel_name,
+                         "algorithmic_flops_per_launch": flops_per_group,
                          "avg_launch_ms": avg_sweep_ms,
                          "peak_source": "derived: 148 SM x 128 lanes x 2 x 2.032 GHz (fp32); "
                                         "nominal 1.25 TFLOP/s (fp64)"},
@@ -306,6 +340,7 @@ def run_ours(args):
             "kernel_ms": {"sweeps": sweep_ms, "sweep_launches": n_sweep,
                           "rate_dt": other_ms, "rate_dt_groups": n_other},
             "gpu_launches": launches,
+            "physical_time_per_s": t_sim / (ms * 1e-3),
             "e2e": {"value": e2e_value, "unit": "cell-updates/s",
                     "h2d_bytes_per_step": state_bytes / args.steps,
                     "d2h_bytes_per_step": 32 + state_bytes / args.steps},

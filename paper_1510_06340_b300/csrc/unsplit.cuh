@@ -73,18 +73,24 @@ k_us_faces(const R *__restrict__ in, R *__restrict__ faces, const EventGeo *__re
         // lanes past the item's end repeat its first unit and store nothing,
         // so a warp stays converged (the MLP Newton seed needs that)
         const bool valid = int(threadIdx.x) < w.count;
-        const long long gi = w.first + (valid ? threadIdx.x : 0);
-        const long long m01 = (long long)u.m[0] * u.m[1];
-        const int x[3] = {int(gi % u.m[0]) - u.g[0], int((gi / u.m[0]) % u.m[1]) - u.g[1],
-                          int(gi / m01) - u.g[2]};
+        // grown boxes hold fewer than 2^31 cells: 32-bit index arithmetic
+        const unsigned gi = unsigned(w.first) + (valid ? threadIdx.x : 0u);
+        const unsigned m0 = unsigned(u.m[0]), m1 = unsigned(u.m[1]);
+        const unsigned r = gi / m0;
+        const int x[3] = {int(gi - r * m0) - u.g[0], int(r % m1) - u.g[1], int(r / m1) - u.g[2]};
         const double dt = clk[w.event].dt;
+        // a coordinate at most 2 cells outside [0, n): one wrap or clamp
+        auto fold = [&](int j, int a) {
+            const int n = g.n[a];
+            if (g.bc[a] == BC_OUTFLOW) return j < 0 ? 0 : (j >= n ? n - 1 : j);
+            return j < 0 ? j + n : (j >= n ? j - n : j);
+        };
         auto cell = [&](int d, int o) {   // the cell o steps from x along axis d
             int y[3] = {x[0], x[1], x[2]};
             y[d] += o;
-            const int a = wrap_index(y[0], g.n[0], g.bc[0]);
-            const int b = wrap_index(y[1], g.n[1], g.bc[1]);
-            const int c = wrap_index(y[2], g.n[2], g.bc[2]);
-            return us_load(in, g, a + (long long)g.n[0] * (b + (long long)g.n[1] * c));
+            const int a = fold(y[0], 0), b = fold(y[1], 1), c = fold(y[2], 2);
+            return us_load(in, g, (long long)(unsigned(a) + unsigned(g.n[0]) *
+                                              (unsigned(b) + unsigned(g.n[1]) * unsigned(c))));
         };
         const V4<R> V0 = cell(0, 0);
         V4<R> UL[3], UR[3];
@@ -127,7 +133,8 @@ k_us_faces(const R *__restrict__ in, R *__restrict__ faces, const EventGeo *__re
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
                 if (!u.g[d]) continue;
-                R *fl = us_face(faces, u, d, 0, gi), *fr = us_face(faces, u, d, 1, gi);
+                R *fl = us_face(faces, u, d, 0, (long long)gi);
+                R *fr = us_face(faces, u, d, 1, (long long)gi);
                 fl[0] = UL[d].e; fl[u.gcells] = UL[d].n;
                 fl[2 * u.gcells] = UL[d].t1; fl[3 * u.gcells] = UL[d].t2;
                 fr[0] = UR[d].e; fr[u.gcells] = UR[d].n;
@@ -137,16 +144,20 @@ k_us_faces(const R *__restrict__ in, R *__restrict__ faces, const EventGeo *__re
     }
 }
 
-// interface index ii along axis d -> (position p of the interface p - 1/2,
-// logical coordinates of the cell on its right)
-__device__ __forceinline__ void us_interface(const EventGeo &g, int d, long long ii, int x[3]) {
-    const int nd = g.n[d];
-    const int p = int(ii % (nd + 1));
-    const long long t = ii / (nd + 1);
-    const int a = d == 0 ? 1 : 0, b = d == 2 ? 1 : 2;   // transverse axes, increasing
-    x[d] = p;
-    x[a] = int(t % g.n[a]);
-    x[b] = int(t / g.n[a]);
+// Interfaces along axis d are numbered x fastest on the grid extended by one
+// cell along d: interface (x, y, z) lies between the cell one step before it
+// along d and the cell (x, y, z), so neighbouring threads touch neighbouring
+// memory for every axis.
+__device__ __forceinline__ unsigned us_iface_index(const EventGeo &g, int d, int x, int y, int z) {
+    const unsigned e0 = unsigned(g.n[0] + (d == 0)), e1 = unsigned(g.n[1] + (d == 1));
+    return unsigned(x) + e0 * (unsigned(y) + e1 * unsigned(z));
+}
+__device__ __forceinline__ void us_interface(const EventGeo &g, int d, unsigned ii, int x[3]) {
+    const unsigned e0 = unsigned(g.n[0] + (d == 0)), e1 = unsigned(g.n[1] + (d == 1));
+    const unsigned r = ii / e0;
+    x[0] = int(ii - r * e0);
+    x[1] = int(r % e1);
+    x[2] = int(r / e1);
 }
 
 template <class R, int PREC, int EOSK, bool COUNT>
@@ -161,7 +172,7 @@ k_us_flux(const R *__restrict__ faces, R *__restrict__ fluxes, const EventGeo *_
         const EventGeo &g = ev[w.event];
         const UnsplitGeo &u = ugeo[w.event];
         const bool valid = int(threadIdx.x) < w.count;
-        const long long ii = w.first + (valid ? threadIdx.x : 0);
+        const unsigned ii = unsigned(w.first) + (valid ? threadIdx.x : 0u);
         int x[3];
         us_interface(g, d, ii, x);
         // grown-box indices of the cells left (p - 1) and right (p) of the interface
@@ -213,22 +224,22 @@ k_us_update(const R *__restrict__ u0, const R *__restrict__ u1, R *__restrict__ 
             ih[d] = R(g.inv_h[d]);
         }
         R m = R(0);
+        const unsigned n0 = unsigned(g.n[0]), n1 = unsigned(g.n[1]);
         for (int k = threadIdx.x; k < w.count; k += blockDim.x) {
             const long long c = w.first + k;
-            const int x[3] = {int(c % g.n[0]), int((c / g.n[0]) % g.n[1]),
-                              int(c / ((long long)g.n[0] * g.n[1]))};
+            const unsigned cu = unsigned(c), row = cu / n0;
+            const int x = int(cu - row * n0), y = int(row % n1), z = int(row / n1);
             // dt L(U) = -D, D = sum_d dt/dx_d (F_d,i+1/2 - F_d,i-1/2), axes in order
             V4<R> D = v4<R>(R(0), R(0), R(0), R(0));
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
                 if (!u.g[d]) continue;
-                const int a = d == 0 ? 1 : 0, b = d == 2 ? 1 : 2;
-                const long long ii =
-                    x[d] + (long long)(g.n[d] + 1) * (x[a] + (long long)g.n[a] * x[b]);
-                const R *f = fluxes + u.xo[d] + ii;
+                const unsigned im = us_iface_index(g, d, x, y, z);
+                const unsigned ip = us_iface_index(g, d, x + (d == 0), y + (d == 1), z + (d == 2));
+                const R *f = fluxes + u.xo[d];
                 const long long s = u.nint[d];
-                const V4<R> Fm = v4<R>(f[0], f[s], f[2 * s], f[3 * s]);
-                const V4<R> Fp = v4<R>(f[1], f[s + 1], f[2 * s + 1], f[3 * s + 1]);
+                const V4<R> Fm = v4<R>(f[im], f[s + im], f[2 * s + im], f[3 * s + im]);
+                const V4<R> Fp = v4<R>(f[ip], f[s + ip], f[2 * s + ip], f[3 * s + ip]);
                 D = vfma<R>(lam[d], vsub(Fp, Fm), D);
             }
             const V4<R> U0 = us_load(u0, g, c);
