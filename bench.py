@@ -50,13 +50,15 @@ BYTES = {"fp32": 4, "fp64": 8}
 FLOPS_PER_CELL_SWEEP = 800
 
 
-def flops_per_cell_sweep(rk=2, stages=2):
+def flops_per_cell_sweep(rk=2, stages=2, limiter="minmod"):
     """The same count for any RK order and MUSTA stage number k: per RK stage
     (2 + 3k) cons->prim + flux evaluations of 25 flops, 61 for slopes, faces,
     Hancock and admissibility, 48 per MUSTA stage and 24 per predictor update
     plus 3, and 4 for the divergence; RK combinations 24 (RK2) or 48 (RK3),
-    8 for RK1.  (rk, k) = (2, 2) gives 800."""
-    per_stage = (2 + 3 * stages) * 25 + 61 + 48 * stages + 24 * (stages - 1) + 3 + 4
+    8 for RK1.  (rk, k) = (2, 2) gives 800.  MC and Superbee take 12 flops per
+    field for the limited slope where Minbee takes 4."""
+    lim_extra = 0 if limiter == "minmod" else 4 * 8
+    per_stage = (2 + 3 * stages) * 25 + 61 + lim_extra + 48 * stages + 24 * (stages - 1) + 3 + 4
     combine = {1: 8, 2: 24, 3: 48}[rk]
     return rk * per_stage + combine
 # FP32 (non-tensor) peak from unit counts and clock: 148 SMs x 128 FP32 lanes x
@@ -159,13 +161,13 @@ def dist_setup():
     return world, rank, local
 
 
-def cpu_baseline_oracle(n=96, steps=1, rk=2, stages=2, unsplit=False):
+def cpu_baseline_oracle(n=96, steps=1, rk=2, stages=2, unsplit=False, limiter="minmod"):
     """The oracle, as it stands, on a bounded sample: the blast recipe on n^3."""
     from oracle import oracle as O
     from paper_1510_06340_b300 import inputs as I
     g, prim = I.spherical_blast(n)
     o = O.Oracle(n, n, n, dx=g["dx"], x0=-1.0, y0=-1.0, z0=-1.0, bc="periodic",
-                 limiter="minmod", stages=stages, rk_order=rk, cfl=0.4,
+                 limiter=limiter, stages=stages, rk_order=rk, cfl=0.4,
                  alpha=3.0 if unsplit else 1.0, unsplit=int(unsplit))
     U = o.prim2cons_field(*prim)
     t0 = time.perf_counter()
@@ -221,14 +223,14 @@ def run_ours(args):
     n, prec = wl["n"], wl["prec"]
     rk, stages = wl.get("rk", 2), wl.get("stages", 2)
     unsplit = wl.get("unsplit", False)
-    flops_cell_sweep = flops_per_cell_sweep(rk, stages)
+    flops_cell_sweep = flops_per_cell_sweep(rk, stages, args.limiter)
     dt_np = np.float64 if prec == "fp64" else np.float32
     g, prim = I.spherical_blast(n)
     prim = [np.ascontiguousarray(a, dtype=dt_np) for a in prim]
     stream = torch.cuda.Stream()
     grid = hydro.make_grid(n, n, n, dx=g["dx"], x0=-1.0, y0=-1.0, z0=-1.0, bc="periodic",
                            prec=prec, cfl=0.4, rk_order=rk, unsplit=unsplit)
-    h = hydro.Hydro(grid, limiter="minmod", stages=stages, stream=stream)
+    h = hydro.Hydro(grid, limiter=args.limiter, stages=stages, stream=stream)
     h.set_primitives(*prim)
     cells = n ** 3
     if args.launch:
@@ -306,7 +308,7 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world >= 1 and not args.no_cpu:
         nb = 96 if (rk, stages) == (2, 2) else 64   # about the same seconds of CPU work
-        v, el, sample = cpu_baseline_oracle(nb, 1, rk, stages, unsplit)
+        v, el, sample = cpu_baseline_oracle(nb, 1, rk, stages, unsplit, args.limiter)
         cpu = {"value": v, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
                "sample": sample + f", {el:.1f} s"}
     if rank == 0:
@@ -317,7 +319,7 @@ def run_ours(args):
             "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "f64",
             "data": "synthetic",
             "config": {"workload": f"3D spherical blast {n}^3 on [-1,1]^3, p=e/3, "
-                                   f"{prec.upper()}, minmod, {stages} MUSTA stages, "
+                                   f"{prec.upper()}, {args.limiter}, {stages} MUSTA stages, "
                                    f"RK{rk}+Hancock, "
                                    f"{'unsplit, alpha 3' if unsplit else 'Strang'}, periodic, "
                                    "CFL 0.4",
@@ -327,7 +329,8 @@ def run_ours(args):
                              f"{state_bytes / 1e6:.0f} MB)"},
             "roofline": {"bound": "alu", "achieved": flops_achieved, "peak": alu_peak,
                          "unit": "TFLOP/s", "frac": flops_achieved / alu_peak,
-                         "traffic": SWEEP_TRAFFIC.get((n, prec, rk, stages, unsplit)),
+                         "traffic": (SWEEP_TRAFFIC.get((n, prec, rk, stages, unsplit))
+                                     if args.limiter == "minmod" else None),
                          "kernel": kernel_name,
                          "algorithmic_flops_per_launch": flops_per_group,
                          "avg_launch_ms": avg_sweep_ms,
@@ -643,6 +646,8 @@ def main():
     ap.add_argument("--events", type=int, default=512, help="events per GPU (batch512)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--launch", default="", help="force 'threads,segments' for every axis")
+    ap.add_argument("--limiter", default="minmod", choices=["minmod", "mc", "superbee"],
+                    help="slope limiter of the blast workloads")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer e2e pass")
     args = ap.parse_args()
     if args.warmup < 3:
