@@ -56,6 +56,11 @@
  *      cells of sum_d max|lam_d| / dx_d over the axes with more than one cell;
  *      (d) the RK stages of Eq. 6-7 act on the whole field, with
  *      dt L(U) = - sum_d dt/dx_d (F_d,i+1/2 - F_d,i-1/2).
+ *  R17 Ellipsoidal flow (Sec. 3.2): v_i = a_i x_i / t (the printed order
+ *      a_1, a_3, a_2 of the velocity is read as a typo; tau pairs a_i with x_i).
+ *  R18 Vacuum threshold: a cell with E <= 2^-500 is vacuum (v = p = 0), so that
+ *      E^2 and M^2 in the cons->prim formulas stay normal numbers; below it the
+ *      closed form of R10 loses all digits (E^2 underflows).
  */
 #include <math.h>
 #include <stdlib.h>
@@ -293,7 +298,7 @@ int or_cons2prim(const or_config *c, const double U[4], double *e_out, double v[
     double M2 = Mx * Mx + My * My + Mz * Mz;
     int status = 0;
     if (iters) *iters = 0;
-    if (!(E > 0.0)) {
+    if (!(E > 0x1p-500)) {            /* vacuum (R9, R18) */
         v[0] = v[1] = v[2] = 0.0;
         *p_out = 0.0; *e_out = 0.0;
         return 2;

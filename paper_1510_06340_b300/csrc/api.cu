@@ -55,6 +55,8 @@ static void set_consts(SchemeConsts<R> &k, R alpha, R delta, R cs2) {
     k.k1 = R(1) - cs2;
     k.hapc = R(0.5) * (R(1) + cs2);
     k.hapc2 = k.hapc * k.hapc;
+    k.emin = sizeof(R) == 8 ? R(std::ldexp(1.0, -500)) : R(std::ldexp(1.0, -60));
+    k.wmin = k.hapc * k.emin;
 }
 
 struct Solver {

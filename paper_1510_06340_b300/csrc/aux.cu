@@ -26,7 +26,7 @@ __device__ __forceinline__ void c2p_full(const Scheme &sc, R E, R Mx, R My, R Mz
     iters = 0;
     const R delta = R(sc.delta);
     R M2 = Mx * Mx + My * My + Mz * Mz;
-    if (!(E > R(0))) { e = R(0); vx = vy = vz = R(0); return; }
+    if (!(E > consts<R>(sc).emin)) { e = R(0); vx = vy = vz = R(0); return; }   // vacuum (R18)
     const R cap = (R(1) - delta) * E;
     R s = R(1);
     if (M2 > cap * cap) {

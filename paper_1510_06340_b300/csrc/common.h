@@ -96,6 +96,9 @@ struct SchemeConsts {
     R hapc;    // (1 + c^2) / 2
     R hapc2;   // ((1 + c^2) / 2)^2
     R lne_min, inv_h, e_max;   // tabulated EOS: first node, 1 / node spacing, last e
+    R emin;    // vacuum threshold: E <= emin is vacuum (2^-500 FP64, 2^-60 FP32),
+               // where E^2 is still a normal number
+    R wmin;    // (1 + c^2)/2 emin: W = E + p at or below it means E <= emin
 };
 
 struct Scheme {

@@ -152,7 +152,9 @@ __device__ __forceinline__ Prim<R> c2p_conformal(const V4<R> &U, const SchemeCon
                                                  bool counting) {
     Prim<R> q;
     // E <= 0 is vacuum (v = p = 0): with E clamped to 0 the cap forces M2c = 0,
-    // so W = p = 0 follow from the same formulas and only 1/W needs a guard
+    // so W = p = 0 follow from the same formulas and only 1/W needs a guard.
+    // So is E <= emin, where E^2 underflows (R18): there W <= (1+c2)/2 E
+    // falls under wmin and the velocity is set to 0 by the same guard.
     const R E = fmax_(U.e, R(0));
     const R M2 = fma_(U.t2, U.t2, fma_(U.t1, U.t1, U.n * U.n));
     const R E2 = E * E;
@@ -161,7 +163,7 @@ __device__ __forceinline__ Prim<R> c2p_conformal(const V4<R> &U, const SchemeCon
     // W^2 - (1+c2) E W + c2 M^2 = 0: W = (1+c2)/2 E + sqrt(((1+c2)/2)^2 E^2 - c2 M^2),
     // the discriminant being positive for |M| < E
     const R W = fma_(k.hapc, E, dsqrt_(fma_(-k.cs2, M2c, k.hapc2 * E2)));
-    R inv = W > R(0) ? rcp_(W) : R(0);
+    R inv = W > k.wmin ? rcp_(W) : R(0);
     // energy flux (E + p) v_n = W (s M_n / W) = s M_n
     R fe = U.n;
     if (M2 > cap2) {      // |M| capped at (1 - delta) E (R9): v = s M / W
@@ -302,7 +304,10 @@ __device__ __forceinline__ Prim<R> c2p_table(const V4<R> &U, R delta, const Sche
         given = R(mlp_seed_warp(sc, __logf(Ef), xf));
         seed = SEED_GIVEN;
     }
-    if (!(E > R(0))) { q.vn = R(0); q.p = R(0); q.W = R(0); q.fe = R(0); vmag = R(0); return q; }
+    if (!(E > consts<R>(sc).emin)) {   // vacuum (R9, R18)
+        q.vn = R(0); q.p = R(0); q.W = R(0); q.fe = R(0); vmag = R(0);
+        return q;
+    }
     const R cap = (R(1) - delta) * E;
     const R Mfull = dsqrt_(M2f);
     R M2 = M2f, M = Mfull;
@@ -403,7 +408,7 @@ struct Physics {
             const R cap2 = k.capf * E2;
             const R M2c = fmin_(M2, cap2);
             const R W = fma_(k.hapc, E, dsqrt_(fma_(-k.cs2, M2c, k.hapc2 * E2)));
-            const R inv = W > R(0) ? rcp_(W) : R(0);
+            const R inv = W > k.wmin ? rcp_(W) : R(0);   // vacuum: v = 0, speed c
             R am = fabs_(U.n);
             if (ih_t1 > R(0)) am = fmax_(am, fabs_(U.t1));
             if (ih_t2 > R(0)) am = fmax_(am, fabs_(U.t2));
@@ -413,12 +418,21 @@ struct Physics {
             const R D = fma_(-v2, k.cs2, R(1));
             const R rad = fmax_((R(1) - v2) * fma_(-a * a, k.k1, D), R(0));
             const R lam = fma_(k.cs, dsqrt_(rad), a * k.k1) * rcp_(D);
-            return U.e > R(0) ? lam * ih_n : R(0);
+            return lam * ih_n;
         }
         const R E = U.e;
         const R cs2 = K().cs2;
         R M2 = U.n * U.n + U.t1 * U.t1 + U.t2 * U.t2;
-        if (!(E > R(0))) return R(0);
+        if (!(E > K().emin)) {   // vacuum: v = 0, e = 0, the speed of sound of e = 0
+            R p0, c20;
+            if (EOSK == EOS_CONFORMAL) c20 = cs2;
+            else eos_table<R>(sc, R(0), p0, c20);
+            const R m0 = dsqrt_(c20);
+            R m = m0 * ih_n;
+            if (ih_t1 > R(0)) m = fmax_(m, m0 * ih_t1);
+            if (ih_t2 > R(0)) m = fmax_(m, m0 * ih_t2);
+            return m;
+        }
         const R cap2 = K().capf * E * E;
         R s = R(1);
         if (M2 > cap2) {

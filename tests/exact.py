@@ -91,3 +91,23 @@ def hubble(r, t, e0=1.0, tau0=4.0, c2=1.0 / 3.0):
     r = np.asarray(r, dtype=np.float64)
     tau = np.sqrt(t * t - r * r)
     return e0 * (tau0 / tau) ** (3.0 * (1.0 + c2)), r / t
+
+
+def ellipsoidal(coords, t, C=2.0, b=1.0, T=(0.4, 0.6, 0.8)):
+    """The ellipsoidal flow of Sec. 3.2 (pressureless, p = 0): with
+    a_i = t/(t + T_i), v_i = a_i x_i / t = x_i/(t + T_i) (reading R17: the
+    printed index order of v is taken as a typo, tau pairs a_i with x_i) and
+    tau^2 = t^2 - sum_i a_i^2 x_i^2,
+        e = C / prod_i(t + T_i) * exp(-b^2 t^2 / tau^2)  inside tau^2 > 0,
+    vacuum (e = v = 0) outside.  Every element moves ballistically (t/tau is
+    its Lorentz factor, constant along the motion) and the lab-frame density
+    e gamma scales with the inverse volume prod_i(t + T_i) of the expansion,
+    so E and M solve the p = 0 equations exactly.  coords: one array per
+    active axis (1, 2 or 3 of them, broadcastable), with T[i] for axis i."""
+    v = [np.asarray(x, dtype=np.float64) / (t + T[i]) for i, x in enumerate(coords)]
+    v2 = sum(vi * vi for vi in v)
+    inside = v2 < 1.0
+    gamma2 = np.where(inside, 1.0 / np.where(inside, 1.0 - v2, 1.0), 0.0)
+    norm = C / np.prod([t + T[i] for i in range(len(coords))])
+    e = np.where(inside, norm * np.exp(-b * b * gamma2), 0.0)
+    return e, [np.where(inside, vi, 0.0) for vi in v]

@@ -137,6 +137,24 @@ def test_cons2prim_caps_and_vacuum():
     assert st == 2 and p == 0 and not v.any()
 
 
+def test_cons2prim_is_scale_free_down_to_the_vacuum_threshold():
+    """R18: the p = c2 e recovery is homogeneous (v of lambda U equals v of U,
+    p scales with lambda) down to E = 2^-500, where E^2 is still normal; below
+    it the state is vacuum.  Without the threshold E ~ 1e-323 gave |v| > 1."""
+    for cs2 in (0.0, 1.0 / 3.0):
+        o = O.Oracle(4, cs2=cs2)
+        U = np.array([1.0, 0.5, 0.3, 0.2])
+        e1, v1, p1, _, _ = o.cons2prim(U)
+        for k in (-200, -450, -499):
+            s = 2.0 ** k
+            e2, v2, p2, st, _ = o.cons2prim(U * s)
+            assert st == 0 and np.allclose(v2, v1, rtol=1e-14, atol=0)
+            assert p2 == pytest.approx(p1 * s, rel=1e-13, abs=0)
+        for E in (2.0 ** -501, 1e-300, 2.47e-323):
+            e, v, p, st, _ = o.cons2prim(np.array([E, 0.4 * E, 0.0, 0.8 * E]))
+            assert st == 2 and p == 0 and not v.any()
+
+
 @pytest.mark.parametrize("d", [0, 1, 2])
 def test_flux_is_row_of_boosted_tensor(d):
     """Eq. 3: F_d = (T^{d0}, T^{dx}, T^{dy}, T^{dz})."""
@@ -587,3 +605,31 @@ def test_unsplit_hubble_expansion_interior_converges():
     e2, v2 = hubble_error(64, 0.05, 0.01, 30, alpha=3.0, unsplit=1)
     assert e1 < 0.04 and v1 < 0.01
     assert e2 < e1 / 2 and v2 < v1 / 2
+
+
+# ------------------------------------------- the paper's ellipsoidal flow (R17)
+def ellipsoidal_1d_error(n, t0=2.0, t1=2.4, half=3.0):
+    """The ellipsoidal flow of Sec. 3.2 along one axis (pressureless, c_s^2 = 0,
+    vacuum outside |v| < 1) from t0 to t1; relative L1 error of e in |x| < 1.2."""
+    dx = 2 * half / n
+    x = I.cell_centres(n, -half, dx)
+    e, (v,) = exact.ellipsoidal([x], t0)
+    dt = 0.2 * dx
+    steps = int(round((t1 - t0) / dt))
+    o = O.Oracle(n, dx=dx, x0=-half, bc="outflow", cs2=0.0, fixed_dt=dt)
+    z = np.zeros((1, 1, n))
+    U = o.prim2cons_field(e.reshape(1, 1, n), v.reshape(1, 1, n), z, z)
+    o.run(U, steps)
+    en = o.cons2prim_field(U)[0].ravel()
+    ex, _ = exact.ellipsoidal([x], t0 + steps * dt)
+    core = np.abs(x) < 1.2
+    return np.abs(en[core] - ex[core]).sum() / ex[core].sum()
+
+
+def test_ellipsoidal_flow_1d_converges_to_the_exact_dust_solution():
+    """p = 0 (the conformal EOS with c_s^2 = 0) keeps the exact ballistic
+    expansion: the error is small and falls under refinement."""
+    e1 = ellipsoidal_1d_error(120)
+    e2 = ellipsoidal_1d_error(240)
+    assert e1 < 2e-3
+    assert e2 < e1 / 1.8
