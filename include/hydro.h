@@ -130,7 +130,9 @@ hydro_status hydro_set_primitives(hydro_t *h, const void *e, const void *vx, con
 /* Set / read the conserved state U[4][nz][ny][nx]. */
 hydro_status hydro_set_conserved(hydro_t *h, const void *U, int on_device);
 hydro_status hydro_get_conserved(hydro_t *h, void *U, int on_device);
-/* Read primitives e, vx, vy, vz (cons->prim of Eq. 23 on the device). */
+/* Read primitives e, vx, vy, vz (cons->prim of Eq. 23 on the device).  A cell
+ * with E <= 2^-500 (FP64) or 2^-60 (FP32, mixed) reads as vacuum, e = v = 0:
+ * below that E^2 underflows in the recovery. */
 hydro_status hydro_get_primitives(hydro_t *h, void *e, void *vx, void *vy, void *vz,
                                   int on_device);
 
@@ -147,11 +149,13 @@ hydro_status hydro_set_jet(hydro_t *h, const double jet[8]);
 hydro_status hydro_step(hydro_t *h, int nsteps, double t_end, double *t_out);
 
 /* One directional sweep (axis 0, 1, 2) of length dt: all RK stages of Sec. 2.3
- * over every pencil along that axis.  Used to check single sweeps. */
+ * over every pencil along that axis.  Used to check single sweeps; it runs the
+ * split sweep even on a handle created with unsplit = 1. */
 hydro_status hydro_sweep(hydro_t *h, int axis, double dt);
 
-/* max over cells and swept axes of (largest characteristic speed) / dx: the
- * CFL step is cfl / rate. */
+/* max over cells of (largest characteristic speed) / dx, taken as the max over
+ * the swept axes (split sweeps) or their sum (unsplit = 1): the CFL step is
+ * cfl / rate.  A vacuum cell contributes c_s / dx. */
 hydro_status hydro_max_rate(hydro_t *h, double *rate);
 
 /* FP64 sums over cells of E dV, Mx dV, My dV, Mz dV. */
@@ -190,8 +194,9 @@ hydro_status hydro_conservation_sums_noalloc(const void *U, int prec, int nx, in
 /* ---------------------------------------------------------------- batch of events */
 
 /* nevents independent grids (each may differ in size; all share precision,
- * scheme, EOS, limiter and stages, taken from grids[0]).  State of all events
- * lives in one device allocation. */
+ * scheme, EOS, limiter and stages, taken from grids[0]; HYDRO_E_INVALID when
+ * their unsplit flags differ).  State of all events lives in one device
+ * allocation. */
 hydro_status hydro_batch_create(const hydro_grid_t *grids, int nevents, const hydro_eos_t *eos,
                                 int limiter, int stages, hydro_batch_t **out);
 void hydro_batch_destroy(hydro_batch_t *b);
