@@ -648,8 +648,9 @@ __device__ __forceinline__ void shift_in(V4<R> (&q)[DEPTH], const V4<R> &v) {
 // Cells [s0, s_end) are stored; the segment's nominal length L may run past
 // the pencil end (those cells are computed with wrapped or clamped inputs and
 // not stored).
-// Rate of the stored cells for the next step's CFL dt (ih = 1/dx per slot;
-// ih.x > 0 switches it on); all lanes evaluate it, stored cells count.
+// The CFL rate for the next step's dt (ih = 1/dx per slot; ih_n > 0 switches
+// it on) is evaluated for the stored cells only, in lane-divergent code, which
+// is why rate() never uses the warp-wide MLP seed.
 template <class R>
 struct RateAcc {
     R ih_n, ih_t1, ih_t2;
