@@ -96,6 +96,7 @@ struct Solver {
     unsigned long long *d_counters = nullptr;
     bool counters_on = false;
     bool any_jet = false;
+    long long jet_cells = 0;   // largest box of cells around a jet (k_jet threads per event)
     bool active[3] = {false, false, false};
     cudaStream_t stream = nullptr;
     cudaStream_t own_stream = nullptr;   // used until the caller sets a stream
@@ -178,6 +179,8 @@ struct Solver {
         c.mixed = prec == HYDRO_MIXED ? 1 : 0;
         c.sc = scheme();
         c.rate_sum = unsplit ? 1 : 0;
+        c.jet_cells = jet_cells;
+        c.nevents = nevents;
         return c;
     }
 
@@ -851,6 +854,15 @@ struct Solver {
         for (int e = 0; e < nevents; ++e) {
             memcpy(geo[e].jet, jets + 8 * e, 8 * sizeof(double));
             geo[e].jet_on = 1;
+            const double sig = geo[e].jet[7];
+            if (!(sig > 0.0)) return fail(HYDRO_E_INVALID, "jet width must be > 0");
+            // as k_jet: at most min(2 (ceil(9 sigma / h) + 1) + 1, n) cells per active axis
+            long long box = 1;
+            for (int a = 0; a < 3; ++a)
+                if (geo[e].n[a] > 1)
+                    box *= std::min<long long>(
+                        2 * ((long long)std::ceil(9.0 * sig / geo[e].h[a]) + 1) + 1, geo[e].n[a]);
+            jet_cells = std::max(jet_cells, box);
         }
         any_jet = true;
         graph_dirty = true;

@@ -203,48 +203,70 @@ __global__ void k_dt(EventClock *__restrict__ clk, double cfl, double fixed_dt, 
 // ------------------------------------------------------------------ jet source
 // reading R12: U += dt S(t_step), S = dEdx (1, n) g(x - x0 - n t), in the
 // state's precision; cells farther than 9 sigma (g < 1e-17 g(0)) get nothing.
+// Blocks of event blockIdx.y cover the box of cells around the jet centre at
+// t_step that contains its 9-sigma ball, clipped to the grid: per active axis
+// the cells within ceil(9 sigma / h) + 1 of the cell holding the centre (at
+// most min(2 (ceil(9 sigma / h) + 1) + 1, n) of them).  The event's constants
+// are computed once per block (FP64 is slow on this GPU).
 template <class R>
-__global__ void k_jet(const EventGeo *__restrict__ ev, const WorkItem *__restrict__ items,
-                      int nitems, R *__restrict__ U, const EventClock *__restrict__ clk) {
-    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
-        const WorkItem w = items[it];
-        const EventGeo &g = ev[w.event];
-        if (!g.jet_on) continue;
-        const double dt = clk[w.event].dt;
-        if (!(dt > 0.0)) continue;
-        const double t = clk[w.event].t_step;
-        const double *j = g.jet;
-        const double sig = j[7];
-        const int nx = g.n[0], ny = g.n[1];
-        const double cz = j[2] + j[5] * t;
-        // whole chunk in z planes farther than the cutoff: nothing to add
-        const int z_lo = int(w.first / ((long long)nx * ny));
-        const int z_hi = int((w.first + w.count - 1) / ((long long)nx * ny));
-        const double zc_lo = g.lo[2] + (z_lo + 0.5) * g.h[2] - cz;
-        const double zc_hi = g.lo[2] + (z_hi + 0.5) * g.h[2] - cz;
-        if (zc_lo > 9.0 * sig || zc_hi < -9.0 * sig) continue;
-        const R amp = R(dt * j[6] / (pow(2.0 * 3.14159265358979323846, 1.5) * sig * sig * sig));
-        const R cx = R(j[0] + j[3] * t), cy = R(j[1] + j[4] * t), czr = R(cz);
-        const R inv2s2 = R(1.0 / (2.0 * sig * sig));
-        const R cut2 = R(81.0 * sig * sig);
-        const R nxr = R(j[3]), nyr = R(j[4]), nzr = R(j[5]);
-        for (int k = threadIdx.x; k < w.count; k += blockDim.x) {
-            const long long c = w.first + k;
-            const int x = int(c % nx);
-            const int y = int((c / nx) % ny);
-            const int z = int(c / ((long long)nx * ny));
-            const R px = R(g.lo[0]) + (R(x) + R(0.5)) * R(g.h[0]) - cx;
-            const R py = R(g.lo[1]) + (R(y) + R(0.5)) * R(g.h[1]) - cy;
-            const R pz = R(g.lo[2]) + (R(z) + R(0.5)) * R(g.h[2]) - czr;
-            const R r2 = px * px + py * py + pz * pz;
-            if (r2 > cut2) continue;
-            const R s = amp * exp(-r2 * inv2s2);
-            R *u = U + g.off + c;
-            u[0] += s;
-            u[g.cells] += s * nxr;
-            u[2 * g.cells] += s * nyr;
-            u[3 * g.cells] += s * nzr;
+__global__ void k_jet(const EventGeo *__restrict__ ev, R *__restrict__ U,
+                      const EventClock *__restrict__ clk) {
+    struct JetBox {
+        int lo[3], B[3];
+        R amp, cx, cy, cz, inv2s2, cut2, nx, ny, nz;
+        int on;
+    };
+    __shared__ JetBox jb;
+    const int e = blockIdx.y;
+    const EventGeo &g = ev[e];
+    if (threadIdx.x == 0) {
+        const double dt = clk[e].dt;
+        jb.on = g.jet_on && dt > 0.0;
+        if (jb.on) {
+            const double t = clk[e].t_step;
+            const double *j = g.jet;
+            const double sig = j[7];
+            const double cen[3] = {j[0] + j[3] * t, j[1] + j[4] * t, j[2] + j[5] * t};
+            for (int d = 0; d < 3; ++d) {
+                if (g.n[d] > 1) {
+                    const double hw = ceil(9.0 * sig / g.h[d]) + 1.0;
+                    const double ic = floor((cen[d] - g.lo[d]) / g.h[d]);
+                    const double a = fmax(ic - hw, 0.0), b = fmin(ic + hw, double(g.n[d] - 1));
+                    jb.lo[d] = int(a);
+                    jb.B[d] = b >= a ? int(b - a) + 1 : 0;
+                } else {
+                    jb.lo[d] = 0;
+                    jb.B[d] = 1;
+                }
+            }
+            const double two_pi_15 = 15.749609945722419;   // (2 pi)^(3/2)
+            jb.amp = R(dt * j[6] / (two_pi_15 * sig * sig * sig));
+            jb.cx = R(cen[0]); jb.cy = R(cen[1]); jb.cz = R(cen[2]);
+            jb.inv2s2 = R(1.0 / (2.0 * sig * sig));
+            jb.cut2 = R(81.0 * sig * sig);
+            jb.nx = R(j[3]); jb.ny = R(j[4]); jb.nz = R(j[5]);
         }
+    }
+    __syncthreads();
+    if (!jb.on) return;
+    const int B0 = jb.B[0], B1 = jb.B[1];
+    const long long total = (long long)B0 * B1 * jb.B[2];
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < total;
+         k += (long long)gridDim.x * blockDim.x) {
+        const int x = jb.lo[0] + int(k % B0);
+        const int y = jb.lo[1] + int((k / B0) % B1);
+        const int z = jb.lo[2] + int(k / ((long long)B0 * B1));
+        const R px = R(g.lo[0]) + (R(x) + R(0.5)) * R(g.h[0]) - jb.cx;
+        const R py = R(g.lo[1]) + (R(y) + R(0.5)) * R(g.h[1]) - jb.cy;
+        const R pz = R(g.lo[2]) + (R(z) + R(0.5)) * R(g.h[2]) - jb.cz;
+        const R r2 = px * px + py * py + pz * pz;
+        if (r2 > jb.cut2) continue;
+        const R s = jb.amp * exp(-r2 * jb.inv2s2);
+        R *u = U + g.off + x + (long long)g.n[0] * (y + (long long)g.n[1] * z);
+        u[0] += s;
+        u[g.cells] += s * jb.nx;
+        u[2 * g.cells] += s * jb.ny;
+        u[3 * g.cells] += s * jb.nz;
     }
 }
 
@@ -455,11 +477,13 @@ cudaError_t launch_dt(EventClock *clk, const double *cfl_fixed, int nevents, cud
 }
 
 cudaError_t launch_jet(const CellLaunch &c, void *U, const EventClock *clk) {
+    if (c.jet_cells <= 0 || c.nevents <= 0) return cudaSuccess;
+    // about 8 cells per thread; the box of one event spread over these blocks
+    const long long per_event = (c.jet_cells + 2047) / 2048;
+    const dim3 grid((unsigned)(per_event < 1 ? 1 : per_event), (unsigned)c.nevents);
     HY_DISPATCH(c.prec,
-        (k_jet<double><<<c.blocks, c.threads, 0, c.stream>>>(c.ev, c.items, c.nitems,
-            (double *)U, clk)),
-        (k_jet<float><<<c.blocks, c.threads, 0, c.stream>>>(c.ev, c.items, c.nitems,
-            (float *)U, clk)));
+        (k_jet<double><<<grid, 256, 0, c.stream>>>(c.ev, (double *)U, clk)),
+        (k_jet<float><<<grid, 256, 0, c.stream>>>(c.ev, (float *)U, clk)));
     return cudaGetLastError();
 }
 

@@ -64,6 +64,8 @@ struct CellLaunch {
     int mixed;            // float state, cons->prim redone in double where |v| > 0.99
     Scheme sc;
     int rate_sum = 0;     // launch_rate: sum over axes (unsplit scheme) instead of max
+    long long jet_cells = 0;   // launch_jet: cells of the largest box around a jet
+    int nevents = 0;
 };
 
 cudaError_t launch_prim2cons(const CellLaunch &c, const void *e, const void *vx, const void *vy,
