@@ -146,7 +146,9 @@ struct Prim {
 
 // Conformal EOS p = cs2 e (reading R10): W = E + p is the positive root of
 // W^2 - (1+cs2) E W + cs2 M^2 = 0; |M| is capped at (1 - delta) E (R9).
-template <class R>
+// CAP = false leaves out the |M| cap: for callers that redo every state with
+// |v| > 0.99 in FP64, which every capped state is
+template <class R, bool CAP = true>
 __device__ __forceinline__ Prim<R> c2p_conformal(const V4<R> &U, const SchemeConsts<R> &k,
                                                  R &M2out, R &Wout, const Scheme &sc,
                                                  bool counting) {
@@ -164,9 +166,10 @@ __device__ __forceinline__ Prim<R> c2p_conformal(const V4<R> &U, const SchemeCon
     // the discriminant being positive for |M| < E
     const R W = fma_(k.hapc, E, dsqrt_(fma_(-k.cs2, M2c, k.hapc2 * E2)));
     R inv = W > k.wmin ? rcp_(W) : R(0);
-    // energy flux (E + p) v_n = W (s M_n / W) = s M_n
-    R fe = U.n;
-    if (M2 > cap2) {      // |M| capped at (1 - delta) E (R9): v = s M / W
+    // energy flux (E + p) v_n = W (s M_n / W) = s M_n (0 in vacuum: there the
+    // cap gives s = 0, or without it the guard below)
+    R fe = CAP ? U.n : (W > k.wmin ? U.n : R(0));
+    if (CAP && M2 > cap2) {   // |M| capped at (1 - delta) E (R9): v = s M / W
         const R s = dsqrt_(cap2 / M2);
         inv *= s;
         fe *= s;
@@ -347,7 +350,8 @@ struct Physics {
     __device__ __forceinline__ Prim<R> prim(const V4<R> &U) const {
         if (EOSK == EOS_CONFORMAL) {
             R M2, W;
-            Prim<R> q = c2p_conformal<R>(U, K(), M2, W, sc, COUNT);
+            // mixed: a capped state has |v| > 0.99 and is redone in FP64 below
+            Prim<R> q = c2p_conformal<R, PREC != PREC_MIXED>(U, K(), M2, W, sc, COUNT);
             if (PREC == PREC_MIXED) {
                 // |v|^2 = M2 / W^2 > 0.99^2: redo in double (cancellation in W - E)
                 if (M2 > R(0.9801) * W * W) {
