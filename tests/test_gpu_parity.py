@@ -307,6 +307,34 @@ def test_table_eos_fp32(H):
     check(h, U, "fp32")
 
 
+def test_table_eos_mixed(H):
+    """Mixed precision with the tabulated EOS: FP32 Newton, redone in FP64
+    (seeded by the FP32 root) where |v| > 0.99."""
+    tab = I.eos_table()
+    g = I.event_grid(16, 0.1)
+    # one fast spot (|u| = 0.999) on the background: cells near its centre
+    # move with |v| > 0.99
+    spots = np.array([[0.05, -0.05, 0.0, 2.0, 0.999, 0.0, 0.0]])
+    prim = I.hotspot_primitives(g, spots)
+    assert np.sqrt(sum(a * a for a in prim[1:])).max() > 0.99
+    h, o, U = pair(H, g, prim, prec="mixed", bc="outflow", eos=tab, cfl=0.3)
+    o.run(U, 4)
+    h.step(4)
+    check(h, U, "mixed")
+
+
+def test_table_eos_fp32_generic_kernel(H):
+    """The runtime-limiter table kernels: MC, RK3, four MUSTA stages."""
+    tab = I.eos_table()
+    g = I.event_grid(14, 0.1)
+    prim = I.hotspot_primitives(g, I.hotspots(3, nspots=60, flow_max=0.6))
+    h, o, U = pair(H, g, prim, prec="fp32", bc="outflow", eos=tab, limiter="mc",
+                   rk_order=3, stages=4)
+    o.run(U, 3)
+    h.step(3)
+    check(h, U, "fp32")
+
+
 # ------------------------------------------------------------------ failure reporting
 def test_nonfinite_state_is_reported(H):
     g, prim = I.spherical_blast(8)

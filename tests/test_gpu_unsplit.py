@@ -173,3 +173,24 @@ def test_unsplit_rejects_mixed_schemes_in_a_batch(H):
     g2 = H.make_grid(8, 8, 8, dx=0.1)
     with pytest.raises(Exception):
         H.Batch([g1, g2])
+
+
+def test_unsplit_cfl_step_with_vacuum_matches_oracle(H):
+    """A fast blob (|v| = 0.9) in vacuum under the CFL step: the summed rate of
+    the vacuum cells (3 c / dx) exceeds the blob's, so dt is set by the vacuum
+    rule (R18: v = 0, speed c) and must equal the oracle's."""
+    n = 16
+    dx = 0.25
+    lo = -0.5 * n * dx
+    g = dict(nx=n, ny=n, nz=n, dx=dx, x0=lo, y0=lo, z0=lo)
+    spots = np.array([[0.0, 0.0, 0.0, 2.0, 0.9, 0.0, 0.0]])
+    e, vx, vy, vz = I.hotspot_primitives(g, spots, sigma=0.5, e_bg=0.0)
+    inside = e > 1e-3 * e.max()          # vacuum (e = v = 0) outside the blob
+    prim = [np.where(inside, a, 0.0) for a in (e, vx, vy, vz)]
+    assert not inside.all()
+    h, o, U = pair(H, (n, n, n), dx, (lo, lo, lo), prim, bc="outflow", cfl=0.3)
+    assert h.max_rate() == pytest.approx(o.max_rate(U), rel=1e-12)
+    _, t = o.run(U, 4)
+    h.step(4)
+    assert h.time() == pytest.approx(t, rel=1e-12)
+    check(h, U, "fp64")
