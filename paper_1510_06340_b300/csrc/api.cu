@@ -513,28 +513,38 @@ struct Solver {
     }
 
     // time candidate launch shapes for one axis (reads the current state,
-    // writes the spare buffer; the state is unchanged)
+    // writes the spare buffer; the state is unchanged).  Every candidate runs
+    // once untimed first (clocks and caches settle), then each is timed in two
+    // passes over the list and keeps its faster pass, so a clock ramp during
+    // tuning does not favour the candidates timed last.
     hydro_status tune(int axis) {
         if (forced[axis] || tuned[axis]) return HYDRO_OK;
         int maxN = 1;
         for (const EventGeo &g : geo) maxN = std::max(maxN, g.n[axis]);
-        const int threads_c[] = {64, 128, 256};
-        std::vector<int> segs = {0};
-        for (int L : {256, 128, 64, 32, 16})
-            if (L < maxN) segs.push_back(L);
+        std::vector<LaunchShape> cand;
+        for (int th : {64, 128, 256}) {
+            LaunchShape s;
+            s.threads = th;
+            s.seg_len = 0;
+            cand.push_back(s);
+            for (int L : {256, 128, 64, 32, 16})
+                if (L < maxN) {
+                    s.seg_len = L;
+                    cand.push_back(s);
+                }
+        }
         cudaEvent_t e0, e1;
         CK(cudaEventCreate(&e0));
         CK(cudaEventCreate(&e1));
-        float best = 1e30f;
-        LaunchShape bs;
-        for (int th : threads_c)
-            for (int L : segs) {
-                LaunchShape s;
-                s.threads = th;
-                s.seg_len = L;
-                hydro_status st = build_sweep_items(axis, s);
+        std::vector<float> best(cand.size(), 1e30f);
+        for (int pass = 0; pass < 3; ++pass)
+            for (size_t c = 0; c < cand.size(); ++c) {
+                hydro_status st = build_sweep_items(axis, cand[c]);
                 if (st != HYDRO_OK) return st;
-                CK(sweep_launch(axis, 1.0, d_clk_tune, cur));
+                if (pass == 0) {
+                    CK(sweep_launch(axis, 1.0, d_clk_tune, cur));
+                    continue;
+                }
                 CK(cudaEventRecord(e0, stream));
                 CK(sweep_launch(axis, 1.0, d_clk_tune, cur));
                 CK(sweep_launch(axis, 1.0, d_clk_tune, cur));
@@ -542,15 +552,15 @@ struct Solver {
                 CK(cudaEventSynchronize(e1));
                 float ms = 0.f;
                 CK(cudaEventElapsedTime(&ms, e0, e1));
-                if (ms < best) {
-                    best = ms;
-                    bs = s;
-                }
+                best[c] = std::min(best[c], ms);
             }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
+        size_t bi = 0;
+        for (size_t c = 1; c < cand.size(); ++c)
+            if (best[c] < best[bi]) bi = c;
         tuned[axis] = true;
-        return build_sweep_items(axis, bs);
+        return build_sweep_items(axis, cand[bi]);
     }
 
     hydro_status ensure_ready() {

@@ -53,6 +53,56 @@ template <class R>
 __device__ __forceinline__ V4<R> vmul(R s, const V4<R> &x) {
     return v4<R>(s * x.e, s * x.n, s * x.t1, s * x.t2);
 }
+// the transverse flux terms (M_t1 v_n, M_t2 v_n)
+template <class R>
+__device__ __forceinline__ void tmul(R s, const V4<R> &x, R &t1, R &t2) {
+    t1 = x.t1 * s; t2 = x.t2 * s;
+}
+
+// FP32: the field-wise helpers act on the pairs (E, M_n) and (M_t1, M_t2)
+// with the two-wide FP32 instructions of sm_100 and later (add/mul/fma
+// .f32x2).  Each lane rounds as the scalar instruction does; the FP32 sweep
+// is bound by instruction issue, and this halves the issued instructions of
+// its per-field arithmetic.
+__device__ __forceinline__ float2 lo2(const V4<float> &x) { return make_float2(x.e, x.n); }
+__device__ __forceinline__ float2 hi2(const V4<float> &x) { return make_float2(x.t1, x.t2); }
+__device__ __forceinline__ float2 dup2(float s) { return make_float2(s, s); }
+__device__ __forceinline__ V4<float> from2(float2 a, float2 b) {
+    return v4<float>(a.x, a.y, b.x, b.y);
+}
+// x - y lane-wise (sub.rn.f32x2; an add of the negated pair would negate
+// each lane with a scalar instruction first)
+__device__ __forceinline__ float2 sub2(float2 x, float2 y) {
+    float2 r;
+    asm("{\n\t.reg .b64 a, b, d;\n\tmov.b64 a, {%2, %3};\n\tmov.b64 b, {%4, %5};\n\t"
+        "sub.rn.f32x2 d, a, b;\n\tmov.b64 {%0, %1}, d;\n\t}"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(x.x), "f"(x.y), "f"(y.x), "f"(y.y));
+    return r;
+}
+template <>
+__device__ __forceinline__ V4<float> vsub<float>(const V4<float> &x, const V4<float> &y) {
+    return from2(sub2(lo2(x), lo2(y)), sub2(hi2(x), hi2(y)));
+}
+template <>
+__device__ __forceinline__ V4<float> vadd<float>(const V4<float> &x, const V4<float> &y) {
+    return from2(__fadd2_rn(lo2(x), lo2(y)), __fadd2_rn(hi2(x), hi2(y)));
+}
+template <>
+__device__ __forceinline__ V4<float> vfma<float>(float s, const V4<float> &x, const V4<float> &y) {
+    const float2 s2 = dup2(s);
+    return from2(__ffma2_rn(s2, lo2(x), lo2(y)), __ffma2_rn(s2, hi2(x), hi2(y)));
+}
+template <>
+__device__ __forceinline__ V4<float> vmul<float>(float s, const V4<float> &x) {
+    const float2 s2 = dup2(s);
+    return from2(__fmul2_rn(s2, lo2(x)), __fmul2_rn(s2, hi2(x)));
+}
+template <>
+__device__ __forceinline__ void tmul<float>(float s, const V4<float> &x, float &t1, float &t2) {
+    const float2 t = __fmul2_rn(hi2(x), dup2(s));
+    t1 = t.x; t2 = t.y;
+}
 
 // ---------------------------------------------------------------- math helpers
 __device__ __forceinline__ double dsqrt_(double x) { return sqrt(x); }
@@ -393,7 +443,9 @@ struct Physics {
     __device__ __forceinline__ V4<R> flux(const V4<R> &U) const {
         const Prim<R> q = prim(U);
         // Eq. 3 along the axis: ((E + p) v_n, M_n v_n + p, M_t1 v_n, M_t2 v_n)
-        return v4<R>(q.fe, fma_(U.n, q.vn, q.p), U.t1 * q.vn, U.t2 * q.vn);
+        R t1, t2;
+        tmul<R>(q.vn, U, t1, t2);
+        return v4<R>(q.fe, fma_(U.n, q.vn, q.p), t1, t2);
     }
 
     // CFL rate of one cell (reading R8): max over swept axes of |lambda^+-| / dx,

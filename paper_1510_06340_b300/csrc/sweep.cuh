@@ -23,10 +23,10 @@ namespace hy {
 
 // XS: RK2 x sweep through the shared-memory row rings (march_x_rk2)
 template <class R, int PREC, int EOSK, int RK, int LIM, bool COUNT, bool RATE, bool XS>
-__global__ void HY_SWEEP_BOUNDS
-k_sweep(const R *__restrict__ in, R *__restrict__ out, const EventGeo *__restrict__ ev,
-        const WorkItem *__restrict__ items, int nitems, int axis, double frac,
-        const EventClock *__restrict__ clk, Scheme sc, int *counter, EventClock *rate_clk) {
+__device__ __forceinline__ void
+sweep_body(const R *__restrict__ in, R *__restrict__ out, const EventGeo *__restrict__ ev,
+           const WorkItem *__restrict__ items, int nitems, int axis, double frac,
+           const EventClock *__restrict__ clk, Scheme sc, int *counter, EventClock *rate_clk) {
     Physics<R, PREC, EOSK, LIM, COUNT> ph;
     ph.sc = sc;
     __shared__ int s_item;
@@ -137,6 +137,39 @@ k_sweep(const R *__restrict__ in, R *__restrict__ out, const EventGeo *__restric
     }
 }
 
+#define HY_SWEEP_PARAMS                                                                      \
+    const R *__restrict__ in, R *__restrict__ out, const EventGeo *__restrict__ ev,          \
+        const WorkItem *__restrict__ items, int nitems, int axis, double frac,              \
+        const EventClock *__restrict__ clk, Scheme sc, int *counter, EventClock *rate_clk
+#define HY_SWEEP_ARGS in, out, ev, items, nitems, axis, frac, clk, sc, counter, rate_clk
+
+template <class R, int PREC, int EOSK, int RK, int LIM, bool COUNT, bool RATE, bool XS>
+__global__ void HY_SWEEP_BOUNDS k_sweep(HY_SWEEP_PARAMS) {
+    sweep_body<R, PREC, EOSK, RK, LIM, COUNT, RATE, XS>(HY_SWEEP_ARGS);
+}
+
+// The FP32 conformal RK3 sweep (three stages chained in registers) wants a
+// few registers more than 168; capped there it keeps 12 warps per SM (six
+// blocks of 64 or three of 128) instead of 10, which is worth more than the
+// registers.  168 x 256 threads still fits a block.
+#ifndef HY_RK3_MAXNREG
+#define HY_RK3_MAXNREG 168
+#endif
+template <class R, int PREC, int EOSK, int RK, int LIM, bool COUNT, bool RATE, bool XS>
+__global__ void __maxnreg__(HY_RK3_MAXNREG) k_sweep_rk3(HY_SWEEP_PARAMS) {
+    sweep_body<R, PREC, EOSK, RK, LIM, COUNT, RATE, XS>(HY_SWEEP_ARGS);
+}
+#undef HY_SWEEP_PARAMS
+#undef HY_SWEEP_ARGS
+
+template <class R, int PREC, int EOSK, int RK, int LIM, bool COUNT, bool RATE, bool XS>
+constexpr auto sweep_kernel() {
+    if constexpr (RK == 3 && PREC == PREC_F32 && EOSK == EOS_CONFORMAL && !COUNT)
+        return &k_sweep_rk3<R, PREC, EOSK, RK, LIM, COUNT, RATE, XS>;
+    else
+        return &k_sweep<R, PREC, EOSK, RK, LIM, COUNT, RATE, XS>;
+}
+
 template <class R, int PREC>
 cudaError_t launch_sweep_prec(const SweepLaunch &a) {
     const R *in = static_cast<const R *>(a.in);
@@ -148,7 +181,7 @@ cudaError_t launch_sweep_prec(const SweepLaunch &a) {
     }
 #define HY_SWEEP_XS(EOSK, RK, LIM, COUNT, RATE, XS)                                          \
     {                                                                                       \
-        auto kfn = k_sweep<R, PREC, EOSK, RK, LIM, COUNT, RATE, XS>;                        \
+        auto kfn = sweep_kernel<R, PREC, EOSK, RK, LIM, COUNT, RATE, XS>();                 \
         const size_t smem = XS                                                              \
             ? size_t(a.threads / 32) * xstage_floats_per_warp<R>() * sizeof(R) : 0;          \
         if (smem > 0) {   /* opt in once per device, for 256 threads */                 \
