@@ -25,7 +25,7 @@ BASE = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + S
 # float sweeps use approximate sqrt/divide and flush denormals (a few ulp, far
 # inside the FP32 tolerance)
 FAST = {"sweep_f32.cu", "sweep_mixed.cu", "unsplit_f32.cu", "unsplit_mixed.cu"}
-FAST_FLAGS = ["-ftz=true", "-prec-div=false", "-prec-sqrt=false"]
+FAST_FLAGS = ["-ftz=true", "-prec-div=false", "-prec-sqrt=false", "-DHY_FTZ"]
 NOFMAD = set()   # units compiled with -fmad=false (none)
 
 

@@ -59,26 +59,45 @@ __device__ __forceinline__ void tmul(R s, const V4<R> &x, R &t1, R &t2) {
     t1 = x.t1 * s; t2 = x.t2 * s;
 }
 
-// FP32: the field-wise helpers act on the pairs (E, M_n) and (M_t1, M_t2)
-// with the two-wide FP32 instructions of sm_100 and later (add/mul/fma
-// .f32x2).  Each lane rounds as the scalar instruction does; the FP32 sweep
-// is bound by instruction issue, and this halves the issued instructions of
-// its per-field arithmetic.
+// Two-wide FP32 arithmetic (add/sub/mul/fma .f32x2 of sm_100 and later): one
+// instruction computes a pair of lanes, each rounded as the scalar
+// instruction is.  Units built with flushed denormals define HY_FTZ, and the
+// pair instructions flush too, so they agree with the scalar code there.
+#ifdef HY_FTZ
+#define HY_F2 ".rn.ftz.f32x2"
+#else
+#define HY_F2 ".rn.f32x2"
+#endif
+#define HY_F2_BINARY(name, op)                                                              \
+    __device__ __forceinline__ float2 name(float2 x, float2 y) {                             \
+        float2 r;                                                                           \
+        asm("{\n\t.reg .b64 a, b, d;\n\tmov.b64 a, {%2, %3};\n\tmov.b64 b, {%4, %5};\n\t" \
+            op HY_F2 " d, a, b;\n\tmov.b64 {%0, %1}, d;\n\t}"                               \
+            : "=f"(r.x), "=f"(r.y)                                                          \
+            : "f"(x.x), "f"(x.y), "f"(y.x), "f"(y.y));                                      \
+        return r;                                                                           \
+    }
+HY_F2_BINARY(add2, "add")
+HY_F2_BINARY(sub2, "sub")
+HY_F2_BINARY(mul2, "mul")
+#undef HY_F2_BINARY
+__device__ __forceinline__ float2 fma2(float2 x, float2 y, float2 z) {
+    float2 r;
+    asm("{\n\t.reg .b64 a, b, c, d;\n\tmov.b64 a, {%2, %3};\n\tmov.b64 b, {%4, %5};\n\t"
+        "mov.b64 c, {%6, %7};\n\tfma" HY_F2 " d, a, b, c;\n\tmov.b64 {%0, %1}, d;\n\t}"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(x.x), "f"(x.y), "f"(y.x), "f"(y.y), "f"(z.x), "f"(z.y));
+    return r;
+}
+
+// FP32: the field-wise helpers act on the pairs (E, M_n) and (M_t1, M_t2).
+// The FP32 sweep is bound by instruction issue, and this halves the issued
+// instructions of its per-field arithmetic.
 __device__ __forceinline__ float2 lo2(const V4<float> &x) { return make_float2(x.e, x.n); }
 __device__ __forceinline__ float2 hi2(const V4<float> &x) { return make_float2(x.t1, x.t2); }
 __device__ __forceinline__ float2 dup2(float s) { return make_float2(s, s); }
 __device__ __forceinline__ V4<float> from2(float2 a, float2 b) {
     return v4<float>(a.x, a.y, b.x, b.y);
-}
-// x - y lane-wise (sub.rn.f32x2; an add of the negated pair would negate
-// each lane with a scalar instruction first)
-__device__ __forceinline__ float2 sub2(float2 x, float2 y) {
-    float2 r;
-    asm("{\n\t.reg .b64 a, b, d;\n\tmov.b64 a, {%2, %3};\n\tmov.b64 b, {%4, %5};\n\t"
-        "sub.rn.f32x2 d, a, b;\n\tmov.b64 {%0, %1}, d;\n\t}"
-        : "=f"(r.x), "=f"(r.y)
-        : "f"(x.x), "f"(x.y), "f"(y.x), "f"(y.y));
-    return r;
 }
 template <>
 __device__ __forceinline__ V4<float> vsub<float>(const V4<float> &x, const V4<float> &y) {
@@ -86,21 +105,21 @@ __device__ __forceinline__ V4<float> vsub<float>(const V4<float> &x, const V4<fl
 }
 template <>
 __device__ __forceinline__ V4<float> vadd<float>(const V4<float> &x, const V4<float> &y) {
-    return from2(__fadd2_rn(lo2(x), lo2(y)), __fadd2_rn(hi2(x), hi2(y)));
+    return from2(add2(lo2(x), lo2(y)), add2(hi2(x), hi2(y)));
 }
 template <>
 __device__ __forceinline__ V4<float> vfma<float>(float s, const V4<float> &x, const V4<float> &y) {
     const float2 s2 = dup2(s);
-    return from2(__ffma2_rn(s2, lo2(x), lo2(y)), __ffma2_rn(s2, hi2(x), hi2(y)));
+    return from2(fma2(s2, lo2(x), lo2(y)), fma2(s2, hi2(x), hi2(y)));
 }
 template <>
 __device__ __forceinline__ V4<float> vmul<float>(float s, const V4<float> &x) {
     const float2 s2 = dup2(s);
-    return from2(__fmul2_rn(s2, lo2(x)), __fmul2_rn(s2, hi2(x)));
+    return from2(mul2(s2, lo2(x)), mul2(s2, hi2(x)));
 }
 template <>
 __device__ __forceinline__ void tmul<float>(float s, const V4<float> &x, float &t1, float &t2) {
-    const float2 t = __fmul2_rn(hi2(x), dup2(s));
+    const float2 t = mul2(hi2(x), dup2(s));
     t1 = t.x; t2 = t.y;
 }
 
@@ -121,6 +140,8 @@ __device__ __forceinline__ double fmin_(double a, double b) { return fmin(a, b);
 __device__ __forceinline__ float fmin_(float a, float b) { return fminf(a, b); }
 __device__ __forceinline__ double fabs_(double a) { return fabs(a); }
 __device__ __forceinline__ float fabs_(float a) { return fabsf(a); }
+__device__ __forceinline__ bool positive(double a) { return a > 0.0; }
+__device__ __forceinline__ bool positive(float a) { return a > 0.0f; }
 
 // ---------------------------------------------------------------- limiters
 // Sec. 2.5 (Eq. 15-21), division-free: returns a * xi(b / a).
@@ -718,12 +739,12 @@ template <class R, int RK, bool RATE, class PH>
 __device__ __forceinline__ void march(const PH &ph, const Pencil<R> &P, int s0, int L, int s_end,
                                       int bc, R lam, bool do_store, RateAcc<R> &ra) {
     const int N = P.N;
-    if (!(lam > R(0))) {   // finished event: copy through
+    if (!positive(lam)) {   // finished event: copy through
         if (do_store)
             for (int o = s0; o < s_end; ++o) P.store(o, P.load(o));
         return;
     }
-    const bool rate_on = RATE && ra.ih_n > R(0);
+    const bool rate_on = RATE && positive(ra.ih_n);
     const R third = R(1.0 / 3.0), two3 = R(2.0 / 3.0), q3 = R(0.75), q1c = R(0.25), half = R(0.5);
     Stage<R> st1, st2, st3;
     st1.n = 0; st2.n = 0; st3.n = 0;
@@ -735,7 +756,7 @@ __device__ __forceinline__ void march(const PH &ph, const Pencil<R> &P, int s0, 
     V4<R> qa[3];
     V4<R> lastA = v4<R>(0, 0, 0, 0), lastB = lastA;
     V4<R> nxt = P.load(wrap_index(js, N, bc));
-    if (RK == 2) {
+    if constexpr (RK == 2) {
         // One loop body for every step: both engines push unchecked from t = 0
         // on zero-initialised windows.  Their outputs before the windows fill
         // (t < 4 for stage 1, t < 10 for stage 2) are never used or stored
@@ -776,15 +797,17 @@ __device__ __forceinline__ void march(const PH &ph, const Pencil<R> &P, int s0, 
             // Eq. 6: U^{n+1} = 1/2 (U + U1 + dt L(U1))
             const V4<R> r = vmul<R>(half, vfma<R>(-lam, Dl, vadd(U0, c)));
             const bool keep = do_store && o >= s0 && o < s_end;
-            if (rate_on && keep) {
-                const R rr = ph.rate(r, ra.ih_n, ra.ih_t1, ra.ih_t2, ra.iso);
-                ra.m = (rr > ra.m || rr != rr) ? rr : ra.m;
+            if constexpr (RATE) {
+                if (rate_on && keep) {
+                    const R rr = ph.rate(r, ra.ih_n, ra.ih_t1, ra.ih_t2, ra.iso);
+                    ra.m = (rr > ra.m || rr != rr) ? rr : ra.m;
+                }
             }
             if (keep) P.store(o, r);
         }
         return;
     }
-    if (RK == 3) {
+    if constexpr (RK == 3) {
         // The same uniform loop for Eq. 7: three engines push from step 0 on
         // zero-initialised windows; each stage reads the previous stage's
         // output two cells behind its newest (the 2 ghost cells of a stage).
@@ -837,27 +860,33 @@ __device__ __forceinline__ void march(const PH &ph, const Pencil<R> &P, int s0, 
             // U^{n+1} = 1/3 U + 2/3 (U2 + dt L(U2))
             const V4<R> r = vfma<R>(third, U00, vmul<R>(two3, vfma<R>(-lam, D3, c3)));
             const bool keep = do_store && o >= s0 && o < s_end;
-            if (rate_on && keep) {
-                const R rr = ph.rate(r, ra.ih_n, ra.ih_t1, ra.ih_t2, ra.iso);
-                ra.m = (rr > ra.m || rr != rr) ? rr : ra.m;
+            if constexpr (RATE) {
+                if (rate_on && keep) {
+                    const R rr = ph.rate(r, ra.ih_n, ra.ih_t1, ra.ih_t2, ra.iso);
+                    ra.m = (rr > ra.m || rr != rr) ? rr : ra.m;
+                }
             }
             if (keep) P.store(o, r);
         }
         return;
     }
-    // RK1 (plain MUSCL-Hancock with MUSTA-FORCE fluxes)
+    if constexpr (RK == 1) {
+        // RK1 (plain MUSCL-Hancock with MUSTA-FORCE fluxes)
 #pragma unroll 1
-    for (int t = 0; t < T; ++t) {
-        const V4<R> V = nxt;
-        if (t + 1 < T) nxt = P.load(wrap_index(js + t + 1, N, bc));
-        if (!st1.push(V, ph, lam, cell, D)) continue;
-        const int i = js + t - 2;   // output cell
-        const V4<R> X = vfma<R>(-lam, D, cell);   // U + dt L(U)
-        if (rate_on) {
-            const R rr = ph.rate(X, ra.ih_n, ra.ih_t1, ra.ih_t2, ra.iso);
-            if (do_store && i < s_end) ra.m = (rr > ra.m || rr != rr) ? rr : ra.m;
+        for (int t = 0; t < T; ++t) {
+            const V4<R> V = nxt;
+            if (t + 1 < T) nxt = P.load(wrap_index(js + t + 1, N, bc));
+            if (!st1.push(V, ph, lam, cell, D)) continue;
+            const int i = js + t - 2;   // output cell
+            const V4<R> X = vfma<R>(-lam, D, cell);   // U + dt L(U)
+            if constexpr (RATE) {
+                if (rate_on) {
+                    const R rr = ph.rate(X, ra.ih_n, ra.ih_t1, ra.ih_t2, ra.iso);
+                    if (do_store && i < s_end) ra.m = (rr > ra.m || rr != rr) ? rr : ra.m;
+                }
+            }
+            if (do_store && i < s_end) P.store(i, X);
         }
-        if (do_store && i < s_end) P.store(i, X);
     }
 }
 
@@ -1069,7 +1098,7 @@ __device__ __forceinline__ void march_x_rk2(const PH &ph, XStage<R> &X, int s0, 
         keep |= (kp ? 1u : 0u) << (t & 7);
         if (((t - psi) & 7) == 0 || t == T - 1) {
             __syncwarp();
-            X.flush<RATE>(t, keep, ph, ra, rate_on);
+            X.template flush<RATE>(t, keep, ph, ra, rate_on);
             __syncwarp();
             keep = 0u;
         }
