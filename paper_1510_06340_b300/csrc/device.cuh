@@ -1072,16 +1072,16 @@ __device__ __forceinline__ void march_x_rk2(const PH &ph, XStage<R> &X, int s0, 
     cp_async_wait_all();
     __syncwarp();
     unsigned keep = 0u;
+    // the ring reads of a step (its input and the RK reload 6 steps behind)
+    // are made at the end of the step before, so their latency overlaps it
+    V4<R> Vn = X.get(0), U0n = X.get(-6);
 #pragma unroll 1
     for (int t = 0; t < T; ++t) {
         if (t >= tf && ((t - phi) & 7) == 0) {   // slots of steps < t - 6 are free
             __syncwarp();
             X.fill(t + 2);
-        } else if (t >= tf + 2 && ((t - 2 - phi) & 7) == 0) {   // the copy is needed now
-            cp_async_wait_all();
-            __syncwarp();
         }
-        const V4<R> V = X.get(t);
+        const V4<R> V = Vn, U0 = U0n;
         st1.push_full(V, ph, lam, cell, D);
         const int i = js + t - 2;
         const V4<R> Xv = vfma<R>(-lam, D, cell);   // U1 = U + dt L(U)
@@ -1091,7 +1091,6 @@ __device__ __forceinline__ void march_x_rk2(const PH &ph, XStage<R> &X, int s0, 
         V4<R> c, Dl;
         st2.push_full(Y, ph, lam, c, Dl);
         const int o = t + s0 - 10;
-        const V4<R> U0 = X.get(t - 6);
         const V4<R> r = vmul<R>(half, vfma<R>(-lam, Dl, vadd(U0, c)));
         const bool kp = do_store && o >= s0 && o < s_end;
         X.put(t, r);
@@ -1101,6 +1100,15 @@ __device__ __forceinline__ void march_x_rk2(const PH &ph, XStage<R> &X, int s0, 
             X.template flush<RATE>(t, keep, ph, ra, rate_on);
             __syncwarp();
             keep = 0u;
+        }
+        // step t + 1 opens a copy group (filled at t - 1): wait for it first
+        if (t + 1 >= tf + 2 && ((t - 1 - phi) & 7) == 0) {
+            cp_async_wait_all();
+            __syncwarp();
+        }
+        if (t + 1 < T) {
+            Vn = X.get(t + 1);
+            U0n = X.get(t - 5);
         }
     }
     cp_async_wait_all();   // a last copy may still be in flight
