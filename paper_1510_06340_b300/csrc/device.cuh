@@ -469,6 +469,35 @@ struct Physics {
         return v4<R>(q.fe, fma_(U.n, q.vn, q.p), t1, t2);
     }
 
+    // The conformal FP32/FP64 sweeps take the |M| cap (R9) per group of flux
+    // evaluations instead of per evaluation: the group runs without it and
+    // only records whether any state exceeded the cap (one predicate-or per
+    // evaluation); a lane that recorded one redoes the group with the capped
+    // flux.  Where the cap does not act the two give the same bits, so the
+    // results are those of flux() throughout.  Counting runs keep flux().
+    static constexpr bool CAP_GROUPS = EOSK == EOS_CONFORMAL && PREC != PREC_MIXED && !COUNT;
+
+    __device__ __forceinline__ V4<R> flux_uncapped(const V4<R> &U, bool &capped) const {
+        const SchemeConsts<R> &k = K();
+        const R E = fmax_(U.e, R(0));
+        const R M2 = fma_(U.t2, U.t2, fma_(U.t1, U.t1, U.n * U.n));
+        const R E2 = E * E;
+        const R cap2 = k.capf * E2;
+        const R M2c = fmin_(M2, cap2);
+        const R W = fma_(k.hapc, E, dsqrt_(fma_(-k.cs2, M2c, k.hapc2 * E2)));
+        const R inv = W > k.wmin ? rcp_(W) : R(0);
+        capped = capped || M2 > cap2;
+        const R vn = U.n * inv;
+        R t1, t2;
+        tmul<R>(vn, U, t1, t2);
+        return v4<R>(U.n, fma_(U.n, vn, W - E), t1, t2);
+    }
+    template <bool UNCAPPED>
+    __device__ __forceinline__ V4<R> flux_g(const V4<R> &U, bool &capped) const {
+        if constexpr (UNCAPPED) return flux_uncapped(U, capped);
+        else return flux(U);
+    }
+
     // CFL rate of one cell (reading R8): max over swept axes of |lambda^+-| / dx,
     // axes given in the sweep's slot order (n, t1, t2) with ih = 1/dx (0: not swept);
     // iso: every swept axis has spacing 1 / ih_n
@@ -576,7 +605,16 @@ struct Physics {
         ul = vfma<R>(-half, sl, v0);
         ur = vfma<R>(half, sl, v0);
         if (sc.hancock) {
-            const V4<R> FL = flux(ul), FR = flux(ur);
+            V4<R> FL, FR;
+            if constexpr (CAP_GROUPS) {
+                bool capped = false;
+                FL = flux_uncapped(ul, capped);
+                FR = flux_uncapped(ur, capped);
+                if (capped) { FL = flux(ul); FR = flux(ur); }
+            } else {
+                FL = flux(ul);
+                FR = flux(ur);
+            }
             const V4<R> d = vsub(FL, FR);
             const R hl = half * lam;
             ul = vfma<R>(hl, d, ul);
@@ -589,7 +627,19 @@ struct Physics {
     }
 
     // MUSTA-FORCE interface flux (Sec. 2.4 steps 1-5, Eq. 8-11; R1, R2, R4)
-    __device__ __forceinline__ V4<R> musta(V4<R> UL, V4<R> UR, R lam) const {
+    __device__ __forceinline__ V4<R> musta(const V4<R> &UL, const V4<R> &UR, R lam) const {
+        if constexpr (CAP_GROUPS) {
+            bool capped = false;
+            const V4<R> F = musta_g<true>(UL, UR, lam, capped);
+            if (capped) return musta_g<false>(UL, UR, lam, capped);
+            return F;
+        } else {
+            bool unused = false;
+            return musta_g<false>(UL, UR, lam, unused);
+        }
+    }
+    template <bool UNCAPPED>
+    __device__ __forceinline__ V4<R> musta_g(V4<R> UL, V4<R> UR, R lam, bool &capped) const {
         const R al = al_;
         const R clw = R(0.5) * al;
         const R half = R(0.5), q4 = R(0.25), hclf = hclf_;
@@ -597,17 +647,17 @@ struct Physics {
         const int k = sc.stages;
 #pragma unroll 1
         for (int l = 0; l < k; ++l) {
-            const V4<R> FL = flux(UL), FR = flux(UR);
+            const V4<R> FL = flux_g<UNCAPPED>(UL, capped), FR = flux_g<UNCAPPED>(UR, capped);
             // F = 1/2 F_lw + 1/2 F_lf = 1/2 F_lw + 1/4 (F_L + F_R) - (clf/2) (U_R - U_L)
             const V4<R> Flf = vfma<R>(-hclf, vsub(UR, UL), vmul<R>(q4, vadd(FL, FR)));
             if (EOSK == EOS_CONFORMAL) {
                 // p = c2 e makes the flux homogeneous of degree 1, F(2U) = 2 F(U),
                 // and doubling is exact: take F(2 U_lw) / 4 for F_lw / 2
                 const V4<R> Ulw2 = vfma<R>(-al, vsub(FR, FL), vadd(UL, UR));
-                Fc = vfma<R>(q4, flux(Ulw2), Flf);
+                Fc = vfma<R>(q4, flux_g<UNCAPPED>(Ulw2, capped), Flf);
             } else {
                 const V4<R> Ulw = vfma<R>(-clw, vsub(FR, FL), vmul<R>(half, vadd(UL, UR)));
-                Fc = vfma<R>(half, flux(Ulw), Flf);
+                Fc = vfma<R>(half, flux_g<UNCAPPED>(Ulw, capped), Flf);
             }
             if (l < k - 1) {
                 UL = vfma<R>(-lam, vsub(Fc, FL), UL);
