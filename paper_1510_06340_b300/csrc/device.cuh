@@ -404,7 +404,9 @@ __device__ __forceinline__ Prim<R> c2p_table(const V4<R> &U, R delta, const Sche
 // Precision policy of a sweep: storage/flux type R and the cons->prim rule.
 enum { PREC_F64 = 0, PREC_F32 = 1, PREC_MIXED = 2 };
 
-template <class R, int PREC, int EOSK, int LIM = -1, bool COUNT = true>
+// MUSTA2: the kernel writes out the two-stage MUSTA-FORCE (the RK3 kernels,
+// whose registers are capped, keep the loop)
+template <class R, int PREC, int EOSK, int LIM = -1, bool COUNT = true, bool MUSTA2 = true>
 struct Physics {
     Scheme sc;
     R al_, hclf_;   // alpha dt/dx and 1 / (4 alpha dt/dx) of the current sweep
@@ -628,15 +630,34 @@ struct Physics {
 
     // MUSTA-FORCE interface flux (Sec. 2.4 steps 1-5, Eq. 8-11; R1, R2, R4)
     __device__ __forceinline__ V4<R> musta(const V4<R> &UL, const V4<R> &UR, R lam) const {
+        bool capped = false;
         if constexpr (CAP_GROUPS) {
-            bool capped = false;
-            const V4<R> F = musta_g<true>(UL, UR, lam, capped);
-            if (capped) return musta_g<false>(UL, UR, lam, capped);
-            return F;
-        } else {
-            bool unused = false;
-            return musta_g<false>(UL, UR, lam, unused);
+            V4<R> F;
+            if (MUSTA2 && sc.stages == 2) {
+                // two stages written out, so that the predicted states take
+                // fresh registers while the inputs stay for a redo
+                V4<R> FL, FR;
+                const V4<R> F0 = musta_stage<true>(UL, UR, FL, FR, capped);
+                const V4<R> UL1 = vfma<R>(-lam, vsub(F0, FL), UL);
+                const V4<R> UR1 = vfma<R>(-lam, vsub(FR, F0), UR);
+                F = musta_stage<true>(UL1, UR1, FL, FR, capped);
+            } else {
+                F = musta_g<true>(UL, UR, lam, capped);
+            }
+            if (!capped) return F;
         }
+        return musta_g<false>(UL, UR, lam, capped);
+    }
+    // one FORCE evaluation of Sec. 2.4 (steps 1-4) at (UL, UR), with F(UL), F(UR)
+    template <bool UNCAPPED>
+    __device__ __forceinline__ V4<R> musta_stage(const V4<R> &UL, const V4<R> &UR, V4<R> &FL,
+                                                 V4<R> &FR, bool &capped) const {
+        const R q4 = R(0.25);
+        FL = flux_g<UNCAPPED>(UL, capped);
+        FR = flux_g<UNCAPPED>(UR, capped);
+        const V4<R> Flf = vfma<R>(-hclf_, vsub(UR, UL), vmul<R>(q4, vadd(FL, FR)));
+        const V4<R> Ulw2 = vfma<R>(-al_, vsub(FR, FL), vadd(UL, UR));
+        return vfma<R>(q4, flux_g<UNCAPPED>(Ulw2, capped), Flf);
     }
     template <bool UNCAPPED>
     __device__ __forceinline__ V4<R> musta_g(V4<R> UL, V4<R> UR, R lam, bool &capped) const {

@@ -27,7 +27,7 @@ __device__ __forceinline__ void
 sweep_body(const R *__restrict__ in, R *__restrict__ out, const EventGeo *__restrict__ ev,
            const WorkItem *__restrict__ items, int nitems, int axis, double frac,
            const EventClock *__restrict__ clk, Scheme sc, int *counter, EventClock *rate_clk) {
-    Physics<R, PREC, EOSK, LIM, COUNT> ph;
+    Physics<R, PREC, EOSK, LIM, COUNT, RK != 3> ph;
     ph.sc = sc;
     __shared__ int s_item;
     __shared__ R s_red[8];
