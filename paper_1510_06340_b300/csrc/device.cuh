@@ -1034,7 +1034,9 @@ struct XStage {
             cp_async_commit();
             return;
         }
-#pragma unroll
+        // rows of several segments or events (the rare case): kept rolled, so
+        // that it does not crowd the instruction cache
+#pragma unroll 1
         for (int k = 0; k < 8; ++k) {
             const int r = (lane >> 3) + 4 * k;
             const int rn = __shfl_sync(0xffffffffu, rowN, r);
@@ -1087,7 +1089,7 @@ struct XStage {
             }
             return;
         }
-#pragma unroll
+#pragma unroll 1
         for (int k = 0; k < 8; ++k) {
             const int r = (lane >> 3) + 4 * k;
             const int rn = __shfl_sync(0xffffffffu, rowN, r);
