@@ -978,6 +978,10 @@ __device__ __forceinline__ void march(const PH &ph, const Pencil<R> &P, int s0, 
 // sectors.
 constexpr int XR = 16;        // input ring: steps per row
 constexpr int XRS = XR + 1;   // row stride (odd: conflict-free column reads)
+// rows per iteration of the output flush, with and without the CFL rate (1
+// and 8, or 2 and 4, measured the same)
+constexpr int kFlushUnrollRate = 2;
+constexpr int kFlushUnroll = 8;
 constexpr int XO = 8;         // output ring: steps per row
 constexpr int XOS = XO + 1;
 
@@ -1070,7 +1074,9 @@ struct XStage {
             if ((keep >> (st & 7)) & 1u) {
                 R *p0 = out + rowN0 + (js0 + st - 6);
                 const R *q0 = oring + (st & (XO - 1));
-#pragma unroll
+                // with the rate: two rows per iteration, which keeps the code
+                // of the step loop in the instruction cache
+#pragma unroll(RATE ? kFlushUnrollRate : kFlushUnroll)
                 for (int k = 0; k < 8; ++k) {
                     const int r = (lane >> 3) + 4 * k;
                     R *p = p0 + r * N;
