@@ -66,7 +66,7 @@ def flops_per_cell_sweep(rk=2, stages=2, limiter="minmod"):
 # DRAM bytes read + written per sweep launch, mean over the five sweeps of one
 # step, from an ncu capture of the current kernels (profiles/
 # sweep_blast256_fp32_step.md); None where no capture of the current kernels exists
-SWEEP_TRAFFIC = {(256, "fp32", 2, 2, False): 598.2e6}
+SWEEP_TRAFFIC = {(256, "fp32", 2, 2, False): 597.4e6}
 
 
 def flops_per_cell_stage_unsplit(stages=2):
