@@ -477,7 +477,9 @@ struct Physics {
     // evaluation); a lane that recorded one redoes the group with the capped
     // flux.  Where the cap does not act the two give the same bits, so the
     // results are those of flux() throughout.  Counting runs keep flux().
-    static constexpr bool CAP_GROUPS = EOSK == EOS_CONFORMAL && PREC != PREC_MIXED && !COUNT;
+    // The mixed sweeps group their FP64 redo the same way: a group is redone
+    // through flux() where a state's FP32 recovery gives |v| > 0.99.
+    static constexpr bool CAP_GROUPS = EOSK == EOS_CONFORMAL && !COUNT;
 
     __device__ __forceinline__ V4<R> flux_uncapped(const V4<R> &U, bool &capped) const {
         const SchemeConsts<R> &k = K();
@@ -487,12 +489,20 @@ struct Physics {
         const R cap2 = k.capf * E2;
         const R M2c = fmin_(M2, cap2);
         const R W = fma_(k.hapc, E, dsqrt_(fma_(-k.cs2, M2c, k.hapc2 * E2)));
-        const R inv = W > k.wmin ? rcp_(W) : R(0);
-        capped = capped || M2 > cap2;
+        const bool live = W > k.wmin;
+        const R inv = live ? rcp_(W) : R(0);
+        R fe;
+        if constexpr (PREC == PREC_MIXED) {   // c2p_conformal<R, false> and prim()'s test
+            fe = live ? U.n : R(0);
+            capped = capped || M2c > R(0.9801) * W * W;
+        } else {
+            fe = U.n;
+            capped = capped || M2 > cap2;
+        }
         const R vn = U.n * inv;
         R t1, t2;
         tmul<R>(vn, U, t1, t2);
-        return v4<R>(U.n, fma_(U.n, vn, W - E), t1, t2);
+        return v4<R>(fe, fma_(U.n, vn, W - E), t1, t2);
     }
     template <bool UNCAPPED>
     __device__ __forceinline__ V4<R> flux_g(const V4<R> &U, bool &capped) const {
