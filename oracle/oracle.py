@@ -7,7 +7,7 @@ file; this module only marshals numpy arrays through ctypes.
 
 Parity unpinned: the MLP seed used inside the Newton solve (it only changes
 the iteration count, never the converged root; its gradients are pinned by
-finite differences in the tests), and the jet source beyond its integral.
+finite differences in the tests).
 """
 from __future__ import annotations
 

@@ -491,6 +491,40 @@ def test_jet_source_deposits_dedx_per_unit_time():
     np.testing.assert_allclose(ds[1:], want * jet[3:6], atol=1e-8 * want)
 
 
+def test_jet_source_profile_moves_with_the_jet_and_has_width_sigma():
+    """R12 beyond the integrals: the deposited energy is a Gaussian centred on
+    x0 + n t (the jet has moved along n for the time t) with variance sigma^2
+    per axis, and the momentum deposit is n times the energy deposit cell by
+    cell.  Sampled on cells of dx = sigma / 3 a Gaussian's first and second
+    moments are exact to far below the tolerances (Poisson summation), so a
+    wrong direction or sign of the motion, a wrong width or a mixed-up axis
+    fails here."""
+    n, dx = 64, 0.1
+    lo = -0.5 * n * dx
+    sig = 0.3
+    jet = np.array([0.3, -0.2, 0.1, 0.6, 0.0, -0.8, 5.0, sig])
+    o = O.Oracle(n, n, n, dx=dx, x0=lo, y0=lo, z0=lo, jet=jet)
+    U = np.zeros(o.shape)
+    t, dt = 0.75, 0.02
+    o.jet_source(U, t, dt)
+    c = lo + (np.arange(n) + 0.5) * dx
+    zz, yy, xx = np.meshgrid(c, c, c, indexing="ij")
+    w = U[0]
+    mass = w.sum()
+    centre = np.array([jet[0], jet[1], jet[2]]) + t * jet[3:6]
+    got = np.array([(xx * w).sum(), (yy * w).sum(), (zz * w).sum()]) / mass
+    np.testing.assert_allclose(got, centre, atol=1e-9)
+    for a, x in zip(range(3), (xx, yy, zz)):
+        var = ((x - centre[a]) ** 2 * w).sum() / mass
+        assert abs(var - sig * sig) < 1e-8, (a, var)
+    for k in range(3):
+        np.testing.assert_allclose(U[1 + k], jet[3 + k] * U[0], rtol=0, atol=1e-15)
+    # the peak deposit: dt dE/dx over (2 pi)^(3/2) sigma^3 at the centre, here
+    # off the cell centres, so the largest cell value lies below it
+    peak = dt * jet[6] / ((2 * np.pi) ** 1.5 * sig ** 3)
+    assert w.max() < peak and w.max() > 0.8 * peak
+
+
 # ----------------------------------------------- unsplit multi-D scheme (R16)
 def test_unsplit_on_a_line_equals_the_1d_sweep():
     """With one active axis the unsplit scheme (Eq. 13 with only the F term)
