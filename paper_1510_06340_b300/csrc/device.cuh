@@ -658,7 +658,8 @@ struct Physics {
         }
         return musta_g<false>(UL, UR, lam, capped);
     }
-    // one FORCE evaluation of Sec. 2.4 (steps 1-4) at (UL, UR), with F(UL), F(UR)
+    // one FORCE evaluation of Sec. 2.4 (steps 1-4) at (UL, UR), with F(UL), F(UR);
+    // the conformal form F_lw / 2 = F(2 U_lw) / 4 (CAP_GROUPS implies p = c2 e)
     template <bool UNCAPPED>
     __device__ __forceinline__ V4<R> musta_stage(const V4<R> &UL, const V4<R> &UR, V4<R> &FL,
                                                  V4<R> &FR, bool &capped) const {
