@@ -8,13 +8,16 @@ Written from the physics, independently of the oracle's code:
   s [T^00] = [T^01], s [T^01] = [T^11];
 * the Bjorken boost-invariant flow v = z/t, e = e0 (tau0/tau)^(1+c^2);
 * the Hubble-like 3-D expansion of Sec. 3.2.2, v = r/t,
-  e = e0 (tau0/tau)^(3(1+c^2)).
+  e = e0 (tau0/tau)^(3(1+c^2));
+* a stationary 2-D vortex: circular flow v_phi(r) held by the radial
+  pressure gradient, dp/dr = (e + p) gamma^2 v_phi^2 / r.
 """
 from __future__ import annotations
 
 import math
 
 import numpy as np
+from scipy.integrate import quad
 from scipy.optimize import brentq
 
 
@@ -111,3 +114,36 @@ def ellipsoidal(coords, t, C=2.0, b=1.0, T=(0.4, 0.6, 0.8)):
     norm = C / np.prod([t + T[i] for i in range(len(coords))])
     e = np.where(inside, norm * np.exp(-b * b * gamma2), 0.0)
     return e, [np.where(inside, vi, 0.0) for vi in v]
+
+
+def vortex(x, y, vmax=0.5, w=0.1, e_far=1.0, c2=1.0 / 3.0):
+    """Stationary vortex of an ideal fluid with p = c^2 e in the xy plane.
+
+    Circular flow v_phi(r) = vmax (r/w) exp((1 - r^2/w^2)/2) (largest, vmax,
+    at r = w).  For steady circular flow the energy equation holds trivially
+    (the flux (e+p) gamma^2 v is divergence-free) and the radial momentum
+    equation is the balance dp/dr = (e + p) gamma^2 v_phi^2 / r, i.e.
+    d ln e / dr = (1 + c^2)/c^2 * v_phi^2 / ((1 - v_phi^2) r), integrated
+    inwards from e = e_far at r = 20 w by adaptive quadrature.  The state is a
+    solution at every time.  Returns (e, vx, vy) on the points (x, y)."""
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    r = np.sqrt(x * x + y * y)
+
+    def vphi(s):
+        return vmax * (s / w) * np.exp(0.5 * (1.0 - (s / w) ** 2))
+
+    def dlne(s):
+        v = vphi(s)
+        return (1.0 + c2) / c2 * v * v / ((1.0 - v * v) * s)
+
+    def lne(s):
+        if s >= 20.0 * w:
+            return math.log(e_far)
+        val, _ = quad(dlne, max(s, 1e-300), 20.0 * w, epsabs=1e-15, epsrel=1e-13, limit=200)
+        return math.log(e_far) - val
+
+    e = np.exp(np.vectorize(lne)(r))
+    vp = vphi(r)
+    rs = np.where(r > 0, r, 1.0)
+    return e, -vp * y / rs, vp * x / rs
