@@ -183,6 +183,10 @@ hydro_status hydro_check_finite(hydro_t *h);
  * The call allocates nothing: its scratch is a 131,104-byte array built into
  * the library and resident on every GPU that loads it until the process
  * exits.  Grids above 268,435,456 cells are rejected with HYDRO_E_INVALID.
+ * Cell sizes follow hydro_create: on an axis of one cell a size <= 0 counts
+ * as 1; on any other axis a size that is not > 0 is HYDRO_E_INVALID.
+ * The call enqueues its kernels and the copy of the four sums on `stream`
+ * and waits for that stream before returning.
  * The first call on each device looks up that array's device address (with
  * that device current), so make the first call before any stream capture.
  * All calls share the array: calls that overlap on the GPU (other streams,
@@ -258,6 +262,11 @@ int hydro_mlp_nparam(void);
  * tensor cores (mma.sync m16n8k16).  All pointers device memory. */
 hydro_status hydro_mlp_forward(const float *params, const float *X, int n, float *out,
                                void *stream);
+/* The first-layer activations of that forward, H1 [n][32] float (device):
+ * tanh of layer 1 rounded to BF16, exactly the values fed to the tensor
+ * cores, so that a check can separate layer 1 from layers 2 and 3. */
+hydro_status hydro_mlp_hidden(const float *params, const float *X, int n, float *H1,
+                              void *stream);
 /* Mean squared error loss and its gradient with respect to the FP32 master
  * parameters (bf16 rounding passed straight through).  Device pointers;
  * grad [nparam] float, loss [1] float. */

@@ -192,19 +192,28 @@ double or_round_bf16(double x) {
     return (double)f;
 }
 
-/* forward for one sample; cache (optional) receives h1[32], h2[32], r */
-static double mlp_forward1(const double *P, int q, double lnE, double x, double *cache) {
-    const double *W1 = P, *b1 = W1 + 2 * MLP_H, *W2 = b1 + MLP_H, *b2 = W2 + MLP_H * MLP_H;
-    const double *W3 = b2 + MLP_H, *b3 = W3 + MLP_H, *nrm = b3 + 1;
+/* layer 1: standardised inputs and h1 = tanh(W1 in + b1), rounded to bf16 when q */
+static void mlp_layer1(const double *P, int q, double lnE, double x, double *h1, double *in0_out,
+                       double *in1_out) {
+    const double *W1 = P, *b1 = W1 + 2 * MLP_H, *nrm = P + MLP_NPARAM - 4;
     double in0 = (lnE - nrm[0]) / nrm[1];
     double in1 = (x - nrm[2]) / nrm[3];
-    double h1[MLP_H], h2[MLP_H];
     for (int j = 0; j < MLP_H; j++) {
         double w0 = q ? or_round_bf16(W1[2 * j]) : W1[2 * j];
         double w1 = q ? or_round_bf16(W1[2 * j + 1]) : W1[2 * j + 1];
         h1[j] = tanh(w0 * in0 + w1 * in1 + b1[j]);
         if (q) h1[j] = or_round_bf16(h1[j]);
     }
+    *in0_out = in0;
+    *in1_out = in1;
+}
+
+/* layers 2 and 3 from h1: h2 = tanh(W2 h1 + b2), z = W3 h2 + b3,
+   v0 = vc + (x - vc) sigmoid(z); h2 and r = sigmoid(z) are returned too */
+static double mlp_layers23(const double *P, int q, double x, const double *h1, double *h2,
+                           double *r_out) {
+    const double *W2 = P + 3 * MLP_H, *b2 = W2 + MLP_H * MLP_H;
+    const double *W3 = b2 + MLP_H, *b3 = W3 + MLP_H;
     for (int j = 0; j < MLP_H; j++) {
         double s = b2[j];
         for (int k = 0; k < MLP_H; k++) {
@@ -220,6 +229,15 @@ static double mlp_forward1(const double *P, int q, double lnE, double x, double 
     }
     double r = 1.0 / (1.0 + exp(-z));
     double vc = 3.0 * x / (2.0 + sqrt(4.0 - 3.0 * x * x));
+    *r_out = r;
+    return vc + (x - vc) * r;
+}
+
+/* forward for one sample; cache (optional) receives h1[32], h2[32], r, in0, in1 */
+static double mlp_forward1(const double *P, int q, double lnE, double x, double *cache) {
+    double h1[MLP_H], h2[MLP_H], in0, in1, r;
+    mlp_layer1(P, q, lnE, x, h1, &in0, &in1);
+    double v0 = mlp_layers23(P, q, x, h1, h2, &r);
     if (cache) {
         memcpy(cache, h1, sizeof h1);
         memcpy(cache + MLP_H, h2, sizeof h2);
@@ -227,7 +245,24 @@ static double mlp_forward1(const double *P, int q, double lnE, double x, double 
         cache[2 * MLP_H + 1] = in0;
         cache[2 * MLP_H + 2] = in1;
     }
-    return vc + (x - vc) * r;
+    return v0;
+}
+
+/* first-layer activations H1[n][32] (bf16-rounded when q) */
+void or_mlp_hidden(const double *P, int q, int n, const double *X, double *H1) {
+    for (int i = 0; i < n; i++) {
+        double in0, in1;
+        mlp_layer1(P, q, X[2 * i], X[2 * i + 1], H1 + (long)i * MLP_H, &in0, &in1);
+    }
+}
+
+/* layers 2 and 3 fed with given first-layer activations H1[n][32] */
+void or_mlp_forward_h1(const double *P, int q, int n, const double *X, const double *H1,
+                       double *out) {
+    for (int i = 0; i < n; i++) {
+        double h2[MLP_H], r;
+        out[i] = mlp_layers23(P, q, X[2 * i + 1], H1 + (long)i * MLP_H, h2, &r);
+    }
 }
 
 /* batch forward: X[n][2] = (ln E, |M|/E), out[n] = seed velocity */

@@ -95,6 +95,8 @@ def lib():
         L.or_round_bf16.restype = C.c_double
         L.or_round_bf16.argtypes = [C.c_double]
         L.or_mlp_forward.argtypes = [_dp, C.c_int, C.c_int, _dp, _dp]
+        L.or_mlp_hidden.argtypes = [_dp, C.c_int, C.c_int, _dp, _dp]
+        L.or_mlp_forward_h1.argtypes = [_dp, C.c_int, C.c_int, _dp, _dp, _dp]
         L.or_mlp_loss_grad.restype = C.c_double
         L.or_mlp_loss_grad.argtypes = [_dp, C.c_int, C.c_int, _dp, _dp, _dp]
         L.or_get_counters.argtypes = [C.POINTER(C.c_long)]
@@ -269,6 +271,25 @@ def mlp_forward(params, X, quantize=0):
     X = np.ascontiguousarray(X, dtype=np.float64)
     out = np.zeros(X.shape[0])
     lib().or_mlp_forward(_ptr(P), quantize, X.shape[0], _ptr(X), _ptr(out))
+    return out
+
+
+def mlp_hidden(params, X, quantize=0):
+    """First-layer activations [n][32] (bf16-rounded with quantize=1)."""
+    P = np.ascontiguousarray(params, dtype=np.float64)
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    H1 = np.zeros((X.shape[0], 32))
+    lib().or_mlp_hidden(_ptr(P), quantize, X.shape[0], _ptr(X), _ptr(H1))
+    return H1
+
+
+def mlp_forward_h1(params, X, H1, quantize=0):
+    """Layers 2 and 3 of the forward fed with the given activations H1 [n][32]."""
+    P = np.ascontiguousarray(params, dtype=np.float64)
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    H1 = np.ascontiguousarray(H1, dtype=np.float64)
+    out = np.zeros(X.shape[0])
+    lib().or_mlp_forward_h1(_ptr(P), quantize, X.shape[0], _ptr(X), _ptr(H1), _ptr(out))
     return out
 
 

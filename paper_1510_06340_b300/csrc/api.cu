@@ -1231,6 +1231,14 @@ hydro_status hydro_mlp_forward(const float *params, const float *X, int n, float
     return HYDRO_OK;
 }
 
+hydro_status hydro_mlp_hidden(const float *params, const float *X, int n, float *H1,
+                              void *stream) {
+    if (!params || !X || !H1 || n < 0) return fail(HYDRO_E_INVALID, "bad argument");
+    CK(launch_mlp_hidden(params, X, n, H1, (cudaStream_t)stream));
+    CK(cudaStreamSynchronize((cudaStream_t)stream));
+    return HYDRO_OK;
+}
+
 hydro_status hydro_mlp_loss_grad(const float *params, const float *X, const float *Y, int n,
                                  float *grad, float *loss, void *stream) {
     if (!params || !X || !Y || !grad || !loss || n < 1) return fail(HYDRO_E_INVALID, "bad argument");

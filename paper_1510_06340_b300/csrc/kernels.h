@@ -91,6 +91,8 @@ cudaError_t launch_c2p_newton(int prec, const Scheme &sc, const void *U, long lo
 // Newton-seed MLP
 cudaError_t launch_mlp_forward(const float *params, const float *X, int n, float *out,
                                cudaStream_t s);
+cudaError_t launch_mlp_hidden(const float *params, const float *X, int n, float *H1,
+                              cudaStream_t s);
 cudaError_t launch_mlp_loss_grad(const float *params, const float *X, const float *Y, int n,
                                  float *grad, float *loss, cudaStream_t s);
 cudaError_t launch_mlp_prepare(const float *params, void *w_bf16, cudaStream_t s);

@@ -43,6 +43,30 @@ __global__ void k_mlp_forward(const float *__restrict__ F, const __nv_bfloat16 *
     if (ok) out[s] = v;
 }
 
+// the bf16-rounded first-layer activations that k_mlp_forward feeds to the
+// tensor cores, H1 [n][32] (same warp forward, its rows kept in shared memory)
+constexpr int HID_WARPS = 4;
+__global__ void __launch_bounds__(32 * HID_WARPS)
+k_mlp_hidden(const float *__restrict__ F, const __nv_bfloat16 *__restrict__ Wb,
+             const float *__restrict__ X, int n, float *__restrict__ H1out) {
+    __shared__ float h1s[HID_WARPS][32 * (MLP_H + 1)];
+    __shared__ float h2s[HID_WARPS][32 * (MLP_H + 1)];
+    const int wl = threadIdx.x >> 5;
+    const int warp = blockIdx.x * HID_WARPS + wl;
+    const int lane = threadIdx.x & 31;
+    const int s = warp * 32 + lane;
+    if (warp * 32 >= n) return;   // whole warp out of range
+    const bool ok = s < n;
+    const float lnE = ok ? X[2 * s] : 0.f, x = ok ? X[2 * s + 1] : 0.f;
+    const float in0 = (lnE - __ldg(F + MLP_OFF_NORM)) / __ldg(F + MLP_OFF_NORM + 1);
+    const float in1 = (x - __ldg(F + MLP_OFF_NORM + 2)) / __ldg(F + MLP_OFF_NORM + 3);
+    float z;
+    mlp_warp_forward<true>(F, Wb, in0, in1, x, h1s[wl], h2s[wl], MLP_H + 1, z);
+    __syncwarp();
+    if (ok)
+        for (int k = 0; k < MLP_H; ++k) H1out[(long long)s * MLP_H + k] = h1s[wl][lane * (MLP_H + 1) + k];
+}
+
 constexpr int TB = 256;          // samples per block in the gradient kernel
 constexpr int LDH = MLP_H + 1;   // padded smem row
 
@@ -166,6 +190,21 @@ cudaError_t launch_mlp_forward(const float *params, const float *X, int n, float
     k_mlp_prepare<<<(MLP_NPARAM + 255) / 256, 256, 0, s>>>(params, w);
     const int warps = (n + 31) / 32;
     if (warps > 0) k_mlp_forward<<<(warps + 3) / 4, 128, 0, s>>>(params, w, X, n, out);
+    e = cudaGetLastError();
+    cudaFreeAsync(w, s);
+    return e;
+}
+
+cudaError_t launch_mlp_hidden(const float *params, const float *X, int n, float *H1,
+                              cudaStream_t s) {
+    __nv_bfloat16 *w;
+    cudaError_t e = cudaMallocAsync(&w, MLP_NPARAM * sizeof(__nv_bfloat16), s);
+    if (e != cudaSuccess) return e;
+    k_mlp_prepare<<<(MLP_NPARAM + 255) / 256, 256, 0, s>>>(params, w);
+    const int warps = (n + 31) / 32;
+    if (warps > 0)
+        k_mlp_hidden<<<(warps + HID_WARPS - 1) / HID_WARPS, 32 * HID_WARPS, 0, s>>>(params, w, X,
+                                                                                  n, H1);
     e = cudaGetLastError();
     cudaFreeAsync(w, s);
     return e;

@@ -102,6 +102,18 @@ extern "C" hydro_status hydro_conservation_sums_noalloc(const void *U, int prec,
         return na_fail(HYDRO_E_INVALID,
                        "grid of " + std::to_string(cells) + " cells exceeds the no-allocation limit of " +
                            std::to_string(NA_MAX_CELLS) + " cells");
+    // cell volume by the rule hydro_create applies: an axis of one cell with a
+    // spacing <= 0 counts as 1; any other spacing must be positive (NaN fails)
+    const int n3[3] = {nx, ny, nz};
+    const double h3[3] = {dx, dy, dz};
+    double dV = 1.0;
+    for (int a = 0; a < 3; ++a) {
+        if (n3[a] > 1 && !(h3[a] > 0.0))
+            return na_fail(HYDRO_E_INVALID, "cell size must be > 0 on an axis of more than one cell");
+        if (n3[a] == 1 && h3[a] != h3[a])
+            return na_fail(HYDRO_E_INVALID, "cell size is NaN");
+        dV *= h3[a] > 0.0 ? h3[a] : 1.0;
+    }
     double *scratch = nullptr;
     hydro_status st = na_scratch(&scratch);
     if (st != HYDRO_OK) return st;
@@ -113,7 +125,7 @@ extern "C" hydro_status hydro_conservation_sums_noalloc(const void *U, int prec,
     else
         k_na_partial<float><<<nblocks, NA_THREADS, 0, s>>>(static_cast<const float *>(U), cells,
                                                             scratch);
-    k_na_final<<<1, 32, 0, s>>>(scratch, nblocks, dx * dy * dz);
+    k_na_final<<<1, 32, 0, s>>>(scratch, nblocks, dV);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(out, scratch + 4 * NA_MAX_BLOCKS, 4 * sizeof(double),

@@ -100,6 +100,7 @@ def lib():
             "hydro_batch_counters": [H, C.POINTER(C.c_longlong)],
             "hydro_conservation_sums_noalloc": [vp, i, i, i, i, d, d, d, dp, vp],
             "hydro_mlp_forward": [vp, vp, i, vp, vp],
+            "hydro_mlp_hidden": [vp, vp, i, vp, vp],
             "hydro_mlp_loss_grad": [vp, vp, vp, i, vp, vp, vp],
             "hydro_mlp_train": [vp, vp, vp, i, i, i, C.c_float, C.c_ulonglong, vp, vp],
         }
@@ -126,26 +127,50 @@ def _is_tensor(a):
     return hasattr(a, "data_ptr") and hasattr(a, "is_cuda")
 
 
-def _arg(a, dtype):
-    """(pointer, on_device, keepalive) for a numpy array or a CUDA tensor."""
+_TORCH_DTYPES = {np.float64: "torch.float64", np.float32: "torch.float32",
+                 np.int32: "torch.int32"}
+
+
+def _arg(a, dtype, numel=None):
+    """(pointer, on_device, keepalive) for a numpy array or a CUDA tensor.
+    numel: the element count the call reads or writes; a shorter buffer is
+    rejected before any pointer reaches the library."""
     if _is_tensor(a):
         if not a.is_cuda:
             a = a.numpy()
         else:
-            want = {np.float64: "torch.float64", np.float32: "torch.float32",
-                    np.int32: "torch.int32"}[dtype]
+            want = _TORCH_DTYPES[dtype]
             if str(a.dtype) != want:
                 raise TypeError(f"tensor dtype {a.dtype}, expected {want}")
             if not a.is_contiguous():
                 raise ValueError("tensor must be contiguous")
+            if numel is not None and a.numel() < numel:
+                raise ValueError(f"tensor holds {a.numel()} elements, the call needs {numel}")
             return C.c_void_p(a.data_ptr()), 1, a
     arr = np.ascontiguousarray(a, dtype=dtype)
+    if numel is not None and arr.size < numel:
+        raise ValueError(f"array holds {arr.size} elements, the call needs {numel}")
     return arr.ctypes.data_as(C.c_void_p), 0, arr
 
 
-def _out_arg(o, dtype):
+def _dev(t, dtype, numel, name="tensor"):
+    """Pointer of a CUDA tensor that a device-only call reads or writes:
+    checked for device, dtype, contiguity and size first."""
+    if not _is_tensor(t) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    want = _TORCH_DTYPES[dtype]
+    if str(t.dtype) != want:
+        raise TypeError(f"{name} dtype {t.dtype}, expected {want}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if t.numel() < numel:
+        raise ValueError(f"{name} holds {t.numel()} elements, the call needs {numel}")
+    return C.c_void_p(t.data_ptr())
+
+
+def _out_arg(o, dtype, numel=None):
     """_arg for an output: a host output must be written in place."""
-    p, dev, keep = _arg(o, dtype)
+    p, dev, keep = _arg(o, dtype, numel)
     if not dev:
         base = o.numpy() if _is_tensor(o) else o
         if not (isinstance(base, np.ndarray) and np.shares_memory(keep, base)):
@@ -244,18 +269,24 @@ class Hydro(_Base):
     def set_stream(self, stream):
         _check(lib().hydro_set_stream(self.h, _stream_ptr(stream)))
 
+    @property
+    def cells(self):
+        return self.grid.nx * self.grid.ny * self.grid.nz
+
     def set_primitives(self, e, vx, vy, vz):
-        args = [_arg(a, self._dtype) for a in (e, vx, vy, vz)]
+        args = [_arg(a, self._dtype, self.cells) for a in (e, vx, vy, vz)]
+        if len({a[1] for a in args}) != 1:
+            raise ValueError("inputs must be all on the host or all on the device")
         _check(lib().hydro_set_primitives(self.h, *[a[0] for a in args], args[0][1]))
 
     def set_conserved(self, U):
-        p, dev, keep = _arg(U, self._dtype)
+        p, dev, keep = _arg(U, self._dtype, 4 * self.cells)
         _check(lib().hydro_set_conserved(self.h, p, dev))
 
     def get_conserved(self, out=None):
         if out is None:
             out = np.empty(self.shape, dtype=self._dtype)
-        p, dev, _ = _arg(out, self._dtype)
+        p, dev, _ = _arg(out, self._dtype, 4 * self.cells)
         if not dev and not (isinstance(out, np.ndarray) and out.flags["C_CONTIGUOUS"]):
             raise ValueError("host output must be a contiguous numpy array")
         _check(lib().hydro_get_conserved(self.h, p, dev))
@@ -267,7 +298,7 @@ class Hydro(_Base):
         four CUDA tensors, of the handle's dtype."""
         if out is None:
             out = [np.empty(self.shape[1:], dtype=self._dtype) for _ in range(4)]
-        args = [_out_arg(o, self._dtype) for o in out]
+        args = [_out_arg(o, self._dtype, self.cells) for o in out]
         if len({a[1] for a in args}) != 1:
             raise ValueError("outputs must be all on the host or all on the device")
         _check(lib().hydro_get_primitives(self.h, *[a[0] for a in args], args[0][1]))
@@ -340,9 +371,11 @@ class Hydro(_Base):
     def c2p_newton(self, U, seed, vmag, iters):
         """Device tensors: U [4][n], vmag [n] (handle dtype), iters [n] int32."""
         n = U.shape[-1]
-        _check(lib().hydro_c2p_newton(self.h, C.c_void_p(U.data_ptr()), n,
-                                      SEEDS[seed] if isinstance(seed, str) else seed,
-                                      C.c_void_p(vmag.data_ptr()), C.c_void_p(iters.data_ptr())))
+        pU = _dev(U, self._dtype, 4 * n, "U")
+        pv = _dev(vmag, self._dtype, n, "vmag")
+        pi = _dev(iters, np.int32, n, "iters")
+        _check(lib().hydro_c2p_newton(self.h, pU, n,
+                                      SEEDS[seed] if isinstance(seed, str) else seed, pv, pi))
 
 
 class Batch(_Base):
@@ -381,8 +414,16 @@ class Batch(_Base):
         _check(lib().hydro_batch_init_hotspots(self.h, s.ctypes.data_as(C.POINTER(C.c_double)),
                                                s.shape[1], sigma, e_bg))
 
+    def _cells(self, event):
+        if not 0 <= event < self.nevents:
+            raise ValueError(f"event {event} out of range")
+        g = self.grids[event]
+        return g.nx * g.ny * g.nz
+
     def set_primitives(self, event, e, vx, vy, vz):
-        args = [_arg(a, self._dtype) for a in (e, vx, vy, vz)]
+        args = [_arg(a, self._dtype, self._cells(event)) for a in (e, vx, vy, vz)]
+        if len({a[1] for a in args}) != 1:
+            raise ValueError("inputs must be all on the host or all on the device")
         _check(lib().hydro_batch_set_primitives(self.h, event, *[a[0] for a in args], args[0][1]))
 
     def set_jets(self, jets):
@@ -395,7 +436,7 @@ class Batch(_Base):
     def get_conserved(self, event, out=None):
         if out is None:
             out = np.empty(self.shape(event), dtype=self._dtype)
-        p, dev, _ = _arg(out, self._dtype)
+        p, dev, _ = _out_arg(out, self._dtype, 4 * self._cells(event))
         _check(lib().hydro_batch_get_conserved(self.h, event, p, dev))
         return out
 
@@ -442,8 +483,12 @@ def conservation_sums_noalloc(U, prec, nx, ny, nz, dx, dy=None, dz=None, stream=
     """FP64 sums of a caller-held device state U [4][nz][ny][nx] without any
     device allocation by the library (see hydro_conservation_sums_noalloc)."""
     out = (C.c_double * 4)()
+    pr = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
+    if pr not in (0, 1, 2):
+        raise ValueError(f"unknown precision {prec}")
+    pU = _dev(U, np.float64 if pr == 0 else np.float32, 4 * nx * ny * nz, "U")
     _check(lib().hydro_conservation_sums_noalloc(
-        C.c_void_p(U.data_ptr()), PRECISIONS[prec] if isinstance(prec, str) else int(prec),
+        pU, pr,
         nx, ny, nz, dx, dx if dy is None else dy, dx if dz is None else dz, out,
         _stream_ptr(stream)))
     return np.array(out[:])
@@ -454,20 +499,36 @@ def mlp_nparam():
     return lib().hydro_mlp_nparam()
 
 
+def _mlp_args(params, X):
+    n = X.shape[0]
+    return n, _dev(params, np.float32, mlp_nparam(), "params"), _dev(X, np.float32, 2 * n, "X")
+
+
 def mlp_forward(params, X, out, stream=None):
     """Device float32 tensors: params [nparam], X [n][2], out [n]."""
-    _check(lib().hydro_mlp_forward(C.c_void_p(params.data_ptr()), C.c_void_p(X.data_ptr()),
-                                   X.shape[0], C.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+    n, pp, px = _mlp_args(params, X)
+    _check(lib().hydro_mlp_forward(pp, px, n, _dev(out, np.float32, n, "out"),
+                                   _stream_ptr(stream)))
+
+
+def mlp_hidden(params, X, H1, stream=None):
+    """Device float32 tensors: params [nparam], X [n][2], H1 [n][32] receives
+    the bf16-rounded first-layer activations the forward feeds to the tensor
+    cores."""
+    n, pp, px = _mlp_args(params, X)
+    _check(lib().hydro_mlp_hidden(pp, px, n, _dev(H1, np.float32, 32 * n, "H1"),
+                                  _stream_ptr(stream)))
 
 
 def mlp_loss_grad(params, X, Y, grad, loss, stream=None):
-    _check(lib().hydro_mlp_loss_grad(C.c_void_p(params.data_ptr()), C.c_void_p(X.data_ptr()),
-                                     C.c_void_p(Y.data_ptr()), X.shape[0],
-                                     C.c_void_p(grad.data_ptr()), C.c_void_p(loss.data_ptr()),
-                                     _stream_ptr(stream)))
+    n, pp, px = _mlp_args(params, X)
+    _check(lib().hydro_mlp_loss_grad(pp, px, _dev(Y, np.float32, n, "Y"), n,
+                                     _dev(grad, np.float32, mlp_nparam(), "grad"),
+                                     _dev(loss, np.float32, 1, "loss"), _stream_ptr(stream)))
 
 
 def mlp_train(params, X, Y, batch, epochs, lr, seed, loss_hist, stream=None):
-    _check(lib().hydro_mlp_train(C.c_void_p(params.data_ptr()), C.c_void_p(X.data_ptr()),
-                                 C.c_void_p(Y.data_ptr()), X.shape[0], batch, epochs, lr, seed,
-                                 C.c_void_p(loss_hist.data_ptr()), _stream_ptr(stream)))
+    n, pp, px = _mlp_args(params, X)
+    _check(lib().hydro_mlp_train(pp, px, _dev(Y, np.float32, n, "Y"), n, batch, epochs, lr,
+                                 seed, _dev(loss_hist, np.float32, epochs, "loss_hist"),
+                                 _stream_ptr(stream)))

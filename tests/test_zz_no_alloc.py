@@ -44,9 +44,36 @@ def test_noalloc_sums_match_the_handle_sums_twice(H, prec):
             np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-12 * abs(want[0]))
 
 
-def test_noalloc_rejects_grids_over_its_limit(H):
+def test_noalloc_one_axis_grid_uses_the_handle_cell_volume(H):
+    """A 1-D grid created with dy = dz = 0: the handle counts those axes as 1,
+    and so does the no-allocation call."""
+    import torch
+    n = 64
+    g, prim = I.shock_tube(n)
+    grid = H.make_grid(n, dx=g["dx"], dy=0.0, dz=0.0, x0=-1.0, bc="outflow")
+    h = H.Hydro(grid)
+    h.set_primitives(*prim)
+    h.step(5)
+    want = h.conservation_sums()
+    U = torch.empty((4, 1, 1, n), dtype=torch.float64, device="cuda")
+    h.get_conserved(out=U)
+    torch.cuda.synchronize()
+    got = H.conservation_sums_noalloc(U, "fp64", n, 1, 1, g["dx"], 0.0, 0.0)
+    np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-12 * abs(want[0]))
+
+
+def _raw_call(H, U, prec, nx, ny, nz, dx, dy, dz):
+    """The entry point itself, without the binding's own size checks."""
+    import ctypes as C
+    out = (C.c_double * 4)()
+    return H.lib().hydro_conservation_sums_noalloc(C.c_void_p(U.data_ptr()), prec, nx, ny, nz,
+                                                   dx, dy, dz, out, None)
+
+
+def test_noalloc_rejects_grids_over_its_limit_and_bad_cell_sizes(H):
     import torch
     U = torch.zeros(16, dtype=torch.float64, device="cuda")
-    with pytest.raises(H.HydroError) as ei:
-        H.conservation_sums_noalloc(U, "fp64", 1 << 15, 1 << 14, 1, 0.1)
-    assert ei.value.status == 1 and "limit" in str(ei.value)
+    assert _raw_call(H, U, 0, 1 << 15, 1 << 14, 1, 0.1, 0.1, 0.1) == 1
+    assert "limit" in H.lib().hydro_last_error().decode()
+    assert _raw_call(H, U, 0, 2, 2, 1, 0.1, 0.0, 0.1) == 1
+    assert _raw_call(H, U, 0, 2, 2, 1, float("nan"), 0.1, 0.1) == 1
