@@ -65,6 +65,9 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef OR_OPENMP
+#include <omp.h>
+#endif
 
 /* ---------------------------------------------------------------- config */
 typedef struct {
@@ -94,9 +97,24 @@ typedef struct {
     int unsplit;               /* 1: unsplit multi-D scheme (R16) instead of Strang sweeps */
 } or_config;
 
-/* diagnostics counters (reset by or_reset_counters) */
+/* diagnostics counters (reset by or_reset_counters); the OpenMP timing build
+   (OR_OPENMP) runs pencils on several threads and keeps no counts */
 static long g_newton_calls = 0, g_newton_iters = 0, g_newton_fail = 0;
 static long g_capped = 0, g_face_fallback = 0;
+#ifdef OR_OPENMP
+#define OR_TALLY(counter, n) ((void)0)
+#else
+#define OR_TALLY(counter, n) ((counter) += (n))
+#endif
+
+/* threads a parallel region of this build uses (1 without OpenMP) */
+int or_threads(void) {
+#ifdef OR_OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
 
 void or_reset_counters(void) {
     g_newton_calls = g_newton_iters = g_newton_fail = 0;
@@ -344,7 +362,7 @@ int or_cons2prim(const or_config *c, const double U[4], double *e_out, double v[
         Mx *= s; My *= s; Mz *= s;
         M2 = Mx * Mx + My * My + Mz * Mz;
         status = 1;
-        g_capped++;
+        OR_TALLY(g_capped, 1);
     }
     double M = sqrt(M2);
     if (c->eos_kind == 0) {
@@ -359,7 +377,7 @@ int or_cons2prim(const or_config *c, const double U[4], double *e_out, double v[
         return status;
     }
     /* R11: safeguarded Newton on f(v) = v - M/(E + p(E - M v)), v in [0, M/E] */
-    g_newton_calls++;
+    OR_TALLY(g_newton_calls, 1);
     double lo = 0.0, hi = M / E;
     double vv;
     if (c->seed_kind == 1) {
@@ -394,9 +412,9 @@ int or_cons2prim(const or_config *c, const double U[4], double *e_out, double v[
         }
         if (it > 50) it = 50;
     }
-    g_newton_iters += it;
+    OR_TALLY(g_newton_iters, it);
     if (iters) *iters = it;
-    if (!conv) { g_newton_fail++; status = 3; }
+    if (!conv) { OR_TALLY(g_newton_fail, 1); status = 3; }
     double e = E - M * vv;
     or_eos_table(c, e, &p, &c2);
     double sc = (M > 0.0) ? vv / M : 0.0;
@@ -490,7 +508,7 @@ void or_hancock_faces(const or_config *c, int d, double lam, const double Vm[4],
     if (!admissible(c, ULt) || !admissible(c, URt)) {
         memcpy(ULt, V0, 4 * sizeof(double));
         memcpy(URt, V0, 4 * sizeof(double));
-        g_face_fallback++;
+        OR_TALLY(g_face_fallback, 1);
     }
 }
 
@@ -519,7 +537,8 @@ static void pencil_L(const or_config *c, int d, double lam, double (*V)[4], int 
         for (int q = 0; q < 4; q++) D[i][q] = F[i + 1][q] - F[i][q];
 }
 
-/* one Runge-Kutta sweep (Sec. 2.3, Eq. 6 or 7) of every pencil along axis d */
+/* one Runge-Kutta sweep (Sec. 2.3, Eq. 6 or 7) of every pencil along axis d;
+   pencils are independent, so the OpenMP timing build splits them over threads */
 void or_sweep(const or_config *c, double *U, int d, double dt) {
     int n[3] = {c->nx, c->ny, c->nz};
     double h[3] = {c->dx, c->dy, c->dz};
@@ -528,55 +547,63 @@ void or_sweep(const or_config *c, double *U, int d, double dt) {
     long stride = (d == 0) ? 1 : (d == 1) ? c->nx : (long)c->nx * c->ny;
     double lam = dt / h[d];
     int a_ax = (d == 0) ? 1 : 0, b_ax = (d == 2) ? 1 : 2;
-    double (*V0)[4] = malloc(sizeof(double[4]) * (N + 4));
-    double (*V1)[4] = malloc(sizeof(double[4]) * (N + 4));
-    double (*V2)[4] = malloc(sizeof(double[4]) * (N + 4));
-    double (*D)[4] = malloc(sizeof(double[4]) * N);
-    double (*ULt)[4] = malloc(sizeof(double[4]) * (N + 2));
-    double (*URt)[4] = malloc(sizeof(double[4]) * (N + 2));
-    double (*F)[4] = malloc(sizeof(double[4]) * (N + 1));
-    for (int b = 0; b < n[b_ax]; b++) {
-        for (int a = 0; a < n[a_ax]; a++) {
-            int idx[3];
-            idx[d] = 0; idx[a_ax] = a; idx[b_ax] = b;
-            long base = idx[0] + (long)c->nx * (idx[1] + (long)c->ny * idx[2]);
+    long npencils = (long)n[a_ax] * n[b_ax];
+#ifdef OR_OPENMP
+#pragma omp parallel
+#endif
+    {
+    double (*V0)[4] = (double (*)[4])malloc(sizeof(double[4]) * (N + 4));
+    double (*V1)[4] = (double (*)[4])malloc(sizeof(double[4]) * (N + 4));
+    double (*V2)[4] = (double (*)[4])malloc(sizeof(double[4]) * (N + 4));
+    double (*D)[4] = (double (*)[4])malloc(sizeof(double[4]) * N);
+    double (*ULt)[4] = (double (*)[4])malloc(sizeof(double[4]) * (N + 2));
+    double (*URt)[4] = (double (*)[4])malloc(sizeof(double[4]) * (N + 2));
+    double (*F)[4] = (double (*)[4])malloc(sizeof(double[4]) * (N + 1));
+#ifdef OR_OPENMP
+#pragma omp for schedule(static)
+#endif
+    for (long pc = 0; pc < npencils; pc++) {
+        int a = (int)(pc % n[a_ax]), b = (int)(pc / n[a_ax]);
+        int idx[3];
+        idx[d] = 0; idx[a_ax] = a; idx[b_ax] = b;
+        long base = idx[0] + (long)c->nx * (idx[1] + (long)c->ny * idx[2]);
+        for (int i = 0; i < N; i++)
+            for (int q = 0; q < 4; q++) V0[i + 2][q] = U[q * cells + base + i * stride];
+        fill_ghosts(V0, N, c->bc[d]);
+        /* stage 1: U1 = U + dt L(U) */
+        pencil_L(c, d, lam, V0, N, D, ULt, URt, F);
+        if (c->rk_order == 1) {
             for (int i = 0; i < N; i++)
-                for (int q = 0; q < 4; q++) V0[i + 2][q] = U[q * cells + base + i * stride];
-            fill_ghosts(V0, N, c->bc[d]);
-            /* stage 1: U1 = U + dt L(U) */
-            pencil_L(c, d, lam, V0, N, D, ULt, URt, F);
-            if (c->rk_order == 1) {
-                for (int i = 0; i < N; i++)
-                    for (int q = 0; q < 4; q++)
-                        U[q * cells + base + i * stride] = V0[i + 2][q] - lam * D[i][q];
-                continue;
-            }
+                for (int q = 0; q < 4; q++)
+                    U[q * cells + base + i * stride] = V0[i + 2][q] - lam * D[i][q];
+            continue;
+        }
+        for (int i = 0; i < N; i++)
+            for (int q = 0; q < 4; q++) V1[i + 2][q] = V0[i + 2][q] - lam * D[i][q];
+        fill_ghosts(V1, N, c->bc[d]);
+        pencil_L(c, d, lam, V1, N, D, ULt, URt, F);
+        if (c->rk_order == 3) {
+            /* U2 = 3/4 U + 1/4 U1 + 1/4 dt L(U1) */
             for (int i = 0; i < N; i++)
-                for (int q = 0; q < 4; q++) V1[i + 2][q] = V0[i + 2][q] - lam * D[i][q];
-            fill_ghosts(V1, N, c->bc[d]);
-            pencil_L(c, d, lam, V1, N, D, ULt, URt, F);
-            if (c->rk_order == 3) {
-                /* U2 = 3/4 U + 1/4 U1 + 1/4 dt L(U1) */
-                for (int i = 0; i < N; i++)
-                    for (int q = 0; q < 4; q++)
-                        V2[i + 2][q] = 0.75 * V0[i + 2][q] + 0.25 * (V1[i + 2][q] - lam * D[i][q]);
-                fill_ghosts(V2, N, c->bc[d]);
-                pencil_L(c, d, lam, V2, N, D, ULt, URt, F);
-                /* U^{n+1} = 1/3 U + 2/3 U2 + 2/3 dt L(U2) */
-                for (int i = 0; i < N; i++)
-                    for (int q = 0; q < 4; q++)
-                        U[q * cells + base + i * stride] =
-                            V0[i + 2][q] / 3.0 + (2.0 / 3.0) * (V2[i + 2][q] - lam * D[i][q]);
-            } else {
-                /* U^{n+1} = 1/2 (U + U1 + dt L(U1)) */
-                for (int i = 0; i < N; i++)
-                    for (int q = 0; q < 4; q++)
-                        U[q * cells + base + i * stride] =
-                            0.5 * (V0[i + 2][q] + V1[i + 2][q] - lam * D[i][q]);
-            }
+                for (int q = 0; q < 4; q++)
+                    V2[i + 2][q] = 0.75 * V0[i + 2][q] + 0.25 * (V1[i + 2][q] - lam * D[i][q]);
+            fill_ghosts(V2, N, c->bc[d]);
+            pencil_L(c, d, lam, V2, N, D, ULt, URt, F);
+            /* U^{n+1} = 1/3 U + 2/3 U2 + 2/3 dt L(U2) */
+            for (int i = 0; i < N; i++)
+                for (int q = 0; q < 4; q++)
+                    U[q * cells + base + i * stride] =
+                        V0[i + 2][q] / 3.0 + (2.0 / 3.0) * (V2[i + 2][q] - lam * D[i][q]);
+        } else {
+            /* U^{n+1} = 1/2 (U + U1 + dt L(U1)) */
+            for (int i = 0; i < N; i++)
+                for (int q = 0; q < 4; q++)
+                    U[q * cells + base + i * stride] =
+                        0.5 * (V0[i + 2][q] + V1[i + 2][q] - lam * D[i][q]);
         }
     }
     free(V0); free(V1); free(V2); free(D); free(ULt); free(URt); free(F);
+    }
 }
 
 /* ------------------------------------------------------------------ CFL */
@@ -602,6 +629,9 @@ double or_max_rate(const or_config *c, const double *U) {
     int n[3] = {c->nx, c->ny, c->nz};
     double h[3] = {c->dx, c->dy, c->dz};
     double m = 0.0;
+#ifdef OR_OPENMP
+#pragma omp parallel for reduction(max : m) schedule(static)
+#endif
     for (long i = 0; i < cells; i++) {
         double u[4] = {U[i], U[cells + i], U[2 * cells + i], U[3 * cells + i]};
         for (int d = 0; d < 3; d++) {
@@ -671,8 +701,8 @@ static void unsplit_L(const or_config *c, const double *U, double dt, double *D)
     long mcells = (long)m[0] * m[1] * m[2];
     long cells = (long)n[0] * n[1] * n[2];
     /* evolved faces: FL[d][cell of the grown box][q], FR likewise */
-    double *FLf = malloc(sizeof(double) * 3 * mcells * 4);
-    double *FRf = malloc(sizeof(double) * 3 * mcells * 4);
+    double *FLf = (double *)malloc(sizeof(double) * 3 * mcells * 4);
+    double *FRf = (double *)malloc(sizeof(double) * 3 * mcells * 4);
     for (int k = -g[2]; k < n[2] + g[2]; k++)
         for (int j = -g[1]; j < n[1] + g[1]; j++)
             for (int i = -g[0]; i < n[0] + g[0]; i++) {
@@ -709,7 +739,7 @@ static void unsplit_L(const or_config *c, const double *U, double dt, double *D)
                     }
                     if (!admissible(c, UL[d]) || !admissible(c, UR[d])) ok = 0;
                 }
-                if (!ok) g_face_fallback++;
+                if (!ok) OR_TALLY(g_face_fallback, 1);
                 for (int d = 0; d < 3; d++) {
                     if (!act[d]) continue;
                     for (int q = 0; q < 4; q++) {
@@ -751,9 +781,9 @@ static void unsplit_L(const or_config *c, const double *U, double dt, double *D)
 static void unsplit_rk(const or_config *c, double *U, double dt) {
     long cells = (long)c->nx * c->ny * c->nz;
     long nv = 4 * cells;
-    double *D = malloc(sizeof(double) * nv);
-    double *U1 = malloc(sizeof(double) * nv);
-    double *U2 = malloc(sizeof(double) * nv);
+    double *D = (double *)malloc(sizeof(double) * nv);
+    double *U1 = (double *)malloc(sizeof(double) * nv);
+    double *U2 = (double *)malloc(sizeof(double) * nv);
     unsplit_L(c, U, dt, D);
     if (c->rk_order == 1) {
         for (long x = 0; x < nv; x++) U[x] = U[x] - D[x];

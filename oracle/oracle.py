@@ -20,18 +20,39 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "musta_oracle.c")
 _LIB = os.path.join(_HERE, "libmusta_oracle.so")
+# the same source with its pencil loops split over threads (timing only)
+_LIB_OMP = os.path.join(_HERE, "libmusta_oracle_omp.so")
+# the same source compiled as C++ with an operation-counting double
+_OPC_SRC = os.path.join(_HERE, "opcount.cpp")
+_LIB_OPC = os.path.join(_HERE, "libmusta_opcount.so")
 
 LIMITERS = {"none": 0, "minmod": 1, "mc": 2, "superbee": 3, "vanleer": 4, "vanalbada": 5}
 BC = {"periodic": 0, "outflow": 1}
 
 
+def _stale(lib, srcs):
+    return not os.path.exists(lib) or any(os.path.getmtime(lib) < os.path.getmtime(s)
+                                          for s in srcs)
+
+
+def _compile(cmd, lib):
+    tmp = lib + f".tmp{os.getpid()}"
+    subprocess.check_call(cmd + ["-o", tmp])
+    os.replace(tmp, lib)
+
+
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (plain -O2, no fast-math, no FMA contraction)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c99", "-D_DEFAULT_SOURCE", "-fPIC",
-                               "-ffp-contract=off", "-shared", "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB)
+    """Compile the oracle with gcc (plain -O2, no fast-math, no FMA contraction),
+    its OpenMP timing build and its op-counting build."""
+    if force or _stale(_LIB, [_SRC]):
+        _compile(["gcc", "-O2", "-std=c99", "-D_DEFAULT_SOURCE", "-fPIC", "-ffp-contract=off",
+                  "-shared", _SRC, "-lm"], _LIB)
+    if force or _stale(_LIB_OMP, [_SRC]):
+        _compile(["gcc", "-O2", "-std=c99", "-D_DEFAULT_SOURCE", "-fPIC", "-ffp-contract=off",
+                  "-fopenmp", "-DOR_OPENMP", "-shared", _SRC, "-lm"], _LIB_OMP)
+    if force or _stale(_LIB_OPC, [_SRC, _OPC_SRC]):
+        _compile(["g++", "-O1", "-std=c++17", "-D_DEFAULT_SOURCE", "-fPIC", "-ffp-contract=off",
+                  "-shared", _OPC_SRC], _LIB_OPC)
     return _LIB
 
 
@@ -55,13 +76,30 @@ class _Cfg(C.Structure):
 
 
 _lib = None
+_lib_omp = None
+_lib_opc = None
 _dp = C.POINTER(C.c_double)
 
 
 def lib():
     global _lib
     if _lib is None:
-        L = C.CDLL(build())
+        _lib = _bind(C.CDLL(build()))
+    return _lib
+
+
+def lib_omp():
+    """The OpenMP timing build (pencils of a sweep split over all host threads);
+    the same arithmetic per pencil, without the diagnostics counters."""
+    global _lib_omp
+    if _lib_omp is None:
+        build()
+        _lib_omp = _bind(C.CDLL(_LIB_OMP))
+    return _lib_omp
+
+
+def _bind(L):
+    if True:
         P = C.POINTER(_Cfg)
         L.or_limiter.restype = C.c_double
         L.or_limiter.argtypes = [C.c_int, C.c_double, C.c_double]
@@ -100,8 +138,8 @@ def lib():
         L.or_mlp_loss_grad.restype = C.c_double
         L.or_mlp_loss_grad.argtypes = [_dp, C.c_int, C.c_int, _dp, _dp, _dp]
         L.or_get_counters.argtypes = [C.POINTER(C.c_long)]
-        _lib = L
-    return _lib
+        L.or_threads.restype = C.c_int
+    return L
 
 
 def _ptr(a: np.ndarray):
@@ -236,9 +274,11 @@ class Oracle:
     def step(self, U, t=0.0, t_end=0.0):
         return lib().or_step(C.byref(self.c), _ptr(U), t, t_end)
 
-    def run(self, U, nsteps, t_end=0.0, t=0.0):
+    def run(self, U, nsteps, t_end=0.0, t=0.0, threads=False):
+        """Advance U in place; threads=True runs the OpenMP timing build."""
         tt = C.c_double(t)
-        n = lib().or_run(C.byref(self.c), _ptr(U), nsteps, t_end, C.byref(tt))
+        L = lib_omp() if threads else lib()
+        n = L.or_run(C.byref(self.c), _ptr(U), nsteps, t_end, C.byref(tt))
         return n, tt.value
 
     def conservation_sums(self, U):
@@ -300,3 +340,49 @@ def mlp_loss_grad(params, X, Y, quantize=0):
     G = np.zeros_like(P)
     loss = lib().or_mlp_loss_grad(_ptr(P), quantize, X.shape[0], _ptr(X), _ptr(Y), _ptr(G))
     return loss, G
+
+
+# ------------------------------------------------------------ op counting
+OP_KINDS = ("leaf", "add", "sub", "mul", "div", "sqrt", "min", "max", "exp", "log", "tanh",
+            "abs", "neg", "floor")
+FLOP_KINDS = ("add", "sub", "mul", "div", "sqrt", "min", "max")
+
+
+def _opc():
+    global _lib_opc
+    if _lib_opc is None:
+        build()
+        L = C.CDLL(_LIB_OPC)
+        L.or_opcount_nkind.restype = C.c_int
+        L.or_opcount_sweep.restype = C.c_int
+        L.or_opcount_sweep.argtypes = [C.c_int] * 6 + [C.POINTER(C.c_longlong)]
+        L.or_opcount_unsplit.restype = C.c_int
+        L.or_opcount_unsplit.argtypes = [C.c_int] * 4 + [C.POINTER(C.c_longlong)]
+        assert L.or_opcount_nkind() == len(OP_KINDS)
+        _lib_opc = L
+    return _lib_opc
+
+
+def opcount_sweep(limiter="minmod", stages=2, rk_order=2, hancock=1, n1=32, n2=64):
+    """Operations per cell of one oracle sweep (conformal EOS), by kind, from
+    the op-counting build: distinct operations on state-derived values that
+    the output depends on.  'flops' sums FLOP_KINDS."""
+    out = (C.c_longlong * len(OP_KINDS))()
+    lim = LIMITERS[limiter] if isinstance(limiter, str) else int(limiter)
+    rc = _opc().or_opcount_sweep(lim, stages, rk_order, hancock, n1, n2, out)
+    if rc != 0:
+        raise RuntimeError("operation count is not a whole number per cell")
+    d = dict(zip(OP_KINDS, out[:]))
+    d["flops"] = sum(d[k] for k in FLOP_KINDS)
+    return d
+
+
+def opcount_unsplit(stages=2, rk_order=2, hancock=1, n=8):
+    """Operations per cell and RK stage of the unsplit scheme, counted the same way."""
+    out = (C.c_longlong * len(OP_KINDS))()
+    rc = _opc().or_opcount_unsplit(stages, rk_order, hancock, n, out)
+    if rc != 0:
+        raise RuntimeError("operation count is not a whole number per cell and stage")
+    d = dict(zip(OP_KINDS, out[:]))
+    d["flops"] = sum(d[k] for k in FLOP_KINDS)
+    return d

@@ -710,3 +710,41 @@ def test_ellipsoidal_flow_1d_converges_to_the_exact_dust_solution():
     e2 = ellipsoidal_1d_error(240)
     assert e1 < 2e-3
     assert e2 < e1 / 1.8
+
+
+# ----------------------------------------------- op counting and timing builds
+def test_op_count_of_a_sweep_follows_the_method_structure():
+    """The op-counting build counts one square root and one division per flux
+    evaluation of the p = c^2 e cons->prim (W from the quadratic, v_d = M_d/W),
+    and a sweep makes 2 Hancock + 3k MUSTA-FORCE evaluations per cell and RK
+    stage (Sec. 2.4): rk (2 + 3k) of each.  RK3's combination adds the
+    division U/3 per field."""
+    for stages, rk in ((1, 2), (2, 2), (3, 2), (2, 1), (4, 3)):
+        d = O.opcount_sweep("minmod", stages, rk)
+        evals = rk * (2 + 3 * stages)
+        assert d["sqrt"] == evals, (stages, rk, d)
+        assert d["div"] == evals + (4 if rk == 3 else 0), (stages, rk, d)
+        # Minbee: one min per field and RK stage; no transcendental anywhere
+        assert d["min"] == 4 * rk and d["max"] == 0
+        assert d["exp"] == d["log"] == d["tanh"] == 0
+
+
+def test_op_counts_pin_the_benchmark_flops():
+    """The algorithmic flops the benchmark reports are the op-counting build's."""
+    import bench
+    for (lim, stages, rk), flops in bench.FLOPS_PER_CELL_SWEEP.items():
+        assert O.opcount_sweep(lim, stages, rk)["flops"] == flops, (lim, stages, rk)
+    for (stages, rk), flops in bench.FLOPS_PER_CELL_STAGE_UNSPLIT.items():
+        assert O.opcount_unsplit(stages, rk)["flops"] == flops
+        # uniform per cell: the same count on a larger periodic grid
+        assert O.opcount_unsplit(stages, rk, n=10)["flops"] == flops
+
+
+def test_openmp_timing_build_equals_the_oracle_bit_for_bit():
+    g, prim = I.spherical_blast(20)
+    o = O.Oracle(20, 20, 20, dx=g["dx"], x0=-1.0, y0=-1.0, z0=-1.0, bc="periodic")
+    U1 = o.prim2cons_field(*prim)
+    U2 = U1.copy()
+    o.run(U1, 2)
+    o.run(U2, 2, threads=True)
+    assert np.array_equal(U1, U2)
