@@ -20,9 +20,10 @@
  *    buffers are borrowed for the duration of the call only; the library
  *    owns all of its device state.
  *  - Every call returns a hydro_status; on failure hydro_last_error() gives
- *    a message (thread-local).  Device-side trouble (capped |M|, Newton
- *    non-convergence, non-finite values) is counted in device words read by
- *    hydro_counters(); nothing traps.
+ *    a message (thread-local).  Device-side trouble never traps: the kernels
+ *    set per-event status bits (HYDRO_FLAG_*) that hydro_check_status and
+ *    hydro_batch_event_status read after the steps, and opt-in counters
+ *    (hydro_counters) count each kind of event.
  *  - Handles are not thread-safe.  Calls on one handle are ordered on its
  *    stream; calls that return host data synchronise that stream.
  */
@@ -40,8 +41,8 @@ typedef enum {
     HYDRO_E_INVALID = 1,      /* bad argument or configuration */
     HYDRO_E_OOM = 2,          /* device allocation failed */
     HYDRO_E_CUDA = 3,         /* a CUDA runtime call failed */
-    HYDRO_E_UNPHYSICAL = 4,   /* reserved: unphysical state reported by a check */
-    HYDRO_E_NEWTON = 5,       /* reserved: Newton solve did not converge */
+    HYDRO_E_UNPHYSICAL = 4,   /* an inadmissible state was met and repaired (status checks) */
+    HYDRO_E_NEWTON = 5,       /* a Newton cons->prim solve hit its iteration cap (status checks) */
     HYDRO_E_NONFINITE = 6     /* the state holds NaN or Inf (hydro_check_finite) */
 } hydro_status;
 
@@ -101,7 +102,17 @@ typedef struct {
     int seed;                 /* hydro_seed (TABLE only) */
     const float *mlp_params;  /* host array [hydro_mlp_nparam()] (copied), for HYDRO_SEED_MLP */
     double newton_tol;        /* |dv| stop of the Newton solve; <= 0 picks 1e-13 (FP64) or 2e-6 (FP32) */
+    int newton_max_iter;      /* iteration cap of the Newton solve, 1..1000; <= 0 picks 50.  A
+                                 solve that reaches it keeps its bracketed iterate and sets
+                                 HYDRO_FLAG_NEWTON on its event */
 } hydro_eos_t;
+
+/* Per-event status bits set by the kernels; they accumulate until the
+ * event's state is set again (set_primitives, set_conserved, init_hotspots). */
+#define HYDRO_FLAG_NEWTON 1u      /* a Newton cons->prim solve hit newton_max_iter */
+#define HYDRO_FLAG_UNPHYSICAL 2u  /* |M| >= (1 - delta) E met and capped in cons->prim, or a
+                                     cell's evolved faces were inadmissible and fell back to
+                                     its average (the admissibility rule of the scheme) */
 
 typedef struct hydro_s hydro_t;
 typedef struct hydro_batch_s hydro_batch_t;
@@ -174,6 +185,12 @@ hydro_status hydro_counters(hydro_t *h, long long out[6]);
 
 /* HYDRO_E_NONFINITE if any state value is NaN or Inf, else HYDRO_OK. */
 hydro_status hydro_check_finite(hydro_t *h);
+/* The handle's status after the steps so far: HYDRO_E_NONFINITE (NaN or Inf
+ * in the state), else HYDRO_E_NEWTON (HYDRO_FLAG_NEWTON set), else
+ * HYDRO_E_UNPHYSICAL (HYDRO_FLAG_UNPHYSICAL set), else HYDRO_OK.  flags (may
+ * be NULL) receives the raw HYDRO_FLAG_* bits.  Synchronises the stream;
+ * hydro_step itself does not wait to read them. */
+hydro_status hydro_check_status(hydro_t *h, unsigned *flags);
 
 /* The same four FP64 sums for callers that cannot allocate device memory
  * (the paper has no counterpart; this is an interface for such callers).
@@ -217,6 +234,8 @@ hydro_status hydro_batch_set_jets(hydro_batch_t *b, const double *jets);
  * sweep covers all events; use_graph = 1 captures one step in a CUDA graph
  * on first use and replays it. */
 hydro_status hydro_batch_step(hydro_batch_t *b, int nsteps, int use_graph);
+/* Set / read one event's conserved state U[4][nz][ny][nx] (setting clears its status bits). */
+hydro_status hydro_batch_set_conserved(hydro_batch_t *b, int event, const void *U, int on_device);
 hydro_status hydro_batch_get_conserved(hydro_batch_t *b, int event, void *U, int on_device);
 hydro_status hydro_batch_get_primitives(hydro_batch_t *b, int event, void *e, void *vx,
                                         void *vy, void *vz, int on_device);
@@ -224,8 +243,11 @@ hydro_status hydro_batch_get_primitives(hydro_batch_t *b, int event, void *e, vo
 hydro_status hydro_batch_times(hydro_batch_t *b, double *times);
 /* out: host [nevents][4], FP64 sums as hydro_conservation_sums. */
 hydro_status hydro_batch_conservation_sums(hydro_batch_t *b, double *out);
-/* status: host [nevents]; 0 ok, else a hydro_status (HYDRO_E_NONFINITE). */
+/* status: host [nevents]; per event the code hydro_check_status gives: 0 ok,
+ * else HYDRO_E_NONFINITE, HYDRO_E_NEWTON or HYDRO_E_UNPHYSICAL. */
 hydro_status hydro_batch_event_status(hydro_batch_t *b, int *status);
+/* The same codes and the raw HYDRO_FLAG_* bits per event (host [nevents] each). */
+hydro_status hydro_batch_event_flags(hydro_batch_t *b, int *status, unsigned *flags);
 hydro_status hydro_batch_enable_counters(hydro_batch_t *b, int on);
 hydro_status hydro_batch_counters(hydro_batch_t *b, long long out[6]);
 

@@ -94,6 +94,7 @@ struct Solver {
     float *d_mlp_f = nullptr;
     void *d_mlp_w = nullptr;
     unsigned long long *d_counters = nullptr;
+    unsigned *d_flags = nullptr;       // FLAG_* status word per event
     bool counters_on = false;
     bool any_jet = false;
     long long jet_cells = 0;   // largest box of cells around a jet (k_jet threads per event)
@@ -136,7 +137,7 @@ struct Solver {
         own_stream = nullptr;
         void *ptrs[] = {d_geo, d_clk, d_clk_tune, d_state[0], d_state[1], d_cell_items,
                         d_sweep_items[0], d_sweep_items[1], d_sweep_items[2], d_partial, d_sums,
-                        d_p64, d_c64, d_p32, d_c32, d_mlp_f, d_mlp_w, d_counters,
+                        d_p64, d_c64, d_p32, d_c32, d_mlp_f, d_mlp_w, d_counters, d_flags,
                         d_work_counter, d_ugeo, d_faces, d_fluxes, d_stage[0], d_stage[1],
                         d_us_face_items, d_us_flux_items[0], d_us_flux_items[1],
                         d_us_flux_items[2]};
@@ -153,6 +154,7 @@ struct Solver {
         d_mlp_f = nullptr;
         d_mlp_w = nullptr;
         d_counters = nullptr;
+        d_flags = nullptr;
         d_work_counter = nullptr;
         d_ugeo = nullptr;
         d_faces = d_fluxes = nullptr;
@@ -256,6 +258,8 @@ struct Solver {
         sc.cs2 = eos->cs2;
         sc.seed = eos->seed;
         sc.tol = eos->newton_tol > 0.0 ? eos->newton_tol : (prec == HYDRO_FP64 ? 1e-13 : 2e-6);
+        sc.newton_max_it = eos->newton_max_iter > 0 ? eos->newton_max_iter : NEWTON_MAX_IT;
+        if (sc.newton_max_it > 1000) return fail(HYDRO_E_INVALID, "newton_max_iter must be <= 1000");
         set_consts(sc.c64, sc.alpha, DELTA_F64, sc.cs2);
         set_consts(sc.c32, float(sc.alpha), float(DELTA_F32), float(sc.cs2));
         if (eos->kind == HYDRO_EOS_CONFORMAL) {
@@ -327,6 +331,9 @@ struct Solver {
         CK(cudaMemcpy(d_clk_tune, clk.data(), n * sizeof(EventClock), cudaMemcpyHostToDevice));
         CK(cudaMalloc(&d_counters, NCOUNTERS * sizeof(unsigned long long)));
         CK(cudaMemset(d_counters, 0, NCOUNTERS * sizeof(unsigned long long)));
+        CK(cudaMalloc(&d_flags, (size_t)n * sizeof(unsigned)));
+        CK(cudaMemset(d_flags, 0, (size_t)n * sizeof(unsigned)));
+        sc.event_flags = d_flags;
         // cell work list: chunks of 2048 cells of one event
         const int chunk = 2048;
         for (int e = 0; e < n; ++e)
@@ -783,12 +790,14 @@ struct Solver {
         c.status = 0;
         c.rate_bits = 0ull;
         CK(cudaMemcpy(d_clk + e, &c, sizeof c, cudaMemcpyHostToDevice));
+        CK(cudaMemset(d_flags + e, 0, sizeof(unsigned)));
         return HYDRO_OK;
     }
 
     hydro_status set_conserved(int e, const void *U, int on_device) {
         rate_valid = false;
         if (e < 0 || e >= nevents || !U) return fail(HYDRO_E_INVALID, "bad argument");
+        CK(cudaMemsetAsync(d_flags + e, 0, sizeof(unsigned), stream));
         CK(cudaMemcpyAsync(event_ptr(cur, e), U, (size_t)4 * geo[e].cells * elem,
                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, stream));
         CK(cudaStreamSynchronize(stream));
@@ -940,13 +949,26 @@ struct Solver {
         return HYDRO_OK;
     }
 
-    hydro_status status(int *st) {
+    // per event: HYDRO_E_NONFINITE if the state holds NaN or Inf, else
+    // HYDRO_E_NEWTON if a Newton solve hit its cap, else HYDRO_E_UNPHYSICAL if
+    // an inadmissible state was met and repaired, else HYDRO_OK; flags (may be
+    // null) receives the raw FLAG_* words
+    hydro_status status(int *st, unsigned *flags_out = nullptr) {
         CellLaunch c = cell_launch();
         CK(launch_finite(c, d_state[cur], d_clk));
         std::vector<EventClock> clk(nevents);
+        std::vector<unsigned> fl(nevents);
         CK(cudaMemcpyAsync(clk.data(), d_clk, nevents * sizeof(EventClock), cudaMemcpyDeviceToHost, stream));
+        CK(cudaMemcpyAsync(fl.data(), d_flags, nevents * sizeof(unsigned), cudaMemcpyDeviceToHost, stream));
         CK(cudaStreamSynchronize(stream));
-        for (int e = 0; e < nevents; ++e) st[e] = clk[e].status;
+        for (int e = 0; e < nevents; ++e) {
+            int s = HYDRO_OK;
+            if (clk[e].status == HYDRO_E_NONFINITE) s = HYDRO_E_NONFINITE;
+            else if (fl[e] & FLAG_NEWTON) s = HYDRO_E_NEWTON;
+            else if (fl[e] & FLAG_UNPHYSICAL) s = HYDRO_E_UNPHYSICAL;
+            st[e] = s;
+            if (flags_out) flags_out[e] = fl[e];
+        }
         return HYDRO_OK;
     }
 
@@ -1074,6 +1096,23 @@ hydro_status hydro_check_finite(hydro_t *h) {
     if (st == HYDRO_E_NONFINITE) return fail(HYDRO_E_NONFINITE, "state holds NaN or Inf");
     return HYDRO_OK;
 }
+hydro_status hydro_check_status(hydro_t *h, unsigned *flags) {
+    HANDLE(h);
+    int st = 0;
+    unsigned fl = 0;
+    hydro_status s = h->s.status(&st, &fl);
+    if (s != HYDRO_OK) return s;
+    if (flags) *flags = fl;
+    switch (st) {
+    case HYDRO_E_NONFINITE: return fail(HYDRO_E_NONFINITE, "state holds NaN or Inf");
+    case HYDRO_E_NEWTON:
+        return fail(HYDRO_E_NEWTON, "a Newton cons->prim solve hit its iteration cap");
+    case HYDRO_E_UNPHYSICAL:
+        return fail(HYDRO_E_UNPHYSICAL,
+                    "an inadmissible state (|M| >= (1 - delta) E) was met and repaired");
+    default: return HYDRO_OK;
+    }
+}
 static hydro_status get_timing(Solver &s, double *ms, long long *n) {
     if (!ms || !n) return fail(HYDRO_E_INVALID, "null output");
     hydro_status st = s.collect_timing();
@@ -1184,6 +1223,10 @@ hydro_status hydro_batch_step(hydro_batch_t *b, int nsteps, int use_graph) {
     HANDLE(b);
     return b->s.step(nsteps, 0.0, use_graph != 0, nullptr);
 }
+hydro_status hydro_batch_set_conserved(hydro_batch_t *b, int event, const void *U, int on_device) {
+    HANDLE(b);
+    return b->s.set_conserved(event, U, on_device);
+}
 hydro_status hydro_batch_get_conserved(hydro_batch_t *b, int event, void *U, int on_device) {
     HANDLE(b);
     return b->s.get_conserved(event, U, on_device);
@@ -1207,6 +1250,11 @@ hydro_status hydro_batch_event_status(hydro_batch_t *b, int *status) {
     HANDLE(b);
     if (!status) return fail(HYDRO_E_INVALID, "null status");
     return b->s.status(status);
+}
+hydro_status hydro_batch_event_flags(hydro_batch_t *b, int *status, unsigned *flags) {
+    HANDLE(b);
+    if (!status || !flags) return fail(HYDRO_E_INVALID, "null output");
+    return b->s.status(status, flags);
 }
 hydro_status hydro_batch_enable_counters(hydro_batch_t *b, int on) {
     HANDLE(b);

@@ -16,7 +16,10 @@ enum { SEED_ZERO = 0, SEED_CONFORMAL = 1, SEED_MLP = 2 };
 enum { CNT_CAPPED = 0, CNT_FACE_FALLBACK = 1, CNT_NEWTON_CALLS = 2, CNT_NEWTON_ITERS = 3,
        CNT_NEWTON_FAIL = 4, CNT_F64_REDO = 5, NCOUNTERS = 6 };
 
-constexpr int NEWTON_MAX_IT = 50;
+constexpr int NEWTON_MAX_IT = 50;   // default iteration cap of the Newton cons->prim solve
+// per-event status bits set on the device (sticky until the event's state is set again)
+enum { FLAG_NEWTON = 1,         // a Newton cons->prim solve hit its iteration cap
+       FLAG_UNPHYSICAL = 2 };   // |M| >= (1 - delta) E met and capped, or a face fell back (R9)
 constexpr double DELTA_F64 = 1e-12;   // admissibility margin |M| < (1 - delta) E
 constexpr double DELTA_F32 = 1e-6;
 
@@ -116,6 +119,8 @@ struct Scheme {
     const void *mlp_w;            // bf16 W1 [32][2], W2 [32][32], W3 [32]
     const float *mlp_f;           // fp32 copy of the full parameter vector
     unsigned long long *counters; // [NCOUNTERS] or null
+    unsigned *event_flags;        // [nevents] FLAG_* words, or null
+    int newton_max_it;            // iteration cap of the Newton solve
     SchemeConsts<double> c64;     // FP64 values, delta of FP64
     SchemeConsts<float> c32;      // FP32 values computed in FP32, delta of FP32
 };

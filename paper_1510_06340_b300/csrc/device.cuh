@@ -194,6 +194,15 @@ __device__ __forceinline__ void count(const Scheme &s, int which, unsigned long 
     if (s.counters) atomicAdd(s.counters + which, v);
 }
 
+// OR the FLAG_* bits of the 32 lanes of a converged warp into the event's
+// status word (one atomic per warp, only when a bit is set) and clear them
+__device__ __forceinline__ void report_flags(const Scheme &s, int event, unsigned &flags) {
+    if (!s.event_flags) return;
+    const unsigned f = __reduce_or_sync(0xffffffffu, flags);
+    if (f && (threadIdx.x & 31) == 0) atomicOr(s.event_flags + event, f);
+    flags = 0;
+}
+
 // the scheme's constants in precision R
 template <class R>
 __device__ __forceinline__ const SchemeConsts<R> &consts(const Scheme &s);
@@ -222,7 +231,7 @@ struct Prim {
 template <class R, bool CAP = true>
 __device__ __forceinline__ Prim<R> c2p_conformal(const V4<R> &U, const SchemeConsts<R> &k,
                                                  R &M2out, R &Wout, const Scheme &sc,
-                                                 bool counting) {
+                                                 bool counting, unsigned *flags = nullptr) {
     Prim<R> q;
     // E <= 0 is vacuum (v = p = 0): with E clamped to 0 the cap forces M2c = 0,
     // so W = p = 0 follow from the same formulas and only 1/W needs a guard.
@@ -245,6 +254,7 @@ __device__ __forceinline__ Prim<R> c2p_conformal(const V4<R> &U, const SchemeCon
         inv *= s;
         fe *= s;
         if (counting) count(sc, CNT_CAPPED);
+        if (flags && U.e > k.emin) *flags |= FLAG_UNPHYSICAL;
     }
     q.vn = U.n * inv;
     q.fe = fe;
@@ -311,7 +321,7 @@ enum { SEED_GIVEN = 100 };   // internal: start from the value passed in
 // three divisions
 template <class R, bool RCP = false>
 __device__ __forceinline__ R newton_speed(const Scheme &sc, R E, R M, R M2, int seed, R given,
-                                          R &p_out, int &iters) {
+                                          R &p_out, int &iters, unsigned *flags = nullptr) {
     R lo = R(0), hi = M / E;
     R v;
     if (seed == SEED_GIVEN) {
@@ -335,7 +345,8 @@ __device__ __forceinline__ R newton_speed(const Scheme &sc, R E, R M, R M2, int 
         v = R(0);
         conv = true;
     } else {
-        for (it = 1; it <= NEWTON_MAX_IT; ++it) {
+        const int max_it = sc.newton_max_it;
+        for (it = 1; it <= max_it; ++it) {
             eos_table<R>(sc, E - M * v, p, c2);
             const R W = E + p;
             const R iw = RCP ? rcp_(W) : R(1);
@@ -349,8 +360,9 @@ __device__ __forceinline__ R newton_speed(const Scheme &sc, R E, R M, R M2, int 
             v = vn;
             if (fabs_(dv) <= R(sc.tol)) { conv = true; break; }
         }
-        if (it > NEWTON_MAX_IT) it = NEWTON_MAX_IT;
+        if (it > max_it) it = max_it;
     }
+    if (!conv && flags) *flags |= FLAG_NEWTON;
     if (sc.counters) {
         count(sc, CNT_NEWTON_CALLS);
         count(sc, CNT_NEWTON_ITERS, (unsigned long long)it);
@@ -366,7 +378,8 @@ __device__ __forceinline__ R newton_speed(const Scheme &sc, R E, R M, R M2, int 
 // converged here); otherwise `seed` is SEED_ZERO, SEED_CONFORMAL or SEED_GIVEN
 template <class R, bool MLP, bool RCP = false>
 __device__ __forceinline__ Prim<R> c2p_table(const V4<R> &U, R delta, const Scheme &sc,
-                                             int seed, R given, R &vmag) {
+                                             int seed, R given, R &vmag,
+                                             unsigned *flags = nullptr) {
     Prim<R> q;
     const R E = U.e;
     const R M2f = fma_(U.t2, U.t2, fma_(U.t1, U.t1, U.n * U.n));
@@ -389,10 +402,11 @@ __device__ __forceinline__ Prim<R> c2p_table(const V4<R> &U, R delta, const Sche
         M2 = cap * cap;
         M = cap;
         count(sc, CNT_CAPPED);
+        if (flags) *flags |= FLAG_UNPHYSICAL;
     }
     R p;
     int it;
-    const R v = newton_speed<R, RCP>(sc, E, M, M2, seed, given, p, it);
+    const R v = newton_speed<R, RCP>(sc, E, M, M2, seed, given, p, it, flags);
     vmag = v;
     q.vn = Mfull > R(0) ? U.n * (v / Mfull) : R(0);
     q.p = p;
@@ -410,6 +424,9 @@ template <class R, int PREC, int EOSK, int LIM = -1, bool COUNT = true, bool MUS
 struct Physics {
     Scheme sc;
     R al_, hclf_;   // alpha dt/dx and 1 / (4 alpha dt/dx) of the current sweep
+    // FLAG_* bits this thread met since the last report_flags (a |M| cap, a
+    // face fallback, a Newton solve that hit its cap)
+    mutable unsigned flags_ = 0;
 
     __device__ __forceinline__ const SchemeConsts<R> &K() const { return consts<R>(sc); }
 
@@ -424,14 +441,14 @@ struct Physics {
         if (EOSK == EOS_CONFORMAL) {
             R M2, W;
             // mixed: a capped state has |v| > 0.99 and is redone in FP64 below
-            Prim<R> q = c2p_conformal<R, PREC != PREC_MIXED>(U, K(), M2, W, sc, COUNT);
+            Prim<R> q = c2p_conformal<R, PREC != PREC_MIXED>(U, K(), M2, W, sc, COUNT, &flags_);
             if (PREC == PREC_MIXED) {
                 // |v|^2 = M2 / W^2 > 0.99^2: redo in double (cancellation in W - E)
                 if (M2 > R(0.9801) * W * W) {
                     V4<double> D = v4<double>(U.e, U.n, U.t1, U.t2);
                     double M2d, Wd;
                     Prim<double> qd =
-                        c2p_conformal<double>(D, sc.c64, M2d, Wd, sc, COUNT);
+                        c2p_conformal<double>(D, sc.c64, M2d, Wd, sc, COUNT, &flags_);
                     q.vn = R(qd.vn);
                     q.p = R(qd.p);
                     q.W = R(qd.W);
@@ -444,13 +461,13 @@ struct Physics {
             R vmag;
             constexpr bool F32 = sizeof(R) == 4;
             Prim<R> q = c2p_table<R, EOSK == EOS_TABLE_MLP, F32>(U, K().delta, sc, sc.seed, R(0),
-                                                                 vmag);
+                                                                 vmag, &flags_);
             if (PREC == PREC_MIXED) {
                 if (vmag > R(0.99)) {   // redo in double, seeded by the float root
                     V4<double> D = v4<double>(U.e, U.n, U.t1, U.t2);
                     double vd;
                     Prim<double> qd = c2p_table<double, false>(D, DELTA_F64, sc, SEED_GIVEN,
-                                                        double(vmag), vd);
+                                                        double(vmag), vd, &flags_);
                     q.vn = R(qd.vn);
                     q.p = R(qd.p);
                     q.W = R(qd.W);
@@ -635,6 +652,7 @@ struct Physics {
         if (!admissible(ul) || !admissible(ur)) {
             ul = v0; ur = v0;
             if (COUNT) count(sc, CNT_FACE_FALLBACK);
+            flags_ |= FLAG_UNPHYSICAL;
         }
     }
 

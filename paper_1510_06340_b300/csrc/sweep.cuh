@@ -116,6 +116,7 @@ sweep_body(const R *__restrict__ in, R *__restrict__ out, const EventGeo *__rest
         } else {
             march<R, RK, RATE>(ph, Pc, s0, L, s_end, g.bc[axis], lam, valid, ra);
         }
+        report_flags(sc, w.event, ph.flags_);
         if (RATE && rate_clk) {   // block max, one atomic per work item
             R m = ra.m;
 #pragma unroll

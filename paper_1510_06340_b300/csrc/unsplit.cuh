@@ -131,6 +131,7 @@ k_us_faces(const R *__restrict__ in, R *__restrict__ faces, const EventGeo *__re
 #pragma unroll
             for (int d = 0; d < 3; ++d) { UL[d] = V0; UR[d] = V0; }
             if (COUNT && valid) count(sc, CNT_FACE_FALLBACK);
+            ph.flags_ |= FLAG_UNPHYSICAL;
         }
         if (valid) {
 #pragma unroll
@@ -144,6 +145,7 @@ k_us_faces(const R *__restrict__ in, R *__restrict__ faces, const EventGeo *__re
                 fr[2 * u.gcells] = UR[d].t1; fr[3 * u.gcells] = UR[d].t2;
             }
         }
+        report_flags(sc, w.event, ph.flags_);
     }
 }
 
@@ -198,6 +200,7 @@ k_us_flux(const R *__restrict__ faces, R *__restrict__ fluxes, const EventGeo *_
             o[2 * u.nint[d]] = F.t1;
             o[3 * u.nint[d]] = F.t2;
         }
+        report_flags(sc, w.event, ph.flags_);
     }
 }
 

@@ -22,6 +22,7 @@ SEEDS = {"zero": 0, "conformal": 1, "mlp": 2}
 STATUS = {0: "OK", 1: "INVALID", 2: "OOM", 3: "CUDA", 4: "UNPHYSICAL", 5: "NEWTON",
           6: "NONFINITE"}
 COUNTERS = ("capped", "face_fallback", "newton_calls", "newton_iters", "newton_fail", "f64_redo")
+FLAG_NEWTON, FLAG_UNPHYSICAL = 1, 2
 
 
 class HydroError(RuntimeError):
@@ -44,7 +45,7 @@ class EosT(C.Structure):
                 ("lne_min", C.c_double), ("lne_max", C.c_double),
                 ("cs2_tab", C.POINTER(C.c_double)), ("p_tab", C.POINTER(C.c_double)),
                 ("seed", C.c_int), ("mlp_params", C.POINTER(C.c_float)),
-                ("newton_tol", C.c_double)]
+                ("newton_tol", C.c_double), ("newton_max_iter", C.c_int)]
 
 
 _lib = None
@@ -78,6 +79,8 @@ def lib():
             "hydro_enable_counters": [H, i],
             "hydro_counters": [H, C.POINTER(C.c_longlong)],
             "hydro_check_finite": [H],
+            "hydro_check_status": [H, C.POINTER(C.c_uint)],
+            "hydro_batch_event_flags": [H, ip, C.POINTER(C.c_uint)],
             "hydro_force_launch": [H, i, i, i],
             "hydro_set_kernel_timing": [H, i],
             "hydro_get_kernel_timing": [H, dp, C.POINTER(C.c_longlong)],
@@ -91,6 +94,7 @@ def lib():
             "hydro_batch_set_primitives": [H, i, vp, vp, vp, vp, i],
             "hydro_batch_set_jets": [H, dp],
             "hydro_batch_step": [H, i, i],
+            "hydro_batch_set_conserved": [H, i, vp, i],
             "hydro_batch_get_conserved": [H, i, vp, i],
             "hydro_batch_get_primitives": [H, i, vp, vp, vp, vp, i],
             "hydro_batch_times": [H, dp],
@@ -209,7 +213,8 @@ def make_grid(nx, ny=1, nz=1, dx=1.0, dy=None, dz=None, x0=0.0, y0=0.0, z0=0.0,
     return g
 
 
-def make_eos(table=None, cs2=1.0 / 3.0, seed="zero", mlp_params=None, newton_tol=0.0):
+def make_eos(table=None, cs2=1.0 / 3.0, seed="zero", mlp_params=None, newton_tol=0.0,
+             newton_max_iter=0):
     """Conformal EOS (table=None) or a table dict from inputs.eos_table()."""
     e = EosT()
     keep = []
@@ -230,6 +235,7 @@ def make_eos(table=None, cs2=1.0 / 3.0, seed="zero", mlp_params=None, newton_tol
         keep.append(m)
         e.mlp_params = m.ctypes.data_as(C.POINTER(C.c_float))
     e.newton_tol = newton_tol
+    e.newton_max_iter = newton_max_iter
     return e, keep
 
 
@@ -350,6 +356,15 @@ class Hydro(_Base):
     def check_finite(self):
         _check(lib().hydro_check_finite(self.h))
 
+    def status(self):
+        """(code, flags): the hydro_check_status code (0, or 4 UNPHYSICAL,
+        5 NEWTON, 6 NONFINITE) and the raw FLAG_* bits, without raising."""
+        fl = C.c_uint()
+        code = lib().hydro_check_status(self.h, C.byref(fl))
+        if code not in (0, 4, 5, 6):
+            _check(code)
+        return code, fl.value
+
     def set_kernel_timing(self, on=True):
         _check(lib().hydro_set_kernel_timing(self.h, int(on)))
 
@@ -433,6 +448,10 @@ class Batch(_Base):
     def step(self, nsteps, use_graph=True):
         _check(lib().hydro_batch_step(self.h, nsteps, int(use_graph)))
 
+    def set_conserved(self, event, U):
+        p, dev, keep = _arg(U, self._dtype, 4 * self._cells(event))
+        _check(lib().hydro_batch_set_conserved(self.h, event, p, dev))
+
     def get_conserved(self, event, out=None):
         if out is None:
             out = np.empty(self.shape(event), dtype=self._dtype)
@@ -460,6 +479,13 @@ class Batch(_Base):
         out = (C.c_int * self.nevents)()
         _check(lib().hydro_batch_event_status(self.h, out))
         return np.array(out[:])
+
+    def event_flags(self):
+        """(codes, flags) per event: hydro_check_status codes and FLAG_* bits."""
+        st = (C.c_int * self.nevents)()
+        fl = (C.c_uint * self.nevents)()
+        _check(lib().hydro_batch_event_flags(self.h, st, fl))
+        return np.array(st[:]), np.array(fl[:])
 
     def enable_counters(self, on=True):
         _check(lib().hydro_batch_enable_counters(self.h, int(on)))

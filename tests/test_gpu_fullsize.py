@@ -42,7 +42,11 @@ def test_full_batch_events_equal_single_runs(H):
     b.init_hotspots(spots, I.SPOT_SIGMA, I.E_BACKGROUND)
     b.set_jets(jets)
     b.step(3)
-    assert not b.event_status().any()
+    codes, flags = b.event_flags()
+    # no NaN/Inf and no Newton trouble (conformal EOS); cells repaired by the
+    # admissibility rule are reported, not failures
+    assert not np.isin(codes, (5, 6)).any(), codes
+    print("events with an inadmissible state repaired:", int((codes == 4).sum()))
     times = b.times()
     for e in (0, nev - 1):
         h = H.Hydro(event_grid(H, sizes[e]))

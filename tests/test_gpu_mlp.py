@@ -59,8 +59,12 @@ def test_mlp_forward_matches_oracle(H):
     H1 = H1d.cpu().numpy().astype(np.float64)
     H1o = O.mlp_hidden(P, Xf, quantize=1)
     step = np.abs(H1 - H1o)
-    # one bf16 step of |h| < 1 is at most 2^-8 |h|
-    assert (step <= 2.0 ** -8 * np.abs(H1o) + 1e-30).all(), step.max()
+    # one bf16 step at |h|: 2^(floor(log2 |h|) - 7) (8 significant bits)
+    big = np.maximum(np.abs(H1), np.abs(H1o))
+    ulp = np.exp2(np.floor(np.log2(np.where(big > 0, big, 1.0))) - 7)
+    print("layer 1: entries one bf16 step apart:", (step > 0).mean(),
+          "max steps:", (step / ulp).max())
+    assert (step <= ulp).all(), (step / ulp).max()
     assert (step > 0).mean() < 0.01, (step > 0).mean()
     want_h1 = O.mlp_forward_h1(P, Xf, H1, quantize=1)
     err23 = np.abs(got - want_h1)
@@ -80,7 +84,8 @@ BLOCKS = {"W1": (0, 64), "b1": (64, 96), "W2": (96, 1120), "b2": (1120, 1152),
 
 def test_mlp_gradient_matches_oracle(H):
     """Element by element, each parameter block on its own scale:
-    |G_i - G_oracle,i| <= 2e-3 |G_oracle,i| + 1e-4 max_block |G_oracle|."""
+    |G_i - G_oracle,i| <= 1e-5 |G_oracle,i| + 1e-6 max_block |G_oracle|
+    (FP32 accumulation over 2048 samples against FP64)."""
     import torch
     rng = np.random.default_rng(12)
     nP = H.mlp_nparam()
@@ -102,7 +107,7 @@ def test_mlp_gradient_matches_oracle(H):
         g, go = G[a:b], G_o[a:b]
         scale = np.abs(go).max()
         assert scale > 0, name
-        bound = 2e-3 * np.abs(go) + 1e-4 * scale
+        bound = 1e-5 * np.abs(go) + 1e-6 * scale
         worst[name] = float((np.abs(g - go) / bound).max())
     print("gradient error / bound per block:", worst)
     assert max(worst.values()) <= 1.0, worst
