@@ -10,8 +10,9 @@
  * from the paper's equations and the readings listed below, in the paper's
  * order, with no blocking, fusion or reordering.
  *
- * State per cell: U = (E, Mx, My, Mz) = T^{00}, T^{0i}  (Sec. 2.1, Eq. 4,
- * without the charge R).  Arrays are field-major [4][nz][ny][nx], x fastest.
+ * State per cell: U = (E, Mx, My, Mz) = T^{00}, T^{0i}, and with charge = 1
+ * the conserved charge R = n gamma as a fifth field (Sec. 2.1, Eq. 1, 3, 4).
+ * Arrays are field-major [nq][nz][ny][nx], x fastest, nq = 4 or 5.
  *
  * Readings of points the paper leaves open (each is also a named item in the
  * design notes):
@@ -58,6 +59,13 @@
  *      dt L(U) = - sum_d dt/dx_d (F_d,i+1/2 - F_d,i-1/2).
  *  R17 Ellipsoidal flow (Sec. 3.2): v_i = a_i x_i / t (the printed order
  *      a_1, a_3, a_2 of the velocity is read as a typo; tau pairs a_i with x_i).
+ *  R19 Conserved charge (charge = 1): R = n gamma is carried as a fifth
+ *      conserved field with flux R v_d (Eq. 3).  The EOS here is p(e) (the
+ *      paper gives no p(e, n)), so R is transported by the energy-momentum
+ *      velocity and feeds nothing back; n = R / gamma on readout.  Slopes,
+ *      Hancock, MUSTA-FORCE and RK act on it like on the other fields; the
+ *      admissibility rule (R9) looks at E and M only.  Not built for the
+ *      unsplit scheme.
  *  R18 Vacuum threshold: a cell with E <= 2^-500 is vacuum (v = p = 0), so that
  *      E^2 and M^2 in the cons->prim formulas stay normal numbers; below it the
  *      closed form of R10 loses all digits (E^2 underflows).
@@ -95,7 +103,11 @@ typedef struct {
     int jet_on;
     double jet[8];             /* x0,y0,z0, nx,ny,nz, dEdx, sigma */
     int unsplit;               /* 1: unsplit multi-D scheme (R16) instead of Strang sweeps */
+    int charge;                /* 1: carry the conserved charge R as a fifth field (R19) */
 } or_config;
+
+#define OR_NQ 5                /* room for the fields of one cell, with the charge */
+static int nq_of(const or_config *c) { return c->charge ? 5 : 4; }
 
 /* diagnostics counters (reset by or_reset_counters); the OpenMP timing build
    (OR_OPENMP) runs pencils on several threads and keeps no counts */
@@ -425,20 +437,27 @@ int or_cons2prim(const or_config *c, const double U[4], double *e_out, double v[
 }
 
 /* ------------------------------------------------------- prim -> cons */
-/* Sec. 2.1, Eq. 4: E = (e+p) g^2 - p, M_i = (e+p) g^2 v_i. */
-void or_prim2cons(const or_config *c, double e, double vx, double vy, double vz, double U[4]) {
+/* Sec. 2.1, Eq. 4: E = (e+p) g^2 - p, M_i = (e+p) g^2 v_i, and R = n g with
+   the charge (U then holds 5 values). */
+void or_prim2cons_n(const or_config *c, double e, double vx, double vy, double vz, double n,
+                    double *U) {
     double p = or_eos_p(c, e);
-    double g2 = 1.0 / (1.0 - (vx * vx + vy * vy + vz * vz));
+    double v2 = vx * vx + vy * vy + vz * vz;
+    double g2 = 1.0 / (1.0 - v2);
     double w = (e + p) * g2;
     U[0] = w - p;
     U[1] = w * vx;
     U[2] = w * vy;
     U[3] = w * vz;
+    if (c->charge) U[4] = n / sqrt(1.0 - v2);
+}
+void or_prim2cons(const or_config *c, double e, double vx, double vy, double vz, double *U) {
+    or_prim2cons_n(c, e, vx, vy, vz, 0.0, U);
 }
 
 /* ----------------------------------------------------------------- flux */
 /* Sec. 2.1, Eq. 3: flux along axis d of U. */
-void or_flux(const or_config *c, int d, const double U[4], double F[4]) {
+void or_flux(const or_config *c, int d, const double *U, double *F) {
     double e, v[3], p;
     or_cons2prim(c, U, &e, v, &p, NULL);
     F[0] = (U[0] + p) * v[d];
@@ -446,36 +465,39 @@ void or_flux(const or_config *c, int d, const double U[4], double F[4]) {
     F[2] = U[2] * v[d];
     F[3] = U[3] * v[d];
     F[1 + d] += p;
+    if (c->charge) F[4] = U[4] * v[d];   /* R v_d */
 }
 
 /* ---------------------------------------------------------- MUSTA-FORCE */
 /* Sec. 2.4, MUSTA steps 1-5 with the FORCE flux of Eq. 9-11 (R1, R2, R4). */
-void or_musta_force(const or_config *c, int d, double lam, const double UL0[4],
-                    const double UR0[4], double Fout[4]) {
-    double UL[4], UR[4], FL[4], FR[4], Ulw[4], Flw[4], Flf[4], Fc[4];
+void or_musta_force(const or_config *c, int d, double lam, const double *UL0,
+                    const double *UR0, double *Fout) {
+    double UL[OR_NQ], UR[OR_NQ], FL[OR_NQ], FR[OR_NQ], Ulw[OR_NQ], Flw[OR_NQ], Flf[OR_NQ],
+        Fc[OR_NQ];
     double al = c->alpha * lam;
-    memcpy(UL, UL0, sizeof UL);
-    memcpy(UR, UR0, sizeof UR);
+    int nq = nq_of(c);
+    memcpy(UL, UL0, nq * sizeof(double));
+    memcpy(UR, UR0, nq * sizeof(double));
     for (int l = 0; l < c->stages; l++) {
         or_flux(c, d, UL, FL);
         or_flux(c, d, UR, FR);
-        for (int q = 0; q < 4; q++)
+        for (int q = 0; q < nq; q++)
             Ulw[q] = 0.5 * (UL[q] + UR[q]) - 0.5 * al * (FR[q] - FL[q]);
         or_flux(c, d, Ulw, Flw);
-        for (int q = 0; q < 4; q++)
+        for (int q = 0; q < nq; q++)
             Flf[q] = 0.5 * (FL[q] + FR[q]) - (0.5 / al) * (UR[q] - UL[q]);
-        for (int q = 0; q < 4; q++) Fc[q] = 0.5 * (Flw[q] + Flf[q]);
+        for (int q = 0; q < nq; q++) Fc[q] = 0.5 * (Flw[q] + Flf[q]);
         if (l < c->stages - 1) {
-            for (int q = 0; q < 4; q++) {
+            for (int q = 0; q < nq; q++) {
                 UL[q] = UL[q] - lam * (Fc[q] - FL[q]);
                 UR[q] = UR[q] - lam * (FR[q] - Fc[q]);
             }
         }
     }
-    memcpy(Fout, Fc, sizeof Fc);
+    memcpy(Fout, Fc, nq * sizeof(double));
 }
 
-static int admissible(const or_config *c, const double U[4]) {
+static int admissible(const or_config *c, const double *U) {
     double M2 = U[1] * U[1] + U[2] * U[2] + U[3] * U[3];
     double cap = (1.0 - c->delta) * U[0];
     return U[0] > 0.0 && M2 < cap * cap;
@@ -486,10 +508,11 @@ static int admissible(const or_config *c, const double U[4]) {
  * the term along the sweep axis), R9 fallback.  V holds cells -1..+1 around
  * the cell; outputs the evolved faces.
  */
-void or_hancock_faces(const or_config *c, int d, double lam, const double Vm[4],
-                      const double V0[4], const double Vp[4], double ULt[4], double URt[4]) {
-    double UL[4], UR[4], FL[4], FR[4];
-    for (int q = 0; q < 4; q++) {
+void or_hancock_faces(const or_config *c, int d, double lam, const double *Vm,
+                      const double *V0, const double *Vp, double *ULt, double *URt) {
+    double UL[OR_NQ], UR[OR_NQ], FL[OR_NQ], FR[OR_NQ];
+    int nq = nq_of(c);
+    for (int q = 0; q < nq; q++) {
         double s = or_limiter(c->limiter, V0[q] - Vm[q], Vp[q] - V0[q]);
         UL[q] = V0[q] - 0.5 * s;
         UR[q] = V0[q] + 0.5 * s;
@@ -497,36 +520,38 @@ void or_hancock_faces(const or_config *c, int d, double lam, const double Vm[4],
     if (c->hancock) {
         or_flux(c, d, UL, FL);
         or_flux(c, d, UR, FR);
-        for (int q = 0; q < 4; q++) {
+        for (int q = 0; q < nq; q++) {
             ULt[q] = UL[q] + 0.5 * lam * (FL[q] - FR[q]);
             URt[q] = UR[q] + 0.5 * lam * (FL[q] - FR[q]);
         }
     } else {
-        memcpy(ULt, UL, sizeof UL);
-        memcpy(URt, UR, sizeof UR);
+        memcpy(ULt, UL, nq * sizeof(double));
+        memcpy(URt, UR, nq * sizeof(double));
     }
     if (!admissible(c, ULt) || !admissible(c, URt)) {
-        memcpy(ULt, V0, 4 * sizeof(double));
-        memcpy(URt, V0, 4 * sizeof(double));
+        memcpy(ULt, V0, nq * sizeof(double));
+        memcpy(URt, V0, nq * sizeof(double));
         OR_TALLY(g_face_fallback, 1);
     }
 }
 
 /* ------------------------------------------------------------- pencils */
-/* V[(N+4)][4]: cell i at V[i+2]; fill two ghost cells on each side. */
-static void fill_ghosts(double (*V)[4], int N, int bc) {
+/* V[(N+4)][OR_NQ]: cell i at V[i+2]; fill two ghost cells on each side. */
+static void fill_ghosts(double (*V)[OR_NQ], int N, int bc) {
     for (int g = 1; g <= 2; g++) {
         int lo_dst = 2 - g, hi_dst = N + 1 + g;
         int lo_src = (bc == 0) ? (N - g + 2) : 2;
         int hi_src = (bc == 0) ? (g + 1) : (N + 1);
-        memcpy(V[lo_dst], V[lo_src], 4 * sizeof(double));
-        memcpy(V[hi_dst], V[hi_src], 4 * sizeof(double));
+        memcpy(V[lo_dst], V[lo_src], OR_NQ * sizeof(double));
+        memcpy(V[hi_dst], V[hi_src], OR_NQ * sizeof(double));
     }
 }
 
 /* D[i] = F_{i+1/2} - F_{i-1/2} for cells 0..N-1 (the divergence, times dx) */
-static void pencil_L(const or_config *c, int d, double lam, double (*V)[4], int N, double (*D)[4],
-                     double (*ULt)[4], double (*URt)[4], double (*F)[4]) {
+static void pencil_L(const or_config *c, int d, double lam, double (*V)[OR_NQ], int N,
+                     double (*D)[OR_NQ], double (*ULt)[OR_NQ], double (*URt)[OR_NQ],
+                     double (*F)[OR_NQ]) {
+    int nq = nq_of(c);
     /* evolved faces of cells -1..N (index +1) */
     for (int i = -1; i <= N; i++)
         or_hancock_faces(c, d, lam, V[i + 1], V[i + 2], V[i + 3], ULt[i + 1], URt[i + 1]);
@@ -534,7 +559,7 @@ static void pencil_L(const or_config *c, int d, double lam, double (*V)[4], int 
     for (int i = -1; i < N; i++)
         or_musta_force(c, d, lam, URt[i + 1], ULt[i + 2], F[i + 1]);
     for (int i = 0; i < N; i++)
-        for (int q = 0; q < 4; q++) D[i][q] = F[i + 1][q] - F[i][q];
+        for (int q = 0; q < nq; q++) D[i][q] = F[i + 1][q] - F[i][q];
 }
 
 /* one Runge-Kutta sweep (Sec. 2.3, Eq. 6 or 7) of every pencil along axis d;
@@ -548,17 +573,18 @@ void or_sweep(const or_config *c, double *U, int d, double dt) {
     double lam = dt / h[d];
     int a_ax = (d == 0) ? 1 : 0, b_ax = (d == 2) ? 1 : 2;
     long npencils = (long)n[a_ax] * n[b_ax];
+    int nq = nq_of(c);
 #ifdef OR_OPENMP
 #pragma omp parallel
 #endif
     {
-    double (*V0)[4] = (double (*)[4])malloc(sizeof(double[4]) * (N + 4));
-    double (*V1)[4] = (double (*)[4])malloc(sizeof(double[4]) * (N + 4));
-    double (*V2)[4] = (double (*)[4])malloc(sizeof(double[4]) * (N + 4));
-    double (*D)[4] = (double (*)[4])malloc(sizeof(double[4]) * N);
-    double (*ULt)[4] = (double (*)[4])malloc(sizeof(double[4]) * (N + 2));
-    double (*URt)[4] = (double (*)[4])malloc(sizeof(double[4]) * (N + 2));
-    double (*F)[4] = (double (*)[4])malloc(sizeof(double[4]) * (N + 1));
+    double (*V0)[OR_NQ] = (double (*)[OR_NQ])malloc(sizeof(double[OR_NQ]) * (N + 4));
+    double (*V1)[OR_NQ] = (double (*)[OR_NQ])malloc(sizeof(double[OR_NQ]) * (N + 4));
+    double (*V2)[OR_NQ] = (double (*)[OR_NQ])malloc(sizeof(double[OR_NQ]) * (N + 4));
+    double (*D)[OR_NQ] = (double (*)[OR_NQ])malloc(sizeof(double[OR_NQ]) * N);
+    double (*ULt)[OR_NQ] = (double (*)[OR_NQ])malloc(sizeof(double[OR_NQ]) * (N + 2));
+    double (*URt)[OR_NQ] = (double (*)[OR_NQ])malloc(sizeof(double[OR_NQ]) * (N + 2));
+    double (*F)[OR_NQ] = (double (*)[OR_NQ])malloc(sizeof(double[OR_NQ]) * (N + 1));
 #ifdef OR_OPENMP
 #pragma omp for schedule(static)
 #endif
@@ -568,36 +594,36 @@ void or_sweep(const or_config *c, double *U, int d, double dt) {
         idx[d] = 0; idx[a_ax] = a; idx[b_ax] = b;
         long base = idx[0] + (long)c->nx * (idx[1] + (long)c->ny * idx[2]);
         for (int i = 0; i < N; i++)
-            for (int q = 0; q < 4; q++) V0[i + 2][q] = U[q * cells + base + i * stride];
+            for (int q = 0; q < nq; q++) V0[i + 2][q] = U[q * cells + base + i * stride];
         fill_ghosts(V0, N, c->bc[d]);
         /* stage 1: U1 = U + dt L(U) */
         pencil_L(c, d, lam, V0, N, D, ULt, URt, F);
         if (c->rk_order == 1) {
             for (int i = 0; i < N; i++)
-                for (int q = 0; q < 4; q++)
+                for (int q = 0; q < nq; q++)
                     U[q * cells + base + i * stride] = V0[i + 2][q] - lam * D[i][q];
             continue;
         }
         for (int i = 0; i < N; i++)
-            for (int q = 0; q < 4; q++) V1[i + 2][q] = V0[i + 2][q] - lam * D[i][q];
+            for (int q = 0; q < nq; q++) V1[i + 2][q] = V0[i + 2][q] - lam * D[i][q];
         fill_ghosts(V1, N, c->bc[d]);
         pencil_L(c, d, lam, V1, N, D, ULt, URt, F);
         if (c->rk_order == 3) {
             /* U2 = 3/4 U + 1/4 U1 + 1/4 dt L(U1) */
             for (int i = 0; i < N; i++)
-                for (int q = 0; q < 4; q++)
+                for (int q = 0; q < nq; q++)
                     V2[i + 2][q] = 0.75 * V0[i + 2][q] + 0.25 * (V1[i + 2][q] - lam * D[i][q]);
             fill_ghosts(V2, N, c->bc[d]);
             pencil_L(c, d, lam, V2, N, D, ULt, URt, F);
             /* U^{n+1} = 1/3 U + 2/3 U2 + 2/3 dt L(U2) */
             for (int i = 0; i < N; i++)
-                for (int q = 0; q < 4; q++)
+                for (int q = 0; q < nq; q++)
                     U[q * cells + base + i * stride] =
                         V0[i + 2][q] / 3.0 + (2.0 / 3.0) * (V2[i + 2][q] - lam * D[i][q]);
         } else {
             /* U^{n+1} = 1/2 (U + U1 + dt L(U1)) */
             for (int i = 0; i < N; i++)
-                for (int q = 0; q < 4; q++)
+                for (int q = 0; q < nq; q++)
                     U[q * cells + base + i * stride] =
                         0.5 * (V0[i + 2][q] + V1[i + 2][q] - lam * D[i][q]);
         }
@@ -680,7 +706,7 @@ static long grid_index(const or_config *c, int i, int j, int k) {
     return x[0] + (long)c->nx * (x[1] + (long)c->ny * x[2]);
 }
 
-static void grid_load(const or_config *c, const double *U, int i, int j, int k, double u[4]) {
+static void grid_load(const or_config *c, const double *U, int i, int j, int k, double *u) {
     long cells = (long)c->nx * c->ny * c->nz;
     long g = grid_index(c, i, j, k);
     for (int q = 0; q < 4; q++) u[q] = U[q * cells + g];
@@ -707,11 +733,11 @@ static void unsplit_L(const or_config *c, const double *U, double dt, double *D)
         for (int j = -g[1]; j < n[1] + g[1]; j++)
             for (int i = -g[0]; i < n[0] + g[0]; i++) {
                 long mi = (i + g[0]) + (long)m[0] * ((j + g[1]) + (long)m[1] * (k + g[2]));
-                double V0[4], UL[3][4], UR[3][4], hq[4] = {0.0, 0.0, 0.0, 0.0};
+                double V0[OR_NQ], UL[3][OR_NQ], UR[3][OR_NQ], hq[4] = {0.0, 0.0, 0.0, 0.0};
                 grid_load(c, U, i, j, k, V0);
                 for (int d = 0; d < 3; d++) {
                     if (!act[d]) continue;
-                    double Vm[4], Vp[4];
+                    double Vm[OR_NQ], Vp[OR_NQ];
                     int o[3] = {0, 0, 0};
                     o[d] = 1;
                     grid_load(c, U, i - o[0], j - o[1], k - o[2], Vm);
@@ -723,7 +749,7 @@ static void unsplit_L(const or_config *c, const double *U, double dt, double *D)
                         UR[d][q] = V0[q] + 0.5 * sl;
                     }
                     if (c->hancock) {   /* Eq. 13: the axis-d term of the half step */
-                        double FLd[4], FRd[4];
+                        double FLd[OR_NQ], FRd[OR_NQ];
                         or_flux(c, d, UL[d], FLd);
                         or_flux(c, d, UR[d], FRd);
                         for (int q = 0; q < 4; q++)
@@ -763,7 +789,7 @@ static void unsplit_L(const or_config *c, const double *U, double dt, double *D)
                               (long)m[0] * ((j - o[1] + g[1]) + (long)m[1] * (k - o[2] + g[2]));
                     long mp = (i + o[0] + g[0]) +
                               (long)m[0] * ((j + o[1] + g[1]) + (long)m[1] * (k + o[2] + g[2]));
-                    double Fm[4], Fp[4];
+                    double Fm[OR_NQ], Fp[OR_NQ];
                     /* interface i-1/2: right face of cell i-1, left face of cell i (R3) */
                     or_musta_force(c, d, lam, &FRf[((long)d * mcells + mm) * 4],
                                    &FLf[((long)d * mcells + mc) * 4], Fm);
@@ -828,6 +854,7 @@ double or_step(const or_config *c, double *U, double t, double t_end) {
     else dt = c->cfl / (c->unsplit ? or_max_rate_unsplit(c, U) : or_max_rate(c, U));
     if (t_end > 0.0 && t + dt > t_end) dt = t_end - t;
     if (!(dt > 0.0)) return 0.0;
+    if (c->unsplit && c->charge) return 0.0;   /* R19: not built for the unsplit scheme */
     if (c->jet_on) or_jet_source(c, U, t, dt);
     if (c->unsplit) {
         unsplit_rk(c, U, dt);
@@ -858,22 +885,34 @@ int or_run(const or_config *c, double *U, int nsteps, double t_end, double *t) {
 
 /* ---------------------------------------------------- whole-field helpers */
 /* sum_cells U * dV for the four conserved fields */
-void or_conservation_sums(const or_config *c, const double *U, double out[4]) {
+void or_conservation_sums(const or_config *c, const double *U, double *out) {
     long cells = (long)c->nx * c->ny * c->nz;
     double dV = c->dx * c->dy * c->dz;
-    for (int q = 0; q < 4; q++) {
+    for (int q = 0; q < nq_of(c); q++) {
         double s = 0.0;
         for (long i = 0; i < cells; i++) s += U[q * cells + i];
         out[q] = s * dV;
     }
 }
 
+/* n may be NULL (charge 0 everywhere) */
 void or_prim2cons_field(const or_config *c, long cells, const double *e, const double *vx,
-                        const double *vy, const double *vz, double *U) {
+                        const double *vy, const double *vz, const double *n, double *U) {
     for (long i = 0; i < cells; i++) {
-        double u[4];
-        or_prim2cons(c, e[i], vx[i], vy[i], vz[i], u);
-        for (int q = 0; q < 4; q++) U[q * cells + i] = u[q];
+        double u[OR_NQ];
+        or_prim2cons_n(c, e[i], vx[i], vy[i], vz[i], n ? n[i] : 0.0, u);
+        for (int q = 0; q < nq_of(c); q++) U[q * cells + i] = u[q];
+    }
+}
+
+/* R19: rest-frame charge density n = R / gamma = R sqrt(1 - v^2) per cell,
+   v from cons->prim of the energy-momentum fields (vacuum: n = R) */
+void or_charge_density_field(const or_config *c, long cells, const double *U, double *n) {
+    for (long i = 0; i < cells; i++) {
+        double u[4] = {U[i], U[cells + i], U[2 * cells + i], U[3 * cells + i]};
+        double e, v[3], p;
+        or_cons2prim(c, u, &e, v, &p, NULL);
+        n[i] = U[4 * cells + i] * sqrt(1.0 - (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]));
     }
 }
 

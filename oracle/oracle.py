@@ -71,7 +71,7 @@ class _Cfg(C.Structure):
         ("seed_kind", C.c_int), ("mlp", C.POINTER(C.c_double)), ("mlp_quantize", C.c_int),
         ("newton_tol", C.c_double),
         ("jet_on", C.c_int), ("jet", C.c_double * 8),
-        ("unsplit", C.c_int),
+        ("unsplit", C.c_int), ("charge", C.c_int),
     ]
 
 
@@ -122,7 +122,10 @@ def _bind(L):
         L.or_run.restype = C.c_int
         L.or_run.argtypes = [P, _dp, C.c_int, C.c_double, _dp]
         L.or_conservation_sums.argtypes = [P, _dp, _dp]
-        L.or_prim2cons_field.argtypes = [P, C.c_long, _dp, _dp, _dp, _dp, _dp]
+        L.or_prim2cons_field.argtypes = [P, C.c_long, _dp, _dp, _dp, _dp, _dp, _dp]
+        L.or_prim2cons_n.argtypes = [P, C.c_double, C.c_double, C.c_double, C.c_double,
+                                     C.c_double, _dp]
+        L.or_charge_density_field.argtypes = [P, C.c_long, _dp, _dp]
         L.or_cons2prim_field.argtypes = [P, C.c_long, _dp, _dp, _dp, _dp, _dp,
                                          C.POINTER(C.c_int)]
         L.or_eos_p.restype = C.c_double
@@ -154,7 +157,7 @@ class Oracle:
                  bc=("periodic", "periodic", "periodic"), limiter="minmod", stages=2,
                  rk_order=2, hancock=1, alpha=1.0, cfl=0.4, fixed_dt=0.0, delta=1e-12, eos=None,
                  cs2=1.0 / 3.0, seed_kind=0, mlp=None, mlp_quantize=0, newton_tol=1e-13,
-                 jet=None, unsplit=0):
+                 jet=None, unsplit=0, charge=0):
         self.keep = []
         c = _Cfg()
         c.nx, c.ny, c.nz = nx, ny, nz
@@ -192,8 +195,10 @@ class Oracle:
             for i in range(8):
                 c.jet[i] = float(jet[i])
         c.unsplit = int(unsplit)
+        c.charge = int(charge)
         self.c = c
-        self.shape = (4, nz, ny, nx)
+        self.nq = 5 if charge else 4
+        self.shape = (self.nq, nz, ny, nx)
 
     @property
     def cells(self):
@@ -212,21 +217,23 @@ class Oracle:
                                 C.byref(it))
         return e.value, v, p.value, st, it.value
 
-    def prim2cons(self, e, v):
-        U = np.zeros(4)
-        lib().or_prim2cons(C.byref(self.c), e, v[0], v[1], v[2], _ptr(U))
+    def prim2cons(self, e, v, n=0.0):
+        U = np.zeros(self.nq)
+        lib().or_prim2cons_n(C.byref(self.c), e, v[0], v[1], v[2], n, _ptr(U))
         return U
 
     def flux(self, d, U):
         U = np.ascontiguousarray(U, dtype=np.float64)
-        F = np.zeros(4)
+        assert U.size >= self.nq
+        F = np.zeros(self.nq)
         lib().or_flux(C.byref(self.c), d, _ptr(U), _ptr(F))
         return F
 
     def musta_force(self, d, lam, UL, UR):
         UL = np.ascontiguousarray(UL, dtype=np.float64)
         UR = np.ascontiguousarray(UR, dtype=np.float64)
-        F = np.zeros(4)
+        assert UL.size >= self.nq and UR.size >= self.nq
+        F = np.zeros(self.nq)
         lib().or_musta_force(C.byref(self.c), d, lam, _ptr(UL), _ptr(UR), _ptr(F))
         return F
 
@@ -241,12 +248,27 @@ class Oracle:
         return lib().or_eos_cs2(C.byref(self.c), e)
 
     # --- whole-field operations --------------------------------------------
-    def prim2cons_field(self, e, vx, vy, vz):
-        n = self.cells
+    def prim2cons_field(self, e, vx, vy, vz, n=None):
+        """Conserved fields from (e, v) and, with the charge, the rest-frame
+        charge density n (None: zero)."""
+        cells = self.cells
         arrs = [np.ascontiguousarray(a, dtype=np.float64).reshape(-1) for a in (e, vx, vy, vz)]
+        nn = None
+        if n is not None:
+            nn = np.ascontiguousarray(n, dtype=np.float64).reshape(-1)
+            assert nn.size == cells
         U = np.zeros(self.shape)
-        lib().or_prim2cons_field(C.byref(self.c), n, *[_ptr(a) for a in arrs], _ptr(U))
+        lib().or_prim2cons_field(C.byref(self.c), cells, *[_ptr(a) for a in arrs],
+                                 _ptr(nn) if nn is not None else None, _ptr(U))
         return U
+
+    def charge_density_field(self, U):
+        """n = R / gamma per cell (needs charge=1)."""
+        assert self.nq == 5
+        U = np.ascontiguousarray(U, dtype=np.float64)
+        n = np.zeros(self.shape[1:])
+        lib().or_charge_density_field(C.byref(self.c), self.cells, _ptr(U), _ptr(n))
+        return n
 
     def cons2prim_field(self, U):
         n = self.cells
@@ -264,6 +286,7 @@ class Oracle:
     def max_rate(self, U):
         """The rate whose inverse times cfl is dt: max over axes (split) or the
         sum over axes (unsplit, R16c)."""
+        self._field(U)
         if self.c.unsplit:
             return lib().or_max_rate_unsplit(C.byref(self.c), _ptr(U))
         return lib().or_max_rate(C.byref(self.c), _ptr(U))
@@ -271,18 +294,24 @@ class Oracle:
     def jet_source(self, U, t, dt):
         lib().or_jet_source(C.byref(self.c), _ptr(U), t, dt)
 
+    def _field(self, U):
+        assert U.dtype == np.float64 and U.size == self.nq * self.cells, (U.shape, self.shape)
+
     def step(self, U, t=0.0, t_end=0.0):
+        self._field(U)
         return lib().or_step(C.byref(self.c), _ptr(U), t, t_end)
 
     def run(self, U, nsteps, t_end=0.0, t=0.0, threads=False):
         """Advance U in place; threads=True runs the OpenMP timing build."""
+        self._field(U)
         tt = C.c_double(t)
         L = lib_omp() if threads else lib()
         n = L.or_run(C.byref(self.c), _ptr(U), nsteps, t_end, C.byref(tt))
         return n, tt.value
 
     def conservation_sums(self, U):
-        out = np.zeros(4)
+        self._field(U)
+        out = np.zeros(self.nq)
         lib().or_conservation_sums(C.byref(self.c), _ptr(U), _ptr(out))
         return out
 

@@ -61,6 +61,25 @@ class Riemann:
         self.head = -self.c
         self.tail = (self.v_star - self.c) / (1.0 - self.v_star * self.c)
 
+    def sample_n(self, x, t, n_l, n_r):
+        """Rest-frame density n of a passive conserved charge (R = n gamma with
+        flux R v, the EOS independent of n) in the same Riemann problem.
+        Smooth flow conserves both s u^mu and n u^mu, so n/s is constant along
+        flow lines, with s ~ e^(1/(1+c^2)) for p = c^2 e (ds/s = de/(e+p)):
+        n = n_l (e/e_l)^(1/(1+c^2)) in the fan and up to the contact, which
+        moves with v*.  Across the shock, n gamma (v - s) is continuous:
+        n = n_r s / (gamma* (s - v*)) between the contact and the shock."""
+        xi = np.asarray(x, dtype=np.float64) / t
+        e, _ = self.sample(x, t)
+        k = 1.0 / (1.0 + self.c2)
+        n = n_l * (e / self.e_l) ** k
+        s = self.shock_speed
+        g = 1.0 / math.sqrt(1.0 - self.v_star ** 2)
+        right_star = (xi >= self.v_star) & (xi < s)
+        n[right_star] = n_r * s / (g * (s - self.v_star))
+        n[xi >= s] = n_r
+        return n
+
     def jump_residuals(self):
         t00, t01, t11 = _tmunu(self.e_star, self.v_star, self.c2)
         s = self.shock_speed

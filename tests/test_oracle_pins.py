@@ -748,3 +748,92 @@ def test_openmp_timing_build_equals_the_oracle_bit_for_bit():
     o.run(U1, 2)
     o.run(U2, 2, threads=True)
     assert np.array_equal(U1, U2)
+
+
+# ------------------------------------------------------------ conserved charge
+def test_charge_flux_and_prim2cons_follow_eq_3_and_4():
+    """R = n gamma (Eq. 4) and its flux R v_d (Eq. 3); the energy-momentum
+    components are those of the four-field scheme."""
+    o5 = O.Oracle(1, charge=1)
+    o4 = O.Oracle(1)
+    v = np.array([0.3, -0.4, 0.2])
+    U5 = o5.prim2cons(2.0, v, n=0.7)
+    g = 1.0 / math.sqrt(1.0 - v @ v)
+    assert U5[4] == pytest.approx(0.7 * g, rel=1e-15)
+    assert np.array_equal(U5[:4], o4.prim2cons(2.0, v))
+    for d in range(3):
+        F5 = o5.flux(d, U5)
+        assert np.array_equal(F5[:4], o4.flux(d, U5[:4]))
+        assert F5[4] == pytest.approx(U5[4] * v[d], rel=1e-14)
+
+
+def charged_shock_tube(n, n_l=1.0, n_r=0.5):
+    g, prim = I.shock_tube(n)
+    o = O.Oracle(n, dx=g["dx"], x0=-1.0, bc="outflow", limiter="minmod", cfl=0.4, charge=1)
+    x = I.cell_centres(n, -1.0, g["dx"])
+    nn = np.where(x < 0.0, n_l, n_r).reshape(1, 1, n)
+    U = o.prim2cons_field(*prim, n=nn)
+    o.run(U, 100000, t_end=0.8)
+    got = o.charge_density_field(U).ravel()
+    want = exact.Riemann().sample_n(x, 0.8, n_l, n_r)
+    return np.abs(got - want).sum() / np.abs(want).sum(), U
+
+
+def test_charged_shock_tube_converges_to_the_exact_charge_density():
+    """e_L = 10, e_R = 1, p = e/3 with n_L = 1, n_R = 0.5: the exact n has a
+    rarefaction fan, a contact moving with v*, and the shock's compression.
+    The energy-momentum fields are those of the four-field run bit for bit."""
+    errs = [charged_shock_tube(n)[0] for n in (250, 500, 1000)]
+    assert errs[0] < 0.05
+    assert errs[1] < errs[0] and errs[2] < errs[1]
+    assert errs[0] / errs[2] > 2.0      # at least half order through the contact
+    _, U5 = charged_shock_tube(250)
+    g, prim = I.shock_tube(250)
+    o4 = O.Oracle(250, dx=g["dx"], x0=-1.0, bc="outflow", limiter="minmod", cfl=0.4)
+    U4 = o4.prim2cons_field(*prim)
+    o4.run(U4, 100000, t_end=0.8)
+    assert np.array_equal(U5[:4], U4)
+
+
+def test_charge_is_conserved_on_a_periodic_blast():
+    n = 16
+    g, prim = I.spherical_blast(n)
+    c = I.cell_centres(n, -1.0, g["dx"])
+    zz, yy, xx = np.meshgrid(c, c, c, indexing="ij")
+    nn = 1.0 + 0.5 * np.cos(np.pi * xx) * np.sin(np.pi * yy)
+    o = O.Oracle(n, n, n, dx=g["dx"], x0=-1.0, y0=-1.0, z0=-1.0, bc="periodic", charge=1)
+    U = o.prim2cons_field(*prim, n=nn)
+    s0 = o.conservation_sums(U)
+    o.run(U, 4)
+    s1 = o.conservation_sums(U)
+    assert abs(s1[4] - s0[4]) <= 1e-13 * abs(s0[4])
+    assert abs(s1[0] - s0[0]) <= 1e-13 * abs(s0[0])
+
+
+def ellipsoidal_charge_error(n, t0=2.0, t1=2.4, half=3.0):
+    """The ellipsoidal flow of Sec. 3.2 along one axis with its charge density
+    n = C_n / prod(t + T_i) exp(-b_n^2 t^2/tau^2) (C_n = 0.75, b_n = 1):
+    relative L1 error of n in |x| < 1.2."""
+    dx = 2 * half / n
+    x = I.cell_centres(n, -half, dx)
+    e, (v,) = exact.ellipsoidal([x], t0)
+    nn, _ = exact.ellipsoidal([x], t0, C=0.75, b=1.0)
+    dt = 0.2 * dx
+    steps = int(round((t1 - t0) / dt))
+    o = O.Oracle(n, dx=dx, x0=-half, bc="outflow", cs2=0.0, fixed_dt=dt, charge=1)
+    z = np.zeros((1, 1, n))
+    U = o.prim2cons_field(e.reshape(1, 1, n), v.reshape(1, 1, n), z, z, n=nn.reshape(1, 1, n))
+    o.run(U, steps)
+    got = o.charge_density_field(U).ravel()
+    want, _ = exact.ellipsoidal([x], t0 + steps * dt, C=0.75, b=1.0)
+    core = np.abs(x) < 1.2
+    return np.abs(got[core] - want[core]).sum() / want[core].sum()
+
+
+def test_ellipsoidal_charge_density_converges_to_the_exact_solution():
+    """The paper's third test carries n with the flow; the charge field
+    follows its exact solution and the error falls under refinement."""
+    e1 = ellipsoidal_charge_error(120)
+    e2 = ellipsoidal_charge_error(240)
+    assert e1 < 2e-3
+    assert e2 < e1 / 1.8
