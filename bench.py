@@ -523,7 +523,8 @@ def batch_measure(nev, steps, warmup, stream, gpu, no_cpu=False):
                    "path": "hydro_batch_init_hotspots + hydro_batch_set_jets from host arrays, "
                            "hydro_batch_step(1) and hydro_batch_conservation_sums per step, "
                            "hydro_batch_event_status"},
-           "init_s": init_s, "events_nonfinite": int((status != 0).sum()),
+           "init_s": init_s, "events_nonfinite": int((status == 6).sum()),
+           "events_repaired": int((status == 4).sum()),
            "clocks": clk.summary()}
     if not no_cpu:
         out["cpu_baseline"] = batch_cpu_baseline(cells / nev)
@@ -611,7 +612,8 @@ def run_batch(args):
                               "rate_dt_jet": other_ms, "groups": n_other},
                 "gpu_launches": int(round(launches_per_step * args.steps)),
                 "kernel_timing": "separate eager pass of min(steps, 4) steps",
-                "init_s": init_s, "events_nonfinite": int((status != 0).sum()),
+                "init_s": init_s, "events_nonfinite": int((status == 6).sum()),
+           "events_repaired": int((status == 4).sum()),
                 "clocks": clk.summary()}
         print(json.dumps(line), flush=True)
     return 0

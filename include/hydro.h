@@ -12,7 +12,9 @@
  *
  * Conventions shared by every entry point
  *  - Layout: fields are structure-of-arrays, field-major, x fastest:
- *    U[4][nz][ny][nx]; primitive arrays e, vx, vy, vz are [nz][ny][nx].
+ *    U[nq][nz][ny][nx] with nq = 4, or nq = 5 when the grid carries the
+ *    conserved charge R = n gamma as field 4 (hydro_grid_t.charge);
+ *    primitive arrays e, vx, vy, vz, n are [nz][ny][nx].
  *  - Element type: double for HYDRO_FP64 handles, float for HYDRO_FP32 and
  *    HYDRO_MIXED handles (state, primitives and conserved arrays alike).
  *  - on_device = 1: the pointer is CUDA device memory readable/writable on
@@ -89,6 +91,11 @@ typedef struct {
                                  1: the unsplit MUSCL-Hancock step of Eq. 13 with every flux
                                  term, one RK update of the whole field per stage, CFL rate
                                  summed over the axes; all events of a batch must agree */
+    int charge;               /* 1: carry the conserved charge R = n gamma (Eq. 1, 3, 4) as a
+                                 fifth field with flux R v_d.  The EOS is p(e), so R rides on
+                                 the energy-momentum flow and n = R / gamma on readout.  Split
+                                 sweeps only (HYDRO_E_INVALID with unsplit = 1 or the MLP
+                                 seed); all events of a batch must agree */
 } hydro_grid_t;
 
 /* Equation of state p(e) of Eq. 2 (no charge). */
@@ -138,7 +145,17 @@ hydro_status hydro_set_stream(hydro_t *h, void *stream);
 /* Set the state from primitive fields (e, v): prim->cons of Eq. 4.  Sets t = 0. */
 hydro_status hydro_set_primitives(hydro_t *h, const void *e, const void *vx, const void *vy,
                                   const void *vz, int on_device);
-/* Set / read the conserved state U[4][nz][ny][nx]. */
+/* Charged handles: the state from (e, v) and the rest-frame charge density n
+ * (R = n gamma).  hydro_set_primitives on a charged handle sets R = 0. */
+hydro_status hydro_set_primitives_charged(hydro_t *h, const void *e, const void *vx,
+                                          const void *vy, const void *vz, const void *n,
+                                          int on_device);
+/* Charged handles: n = R / gamma per cell [nz][ny][nx] (v from cons->prim of
+ * the energy-momentum fields; a vacuum cell reads n = R). */
+hydro_status hydro_get_charge_density(hydro_t *h, void *n, int on_device);
+/* Charged handles: the FP64 sum over cells of R dV. */
+hydro_status hydro_charge_sum(hydro_t *h, double *out);
+/* Set / read the conserved state U[nq][nz][ny][nx]. */
 hydro_status hydro_set_conserved(hydro_t *h, const void *U, int on_device);
 hydro_status hydro_get_conserved(hydro_t *h, void *U, int on_device);
 /* Read primitives e, vx, vy, vz (cons->prim of Eq. 23 on the device).  A cell
@@ -151,7 +168,8 @@ hydro_status hydro_get_primitives(hydro_t *h, void *e, void *vx, void *vy, void 
  * v = sum_j A_j g_j u_j / e.  spots: host array [nspots][7] = (cx, cy, cz, A, ux, uy, uz). */
 hydro_status hydro_init_hotspots(hydro_t *h, const double *spots, int nspots, double sigma,
                                  double e_bg);
-/* Jet source (x0, y0, z0, nx, ny, nz, dE/dx, sigma), added as U += dt S(t) once per step. */
+/* Jet source (x0, y0, z0, nx, ny, nz, dE/dx, sigma), added as U += dt S(t) once per step
+ * (energy and momentum only; a hot-spot state carries no charge, R = 0). */
 hydro_status hydro_set_jet(hydro_t *h, const double jet[8]);
 
 /* Advance up to nsteps full steps (CFL or fixed dt, jet source, Strang sweeps),
@@ -228,13 +246,19 @@ hydro_status hydro_batch_init_hotspots(hydro_batch_t *b, const double *spots, in
 hydro_status hydro_batch_set_primitives(hydro_batch_t *b, int event, const void *e,
                                         const void *vx, const void *vy, const void *vz,
                                         int on_device);
+/* Charged batches: one event's state from (e, v, n). */
+hydro_status hydro_batch_set_primitives_charged(hydro_batch_t *b, int event, const void *e,
+                                                const void *vx, const void *vy, const void *vz,
+                                                const void *n, int on_device);
+/* Charged batches: out host [nevents], the FP64 sum of R dV per event. */
+hydro_status hydro_batch_charge_sums(hydro_batch_t *b, double *out);
 /* jets: host array [nevents][8]. */
 hydro_status hydro_batch_set_jets(hydro_batch_t *b, const double *jets);
 /* Advance every event nsteps steps, each with its own CFL dt.  One launch per
  * sweep covers all events; use_graph = 1 captures one step in a CUDA graph
  * on first use and replays it. */
 hydro_status hydro_batch_step(hydro_batch_t *b, int nsteps, int use_graph);
-/* Set / read one event's conserved state U[4][nz][ny][nx] (setting clears its status bits). */
+/* Set / read one event's conserved state U[nq][nz][ny][nx] (setting clears its status bits). */
 hydro_status hydro_batch_set_conserved(hydro_batch_t *b, int event, const void *U, int on_device);
 hydro_status hydro_batch_get_conserved(hydro_batch_t *b, int event, void *U, int on_device);
 hydro_status hydro_batch_get_primitives(hydro_batch_t *b, int event, void *e, void *vx,

@@ -61,6 +61,7 @@ static void set_consts(SchemeConsts<R> &k, R alpha, R delta, R cs2) {
 
 struct Solver {
     int nevents = 0;
+    int nq = 4;               // conserved fields per cell: 4, or 5 with the charge R
     int prec = HYDRO_FP64;
     int rk = 2;
     double cfl = 0.4, fixed_dt = 0.0;
@@ -183,6 +184,7 @@ struct Solver {
         c.rate_sum = unsplit ? 1 : 0;
         c.jet_cells = jet_cells;
         c.nevents = nevents;
+        c.nq = nq;
         return c;
     }
 
@@ -205,6 +207,14 @@ struct Solver {
         for (int e = 1; e < n; ++e)
             if ((grids[e].unsplit != 0) != unsplit)
                 return fail(HYDRO_E_INVALID, "all events of a batch use the same scheme (unsplit)");
+        nq = g0.charge ? 5 : 4;
+        for (int e = 1; e < n; ++e)
+            if ((grids[e].charge ? 5 : 4) != nq)
+                return fail(HYDRO_E_INVALID, "all events of a batch carry the charge or none does");
+        if (nq == 5 && unsplit)
+            return fail(HYDRO_E_INVALID, "the conserved charge is carried by the split sweeps only");
+        if (nq == 5 && eos && eos->kind == HYDRO_EOS_TABLE && eos->seed == HYDRO_SEED_MLP)
+            return fail(HYDRO_E_INVALID, "the conserved charge does not run with the MLP seed");
         cfl = g0.cfl;
         fixed_dt = g0.fixed_dt;
         elem = prec == HYDRO_FP64 ? 8 : 4;
@@ -238,10 +248,12 @@ struct Solver {
             }
             q.lo[0] = g.x0; q.lo[1] = g.y0; q.lo[2] = g.z0;
             q.cells = (long long)g.nx * g.ny * g.nz;
-            if (4 * q.cells > 2147483647LL)   // sweeps index fields with 32-bit offsets
-                return fail(HYDRO_E_INVALID, "an event may hold at most 536,870,911 cells");
+            if (nq * q.cells > 2147483647LL)   // sweeps index fields with 32-bit offsets
+                return fail(HYDRO_E_INVALID, nq == 4 ? "an event may hold at most 536,870,911 cells"
+                                                     : "a charged event may hold at most "
+                                                       "429,496,729 cells");
             q.off = off;
-            off += 4 * q.cells;
+            off += nq * q.cells;
             total_cells += q.cells;
         }
         // scheme
@@ -310,7 +322,7 @@ struct Solver {
         sc.c32.inv_h = float(sc.inv_h);
         sc.c32.e_max = float(sc.e_max);
         // device memory
-        const size_t bytes = (size_t)4 * total_cells * elem;
+        const size_t bytes = (size_t)nq * total_cells * elem;
         CK(cudaMalloc(&d_state[0], bytes));
         CK(cudaMalloc(&d_state[1], bytes));
         CK(cudaMemset(d_state[0], 0, bytes));
@@ -347,8 +359,8 @@ struct Solver {
         CK(cudaMalloc(&d_cell_items, cell_items.size() * sizeof(WorkItem)));
         CK(cudaMemcpy(d_cell_items, cell_items.data(), cell_items.size() * sizeof(WorkItem),
                       cudaMemcpyHostToDevice));
-        CK(cudaMalloc(&d_partial, cell_items.size() * 4 * sizeof(double)));
-        CK(cudaMalloc(&d_sums, (size_t)n * 4 * sizeof(double)));
+        CK(cudaMalloc(&d_partial, cell_items.size() * nq * sizeof(double)));
+        CK(cudaMalloc(&d_sums, (size_t)n * nq * sizeof(double)));
         if (n > 1) CK(cudaMalloc(&d_work_counter, sizeof(int)));
         if (unsplit) {
             hydro_status st = init_unsplit();
@@ -514,6 +526,7 @@ struct Solver {
         a.rate_clk = rate_clk;
         a.sms = sms;
         a.stream = stream;
+        a.charge = nq == 5;
         if (prec == HYDRO_FP64) return launch_sweep_f64(a);
         if (prec == HYDRO_FP32) return launch_sweep_f32(a);
         return launch_sweep_mixed(a);
@@ -746,16 +759,19 @@ struct Solver {
         return (char *)d_state[buf] + (size_t)geo[e].off * elem;
     }
 
+    // pn: the rest-frame charge density (charged handles; null sets R = 0)
     hydro_status set_primitives(int e, const void *pe, const void *pvx, const void *pvy,
-                                const void *pvz, int on_device) {
+                                const void *pvz, int on_device, const void *pn = nullptr) {
         rate_valid = false;
         if (e < 0 || e >= nevents) return fail(HYDRO_E_INVALID, "bad event");
         if (!pe || !pvx || !pvy || !pvz) return fail(HYDRO_E_INVALID, "null pointer");
+        if (pn && nq != 5) return fail(HYDRO_E_INVALID, "the handle carries no charge");
         const size_t fb = (size_t)geo[e].cells * elem;
         // stage the primitives in the spare buffer at this event's place
         char *stage = (char *)event_ptr(1 - cur, e);
-        const void *src[4] = {pe, pvx, pvy, pvz};
-        for (int f = 0; f < 4; ++f)
+        const void *src[5] = {pe, pvx, pvy, pvz, pn};
+        const int nsrc = pn ? 5 : 4;
+        for (int f = 0; f < nsrc; ++f)
             CK(cudaMemcpyAsync(stage + f * fb, src[f], fb,
                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, stream));
         CellLaunch c = cell_launch();
@@ -776,7 +792,8 @@ struct Solver {
         CK(launch_prim2cons(c, base + (off + 0 * geo[e].cells) * elem - 0,
                             base + (off + 1 * geo[e].cells) * elem,
                             base + (off + 2 * geo[e].cells) * elem,
-                            base + (off + 3 * geo[e].cells) * elem, d_state[cur]));
+                            base + (off + 3 * geo[e].cells) * elem,
+                            pn ? base + (off + 4 * geo[e].cells) * elem : nullptr, d_state[cur]));
         CK(cudaStreamSynchronize(stream));
         return reset_time(e);
     }
@@ -798,7 +815,7 @@ struct Solver {
         rate_valid = false;
         if (e < 0 || e >= nevents || !U) return fail(HYDRO_E_INVALID, "bad argument");
         CK(cudaMemsetAsync(d_flags + e, 0, sizeof(unsigned), stream));
-        CK(cudaMemcpyAsync(event_ptr(cur, e), U, (size_t)4 * geo[e].cells * elem,
+        CK(cudaMemcpyAsync(event_ptr(cur, e), U, (size_t)nq * geo[e].cells * elem,
                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, stream));
         CK(cudaStreamSynchronize(stream));
         return HYDRO_OK;
@@ -806,7 +823,7 @@ struct Solver {
 
     hydro_status get_conserved(int e, void *U, int on_device) {
         if (e < 0 || e >= nevents || !U) return fail(HYDRO_E_INVALID, "bad argument");
-        CK(cudaMemcpyAsync(U, event_ptr(cur, e), (size_t)4 * geo[e].cells * elem,
+        CK(cudaMemcpyAsync(U, event_ptr(cur, e), (size_t)nq * geo[e].cells * elem,
                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, stream));
         CK(cudaStreamSynchronize(stream));
         return HYDRO_OK;
@@ -836,13 +853,42 @@ struct Solver {
         return HYDRO_OK;
     }
 
-    hydro_status sums(double *out) {
+    // per event: out[event][4] the energy-momentum sums, charge[event] (may be
+    // null) the charge sum of a charged handle
+    hydro_status sums(double *out, double *charge = nullptr) {
+        if (charge && nq != 5) return fail(HYDRO_E_INVALID, "the handle carries no charge");
         CellLaunch c = cell_launch();
         CK(launch_sums(c, d_state[cur], d_partial));
         CK(launch_sums_final(d_cell_items, (int)cell_items.size(), d_partial, d_geo, d_sums,
-                             nevents, stream));
-        CK(cudaMemcpyAsync(out, d_sums, (size_t)nevents * 4 * sizeof(double),
-                           cudaMemcpyDeviceToHost, stream));
+                             nevents, nq, stream));
+        std::vector<double> h((size_t)nevents * nq);
+        CK(cudaMemcpyAsync(h.data(), d_sums, h.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                           stream));
+        CK(cudaStreamSynchronize(stream));
+        for (int e = 0; e < nevents; ++e) {
+            if (out)
+                for (int q = 0; q < 4; ++q) out[4 * e + q] = h[(size_t)nq * e + q];
+            if (charge) charge[e] = h[(size_t)nq * e + 4];
+        }
+        return HYDRO_OK;
+    }
+
+    // n = R / gamma of event e into n (host or device), via the spare buffer
+    hydro_status charge_density(int e, void *n, int on_device) {
+        if (nq != 5) return fail(HYDRO_E_INVALID, "the handle carries no charge");
+        if (e < 0 || e >= nevents || !n) return fail(HYDRO_E_INVALID, "bad argument");
+        size_t first = 0;
+        while (cell_items[first].event != e) ++first;
+        size_t last = first;
+        while (last < cell_items.size() && cell_items[last].event == e) ++last;
+        CellLaunch c = cell_launch();
+        c.items = d_cell_items + first;
+        c.nitems = (int)(last - first);
+        c.blocks = std::min(c.nitems, sms * 8);
+        char *stage = (char *)event_ptr(1 - cur, e);
+        CK(launch_charge_density(c, d_state[cur], stage));
+        CK(cudaMemcpyAsync(n, stage, (size_t)geo[e].cells * elem,
+                           on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, stream));
         CK(cudaStreamSynchronize(stream));
         return HYDRO_OK;
     }
@@ -1027,6 +1073,22 @@ hydro_status hydro_set_primitives(hydro_t *h, const void *e, const void *vx, con
                                   const void *vz, int on_device) {
     HANDLE(h);
     return h->s.set_primitives(0, e, vx, vy, vz, on_device);
+}
+hydro_status hydro_set_primitives_charged(hydro_t *h, const void *e, const void *vx,
+                                          const void *vy, const void *vz, const void *n,
+                                          int on_device) {
+    HANDLE(h);
+    if (!n) return fail(HYDRO_E_INVALID, "null n");
+    return h->s.set_primitives(0, e, vx, vy, vz, on_device, n);
+}
+hydro_status hydro_get_charge_density(hydro_t *h, void *n, int on_device) {
+    HANDLE(h);
+    return h->s.charge_density(0, n, on_device);
+}
+hydro_status hydro_charge_sum(hydro_t *h, double *out) {
+    HANDLE(h);
+    if (!out) return fail(HYDRO_E_INVALID, "null out");
+    return h->s.sums(nullptr, out);
 }
 hydro_status hydro_set_conserved(hydro_t *h, const void *U, int on_device) {
     HANDLE(h);
@@ -1214,6 +1276,18 @@ hydro_status hydro_batch_set_primitives(hydro_batch_t *b, int event, const void 
                                         int on_device) {
     HANDLE(b);
     return b->s.set_primitives(event, e, vx, vy, vz, on_device);
+}
+hydro_status hydro_batch_set_primitives_charged(hydro_batch_t *b, int event, const void *e,
+                                                const void *vx, const void *vy, const void *vz,
+                                                const void *n, int on_device) {
+    HANDLE(b);
+    if (!n) return fail(HYDRO_E_INVALID, "null n");
+    return b->s.set_primitives(event, e, vx, vy, vz, on_device, n);
+}
+hydro_status hydro_batch_charge_sums(hydro_batch_t *b, double *out) {
+    HANDLE(b);
+    if (!out) return fail(HYDRO_E_INVALID, "null out");
+    return b->s.sums(nullptr, out);
 }
 hydro_status hydro_batch_set_jets(hydro_batch_t *b, const double *jets) {
     HANDLE(b);

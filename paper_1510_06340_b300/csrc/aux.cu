@@ -52,11 +52,13 @@ __device__ __forceinline__ void c2p_full(const Scheme &sc, R E, R Mx, R My, R Mz
 }
 
 // ------------------------------------------------------------------ prim -> cons
+// with nq = 5 also R = n gamma (Eq. 4) from the rest-frame charge density n
+// (n null: R = 0)
 template <class R>
 __global__ void k_prim2cons(const EventGeo *__restrict__ ev, const WorkItem *__restrict__ items,
                             int nitems, const R *__restrict__ e, const R *__restrict__ vx,
-                            const R *__restrict__ vy, const R *__restrict__ vz, R *__restrict__ U,
-                            Scheme sc) {
+                            const R *__restrict__ vy, const R *__restrict__ vz,
+                            const R *__restrict__ nr, R *__restrict__ U, Scheme sc, int nq) {
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
         const WorkItem w = items[it];
         const EventGeo &g = ev[w.event];
@@ -72,6 +74,7 @@ __global__ void k_prim2cons(const EventGeo *__restrict__ ev, const WorkItem *__r
             u[g.cells] = wv * x;
             u[2 * g.cells] = wv * y;
             u[3 * g.cells] = wv * z;
+            if (nq == 5) u[4 * g.cells] = nr ? nr[c] * sqrt(g2) : R(0);
         }
     }
 }
@@ -101,6 +104,26 @@ __global__ void k_cons2prim(const EventGeo *__restrict__ ev, const WorkItem *__r
                 ee = R(de); x = R(dx_); y = R(dy_); z = R(dz_);
             }
             e[c] = ee; vx[c] = x; vy[c] = y; vz[c] = z;
+        }
+    }
+}
+
+// rest-frame charge density n = R / gamma = R sqrt(1 - v^2), v from the
+// energy-momentum fields (vacuum: v = 0, n = R)
+template <class R>
+__global__ void k_charge_density(const EventGeo *__restrict__ ev,
+                                 const WorkItem *__restrict__ items, int nitems,
+                                 const R *__restrict__ U, R *__restrict__ n, Scheme sc) {
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const WorkItem w = items[it];
+        const EventGeo &g = ev[w.event];
+        for (int k = threadIdx.x; k < w.count; k += blockDim.x) {
+            const long long c = w.first + k;
+            const R *u = U + g.off + c;
+            int iters;
+            R ee, x, y, z;
+            c2p_full<R>(sc, u[0], u[g.cells], u[2 * g.cells], u[3 * g.cells], ee, x, y, z, iters);
+            n[c] = u[4 * g.cells] * dsqrt_(R(1) - (x * x + y * y + z * z));
         }
     }
 }
@@ -271,31 +294,33 @@ __global__ void k_jet(const EventGeo *__restrict__ ev, R *__restrict__ U,
 }
 
 // ------------------------------------------------------------------ FP64 sums
+// sums of the nq fields (4, or 5 with the charge) per work item: partial[item][nq]
 template <class R>
 __global__ void k_sums(const EventGeo *__restrict__ ev, const WorkItem *__restrict__ items,
-                       int nitems, const R *__restrict__ U, double *__restrict__ partial) {
-    __shared__ double red[4][32];
+                       int nitems, const R *__restrict__ U, double *__restrict__ partial, int nq) {
+    __shared__ double red[5][32];
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
         const WorkItem w = items[it];
         const EventGeo &g = ev[w.event];
-        double s[4] = {0.0, 0.0, 0.0, 0.0};
+        double s[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
         for (int k = threadIdx.x; k < w.count; k += blockDim.x) {
             const R *u = U + g.off + w.first + k;
 #pragma unroll
             for (int q = 0; q < 4; ++q) s[q] += double(u[q * g.cells]);
+            if (nq == 5) s[4] += double(u[4 * g.cells]);
         }
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
+        for (int q = 0; q < 5; ++q)
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) s[q] += __shfl_xor_sync(0xffffffffu, s[q], o);
         const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
         if (lane == 0)
-            for (int q = 0; q < 4; ++q) red[q][wid] = s[q];
+            for (int q = 0; q < 5; ++q) red[q][wid] = s[q];
         __syncthreads();
-        if (threadIdx.x < 4) {
+        if (int(threadIdx.x) < nq) {
             double t = 0.0;
             for (int k = 0; k < int(blockDim.x >> 5); ++k) t += red[threadIdx.x][k];
-            partial[4LL * it + threadIdx.x] = t;
+            partial[(long long)nq * it + threadIdx.x] = t;
         }
         __syncthreads();
     }
@@ -308,8 +333,8 @@ constexpr int SUMS_FINAL_THREADS = 256;
 
 __global__ void __launch_bounds__(SUMS_FINAL_THREADS)
 k_sums_final(const WorkItem *__restrict__ items, int nitems, const double *__restrict__ partial,
-             const EventGeo *__restrict__ ev, double *__restrict__ out, int nevents) {
-    __shared__ double red[4][SUMS_FINAL_THREADS];
+             const EventGeo *__restrict__ ev, double *__restrict__ out, int nevents, int nq) {
+    __shared__ double red[5][SUMS_FINAL_THREADS];
     __shared__ int range[2];
     const int e = blockIdx.x;
     if (threadIdx.x < 2) {   // first item of event e (t = 0) and of event e + 1 (t = 1)
@@ -322,24 +347,23 @@ k_sums_final(const WorkItem *__restrict__ items, int nitems, const double *__res
         range[threadIdx.x] = lo;
     }
     __syncthreads();
-    double s[4] = {0.0, 0.0, 0.0, 0.0};
+    double s[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
     for (int it = range[0] + int(threadIdx.x); it < range[1]; it += SUMS_FINAL_THREADS) {
-        const double *p = partial + 4LL * it;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) s[q] += p[q];
+        const double *p = partial + (long long)nq * it;
+        for (int q = 0; q < nq; ++q) s[q] += p[q];
     }
 #pragma unroll
-    for (int q = 0; q < 4; ++q) red[q][threadIdx.x] = s[q];
+    for (int q = 0; q < 5; ++q) red[q][threadIdx.x] = s[q];
     __syncthreads();
     for (int w = SUMS_FINAL_THREADS / 2; w > 0; w >>= 1) {
         if (int(threadIdx.x) < w)
 #pragma unroll
-            for (int q = 0; q < 4; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + w];
+            for (int q = 0; q < 5; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + w];
         __syncthreads();
     }
-    if (threadIdx.x < 4) {
+    if (int(threadIdx.x) < nq) {
         const EventGeo &g = ev[e];
-        out[4 * e + threadIdx.x] = red[threadIdx.x][0] * (g.h[0] * g.h[1] * g.h[2]);
+        out[nq * e + threadIdx.x] = red[threadIdx.x][0] * (g.h[0] * g.h[1] * g.h[2]);
     }
 }
 
@@ -351,7 +375,7 @@ k_sums_final(const WorkItem *__restrict__ items, int nitems, const double *__res
 template <class R>
 __global__ void k_hotspots(const EventGeo *__restrict__ ev, const WorkItem *__restrict__ items,
                            int nitems, const double *__restrict__ spots, int nspots, double sigma,
-                           double e_bg, R *__restrict__ U, Scheme sc) {
+                           double e_bg, R *__restrict__ U, Scheme sc, int nq) {
     const R inv = R(1.0 / (2.0 * sigma * sigma));
     const R cut = R(9.0 * sigma);
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
@@ -393,6 +417,7 @@ __global__ void k_hotspots(const EventGeo *__restrict__ ev, const WorkItem *__re
             u[g.cells] = wv * vx;
             u[2 * g.cells] = wv * vy;
             u[3 * g.cells] = wv * vz;
+            if (nq == 5) u[4 * g.cells] = R(0);   // hot-spot states carry no charge
         }
     }
 }
@@ -400,15 +425,15 @@ __global__ void k_hotspots(const EventGeo *__restrict__ ev, const WorkItem *__re
 // ------------------------------------------------------------------ finite check
 template <class R>
 __global__ void k_finite(const EventGeo *__restrict__ ev, const WorkItem *__restrict__ items,
-                         int nitems, const R *__restrict__ U, EventClock *__restrict__ clk) {
+                         int nitems, const R *__restrict__ U, EventClock *__restrict__ clk,
+                         int nq) {
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
         const WorkItem w = items[it];
         const EventGeo &g = ev[w.event];
         bool bad = false;
         for (int k = threadIdx.x; k < w.count; k += blockDim.x) {
             const R *u = U + g.off + w.first + k;
-#pragma unroll
-            for (int q = 0; q < 4; ++q) bad |= !isfinite(double(u[q * g.cells]));
+            for (int q = 0; q < nq; ++q) bad |= !isfinite(double(u[q * g.cells]));
         }
         if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) clk[w.event].status = 6;
     }
@@ -440,14 +465,23 @@ __global__ void k_c2p_newton(Scheme sc, const R *__restrict__ U, long long n, in
     } while (0)
 
 cudaError_t launch_prim2cons(const CellLaunch &c, const void *e, const void *vx, const void *vy,
-                             const void *vz, void *U) {
+                             const void *vz, const void *n, void *U) {
     HY_DISPATCH(c.prec,
         (k_prim2cons<double><<<c.blocks, c.threads, 0, c.stream>>>(c.ev, c.items, c.nitems,
             (const double *)e, (const double *)vx, (const double *)vy, (const double *)vz,
-            (double *)U, c.sc)),
+            (const double *)n, (double *)U, c.sc, c.nq)),
         (k_prim2cons<float><<<c.blocks, c.threads, 0, c.stream>>>(c.ev, c.items, c.nitems,
             (const float *)e, (const float *)vx, (const float *)vy, (const float *)vz,
-            (float *)U, c.sc)));
+            (const float *)n, (float *)U, c.sc, c.nq)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_charge_density(const CellLaunch &c, const void *U, void *n) {
+    HY_DISPATCH(c.prec,
+        (k_charge_density<double><<<c.blocks, c.threads, 0, c.stream>>>(c.ev, c.items, c.nitems,
+            (const double *)U, (double *)n, c.sc)),
+        (k_charge_density<float><<<c.blocks, c.threads, 0, c.stream>>>(c.ev, c.items, c.nitems,
+            (const float *)U, (float *)n, c.sc)));
     return cudaGetLastError();
 }
 
@@ -490,15 +524,16 @@ cudaError_t launch_jet(const CellLaunch &c, void *U, const EventClock *clk) {
 cudaError_t launch_sums(const CellLaunch &c, const void *U, double *partial) {
     HY_DISPATCH(c.prec,
         (k_sums<double><<<c.blocks, c.threads, 0, c.stream>>>(c.ev, c.items, c.nitems,
-            (const double *)U, partial)),
+            (const double *)U, partial, c.nq)),
         (k_sums<float><<<c.blocks, c.threads, 0, c.stream>>>(c.ev, c.items, c.nitems,
-            (const float *)U, partial)));
+            (const float *)U, partial, c.nq)));
     return cudaGetLastError();
 }
 
 cudaError_t launch_sums_final(const WorkItem *items, int nitems, const double *partial,
-                              const EventGeo *ev, double *out, int nevents, cudaStream_t s) {
-    k_sums_final<<<nevents, SUMS_FINAL_THREADS, 0, s>>>(items, nitems, partial, ev, out, nevents);
+                              const EventGeo *ev, double *out, int nevents, int nq, cudaStream_t s) {
+    k_sums_final<<<nevents, SUMS_FINAL_THREADS, 0, s>>>(items, nitems, partial, ev, out, nevents,
+                                                        nq);
     return cudaGetLastError();
 }
 
@@ -506,18 +541,18 @@ cudaError_t launch_hotspots(const CellLaunch &c, const double *spots, int nspots
                             double e_bg, void *U) {
     HY_DISPATCH(c.prec,
         (k_hotspots<double><<<c.blocks, c.threads, 0, c.stream>>>(c.ev, c.items, c.nitems, spots,
-            nspots, sigma, e_bg, (double *)U, c.sc)),
+            nspots, sigma, e_bg, (double *)U, c.sc, c.nq)),
         (k_hotspots<float><<<c.blocks, c.threads, 0, c.stream>>>(c.ev, c.items, c.nitems, spots,
-            nspots, sigma, e_bg, (float *)U, c.sc)));
+            nspots, sigma, e_bg, (float *)U, c.sc, c.nq)));
     return cudaGetLastError();
 }
 
 cudaError_t launch_finite(const CellLaunch &c, const void *U, EventClock *clk) {
     HY_DISPATCH(c.prec,
         (k_finite<double><<<c.blocks, c.threads, 0, c.stream>>>(c.ev, c.items, c.nitems,
-            (const double *)U, clk)),
+            (const double *)U, clk, c.nq)),
         (k_finite<float><<<c.blocks, c.threads, 0, c.stream>>>(c.ev, c.items, c.nitems,
-            (const float *)U, clk)));
+            (const float *)U, clk, c.nq)));
     return cudaGetLastError();
 }
 

@@ -21,14 +21,39 @@
 
 namespace hy {
 
-template <class R>
-struct V4 {
-    R e, n, t1, t2;   // E, M along the sweep axis, the two transverse M
+// The conserved fields of one cell in sweep-slot order: E, M along the
+// sweep axis, the two transverse M; with CH the conserved charge R = n gamma
+// (Eq. 3-4) rides along as a fifth field.
+template <class R, bool CH = false>
+struct VS {
+    R e, n, t1, t2;
 };
+template <class R>
+struct VS<R, true> {
+    R e, n, t1, t2, r;
+};
+template <class R>
+using V4 = VS<R, false>;
+template <class R>
+using V5 = VS<R, true>;
 
 template <class R>
 __device__ __forceinline__ V4<R> v4(R a, R b, R c, R d) {
     V4<R> v; v.e = a; v.n = b; v.t1 = c; v.t2 = d; return v;
+}
+// the energy-momentum part of a cell, and a cell made of one plus a charge
+template <class R>
+__device__ __forceinline__ V4<R> head(const V4<R> &x) { return x; }
+template <class R>
+__device__ __forceinline__ V4<R> head(const V5<R> &x) { return v4<R>(x.e, x.n, x.t1, x.t2); }
+template <class R>
+__device__ __forceinline__ V5<R> with_r(const V4<R> &x, R r) {
+    V5<R> v; v.e = x.e; v.n = x.n; v.t1 = x.t1; v.t2 = x.t2; v.r = r; return v;
+}
+template <class V>
+__device__ __forceinline__ V vzero() {
+    V v{};
+    return v;
 }
 
 // Multiply-adds of the formulas are written out as fma_, so they are fused
@@ -121,6 +146,24 @@ template <>
 __device__ __forceinline__ void tmul<float>(float s, const V4<float> &x, float &t1, float &t2) {
     const float2 t = mul2(hi2(x), dup2(s));
     t1 = t.x; t2 = t.y;
+}
+
+// the same field-wise helpers with the charge: the four-field forms plus R
+template <class R>
+__device__ __forceinline__ V5<R> vsub(const V5<R> &x, const V5<R> &y) {
+    return with_r(vsub<R>(head(x), head(y)), x.r - y.r);
+}
+template <class R>
+__device__ __forceinline__ V5<R> vadd(const V5<R> &x, const V5<R> &y) {
+    return with_r(vadd<R>(head(x), head(y)), x.r + y.r);
+}
+template <class R>
+__device__ __forceinline__ V5<R> vfma(R s, const V5<R> &x, const V5<R> &y) {
+    return with_r(vfma<R>(s, head(x), head(y)), fma_(s, x.r, y.r));
+}
+template <class R>
+__device__ __forceinline__ V5<R> vmul(R s, const V5<R> &x) {
+    return with_r(vmul<R>(s, head(x)), s * x.r);
 }
 
 // ---------------------------------------------------------------- math helpers
@@ -420,8 +463,11 @@ enum { PREC_F64 = 0, PREC_F32 = 1, PREC_MIXED = 2 };
 
 // MUSTA2: the kernel writes out the two-stage MUSTA-FORCE (the RK3 kernels,
 // whose registers are capped, keep the loop)
-template <class R, int PREC, int EOSK, int LIM = -1, bool COUNT = true, bool MUSTA2 = true>
+template <class R, int PREC, int EOSK, int LIM = -1, bool COUNT = true, bool MUSTA2 = true,
+          bool CH = false>
 struct Physics {
+    using V = VS<R, CH>;   // the fields a sweep carries
+    static constexpr bool kCharge = CH;
     Scheme sc;
     R al_, hclf_;   // alpha dt/dx and 1 / (4 alpha dt/dx) of the current sweep
     // FLAG_* bits this thread met since the last report_flags (a |M| cap, a
@@ -480,12 +526,18 @@ struct Physics {
     }
 
     // Eq. 3 along the sweep axis
-    __device__ __forceinline__ V4<R> flux(const V4<R> &U) const {
-        const Prim<R> q = prim(U);
-        // Eq. 3 along the axis: ((E + p) v_n, M_n v_n + p, M_t1 v_n, M_t2 v_n)
+    __device__ __forceinline__ V flux(const V &U) const {
+        const V4<R> U4 = head(U);
+        const Prim<R> q = prim(U4);
+        // Eq. 3 along the axis: ((E + p) v_n, M_n v_n + p, M_t1 v_n, M_t2 v_n, R v_n)
         R t1, t2;
-        tmul<R>(q.vn, U, t1, t2);
-        return v4<R>(q.fe, fma_(U.n, q.vn, q.p), t1, t2);
+        tmul<R>(q.vn, U4, t1, t2);
+        return make(v4<R>(q.fe, fma_(U.n, q.vn, q.p), t1, t2), U, q.vn);
+    }
+    // the four energy-momentum components, with the charge flux R v_n when carried
+    __device__ __forceinline__ static V make(const V4<R> &f, const V &U, R vn) {
+        if constexpr (CH) return with_r(f, U.r * vn);
+        else return f;
     }
 
     // The conformal FP32/FP64 sweeps take the |M| cap (R9) per group of flux
@@ -498,7 +550,7 @@ struct Physics {
     // through flux() where a state's FP32 recovery gives |v| > 0.99.
     static constexpr bool CAP_GROUPS = EOSK == EOS_CONFORMAL && !COUNT;
 
-    __device__ __forceinline__ V4<R> flux_uncapped(const V4<R> &U, bool &capped) const {
+    __device__ __forceinline__ V flux_uncapped(const V &U, bool &capped) const {
         const SchemeConsts<R> &k = K();
         const R E = fmax_(U.e, R(0));
         const R M2 = fma_(U.t2, U.t2, fma_(U.t1, U.t1, U.n * U.n));
@@ -518,11 +570,11 @@ struct Physics {
         }
         const R vn = U.n * inv;
         R t1, t2;
-        tmul<R>(vn, U, t1, t2);
-        return v4<R>(fe, fma_(U.n, vn, W - E), t1, t2);
+        tmul<R>(vn, head(U), t1, t2);
+        return make(v4<R>(fe, fma_(U.n, vn, W - E), t1, t2), U, vn);
     }
     template <bool UNCAPPED>
-    __device__ __forceinline__ V4<R> flux_g(const V4<R> &U, bool &capped) const {
+    __device__ __forceinline__ V flux_g(const V &U, bool &capped) const {
         if constexpr (UNCAPPED) return flux_uncapped(U, capped);
         else return flux(U);
     }
@@ -615,7 +667,8 @@ struct Physics {
         return m;
     }
 
-    __device__ __forceinline__ bool admissible(const V4<R> &U) const {
+    template <class VV>
+    __device__ __forceinline__ bool admissible(const VV &U) const {
         const R M2 = fma_(U.t2, U.t2, fma_(U.t1, U.t1, U.n * U.n));
         const R cap = K().omd * U.e;
         return U.e > R(0) && M2 < cap * cap;
@@ -623,18 +676,21 @@ struct Physics {
 
     // Limited MUSCL faces (Eq. 15-17) and the Hancock half step (Eq. 13, the
     // sweep-axis term), with the admissibility fallback (R9).
-    __device__ __forceinline__ void faces(const V4<R> &vm, const V4<R> &v0, const V4<R> &vp, R lam,
-                                          V4<R> &ul, V4<R> &ur) const {
+    __device__ __forceinline__ void faces(const V &vm, const V &v0, const V &vp, R lam, V &ul,
+                                          V &ur) const {
         const int lim = sc.limiter;
         const R half = R(0.5);
-        const V4<R> a = vsub(v0, vm), b = vsub(vp, v0);
-        const V4<R> sl = v4<R>(slope_ct<LIM, R>(lim, a.e, b.e), slope_ct<LIM, R>(lim, a.n, b.n),
-                               slope_ct<LIM, R>(lim, a.t1, b.t1),
-                               slope_ct<LIM, R>(lim, a.t2, b.t2));
+        const V a = vsub(v0, vm), b = vsub(vp, v0);
+        const V4<R> sl4 = v4<R>(slope_ct<LIM, R>(lim, a.e, b.e), slope_ct<LIM, R>(lim, a.n, b.n),
+                                slope_ct<LIM, R>(lim, a.t1, b.t1),
+                                slope_ct<LIM, R>(lim, a.t2, b.t2));
+        V sl;
+        if constexpr (CH) sl = with_r(sl4, slope_ct<LIM, R>(lim, a.r, b.r));
+        else sl = sl4;
         ul = vfma<R>(-half, sl, v0);
         ur = vfma<R>(half, sl, v0);
         if (sc.hancock) {
-            V4<R> FL, FR;
+            V FL, FR;
             if constexpr (CAP_GROUPS) {
                 bool capped = false;
                 FL = flux_uncapped(ul, capped);
@@ -644,7 +700,7 @@ struct Physics {
                 FL = flux(ul);
                 FR = flux(ur);
             }
-            const V4<R> d = vsub(FL, FR);
+            const V d = vsub(FL, FR);
             const R hl = half * lam;
             ul = vfma<R>(hl, d, ul);
             ur = vfma<R>(hl, d, ur);
@@ -657,17 +713,17 @@ struct Physics {
     }
 
     // MUSTA-FORCE interface flux (Sec. 2.4 steps 1-5, Eq. 8-11; R1, R2, R4)
-    __device__ __forceinline__ V4<R> musta(const V4<R> &UL, const V4<R> &UR, R lam) const {
+    __device__ __forceinline__ V musta(const V &UL, const V &UR, R lam) const {
         bool capped = false;
         if constexpr (CAP_GROUPS) {
-            V4<R> F;
+            V F;
             if (MUSTA2 && sc.stages == 2) {
                 // two stages written out, so that the predicted states take
                 // fresh registers while the inputs stay for a redo
-                V4<R> FL, FR;
-                const V4<R> F0 = musta_stage<true>(UL, UR, FL, FR, capped);
-                const V4<R> UL1 = vfma<R>(-lam, vsub(F0, FL), UL);
-                const V4<R> UR1 = vfma<R>(-lam, vsub(FR, F0), UR);
+                V FL, FR;
+                const V F0 = musta_stage<true>(UL, UR, FL, FR, capped);
+                const V UL1 = vfma<R>(-lam, vsub(F0, FL), UL);
+                const V UR1 = vfma<R>(-lam, vsub(FR, F0), UR);
                 F = musta_stage<true>(UL1, UR1, FL, FR, capped);
             } else {
                 F = musta_g<true>(UL, UR, lam, capped);
@@ -679,34 +735,34 @@ struct Physics {
     // one FORCE evaluation of Sec. 2.4 (steps 1-4) at (UL, UR), with F(UL), F(UR);
     // the conformal form F_lw / 2 = F(2 U_lw) / 4 (CAP_GROUPS implies p = c2 e)
     template <bool UNCAPPED>
-    __device__ __forceinline__ V4<R> musta_stage(const V4<R> &UL, const V4<R> &UR, V4<R> &FL,
-                                                 V4<R> &FR, bool &capped) const {
+    __device__ __forceinline__ V musta_stage(const V &UL, const V &UR, V &FL, V &FR,
+                                             bool &capped) const {
         const R q4 = R(0.25);
         FL = flux_g<UNCAPPED>(UL, capped);
         FR = flux_g<UNCAPPED>(UR, capped);
-        const V4<R> Flf = vfma<R>(-hclf_, vsub(UR, UL), vmul<R>(q4, vadd(FL, FR)));
-        const V4<R> Ulw2 = vfma<R>(-al_, vsub(FR, FL), vadd(UL, UR));
+        const V Flf = vfma<R>(-hclf_, vsub(UR, UL), vmul<R>(q4, vadd(FL, FR)));
+        const V Ulw2 = vfma<R>(-al_, vsub(FR, FL), vadd(UL, UR));
         return vfma<R>(q4, flux_g<UNCAPPED>(Ulw2, capped), Flf);
     }
     template <bool UNCAPPED>
-    __device__ __forceinline__ V4<R> musta_g(V4<R> UL, V4<R> UR, R lam, bool &capped) const {
+    __device__ __forceinline__ V musta_g(V UL, V UR, R lam, bool &capped) const {
         const R al = al_;
         const R clw = R(0.5) * al;
         const R half = R(0.5), q4 = R(0.25), hclf = hclf_;
-        V4<R> Fc;
+        V Fc;
         const int k = sc.stages;
 #pragma unroll 1
         for (int l = 0; l < k; ++l) {
-            const V4<R> FL = flux_g<UNCAPPED>(UL, capped), FR = flux_g<UNCAPPED>(UR, capped);
+            const V FL = flux_g<UNCAPPED>(UL, capped), FR = flux_g<UNCAPPED>(UR, capped);
             // F = 1/2 F_lw + 1/2 F_lf = 1/2 F_lw + 1/4 (F_L + F_R) - (clf/2) (U_R - U_L)
-            const V4<R> Flf = vfma<R>(-hclf, vsub(UR, UL), vmul<R>(q4, vadd(FL, FR)));
+            const V Flf = vfma<R>(-hclf, vsub(UR, UL), vmul<R>(q4, vadd(FL, FR)));
             if (EOSK == EOS_CONFORMAL) {
                 // p = c2 e makes the flux homogeneous of degree 1, F(2U) = 2 F(U),
                 // and doubling is exact: take F(2 U_lw) / 4 for F_lw / 2
-                const V4<R> Ulw2 = vfma<R>(-al, vsub(FR, FL), vadd(UL, UR));
+                const V Ulw2 = vfma<R>(-al, vsub(FR, FL), vadd(UL, UR));
                 Fc = vfma<R>(q4, flux_g<UNCAPPED>(Ulw2, capped), Flf);
             } else {
-                const V4<R> Ulw = vfma<R>(-clw, vsub(FR, FL), vmul<R>(half, vadd(UL, UR)));
+                const V Ulw = vfma<R>(-clw, vsub(FR, FL), vmul<R>(half, vadd(UL, UR)));
                 Fc = vfma<R>(half, flux_g<UNCAPPED>(Ulw, capped), Flf);
             }
             if (l < k - 1) {
@@ -722,22 +778,21 @@ struct Physics {
 //   window (w0, w1, w2) = (V_{j-2}, V_{j-1}, V_j); faces of cell j-1 are
 //   computed; the flux of interface (j-2)+1/2 once faces of j-2 exist; and
 //   the divergence D_{j-2} = F_{j-3/2} - F_{j-5/2} once both fluxes exist.
-template <class R>
+template <class V>
 struct Stage {
-    V4<R> w0, w1, w2, urp, fp;
+    V w0, w1, w2, urp, fp;
     int n;
 
-    template <class PH>
-    __device__ __forceinline__ bool push(const V4<R> &v, const PH &ph, R lam, V4<R> &cell,
-                                         V4<R> &D) {
+    template <class PH, class R>
+    __device__ __forceinline__ bool push(const V &v, const PH &ph, R lam, V &cell, V &D) {
         w0 = w1; w1 = w2; w2 = v;
         ++n;
         if (n < 3) return false;
-        V4<R> ul, ur;
+        V ul, ur;
         ph.faces(w0, w1, w2, lam, ul, ur);
         bool out = false;
         if (n >= 4) {
-            const V4<R> F = ph.musta(urp, ul, lam);
+            const V F = ph.musta(urp, ul, lam);
             if (n >= 5) {
                 D = vsub(F, fp);
                 cell = w0;
@@ -750,13 +805,12 @@ struct Stage {
     }
 
     // push once the window is full (n >= 5): always yields an output
-    template <class PH>
-    __device__ __forceinline__ void push_full(const V4<R> &v, const PH &ph, R lam, V4<R> &cell,
-                                              V4<R> &D) {
+    template <class PH, class R>
+    __device__ __forceinline__ void push_full(const V &v, const PH &ph, R lam, V &cell, V &D) {
         w0 = w1; w1 = w2; w2 = v;
-        V4<R> ul, ur;
+        V ul, ur;
         ph.faces(w0, w1, w2, lam, ul, ur);
-        const V4<R> F = ph.musta(urp, ul, lam);
+        const V F = ph.musta(urp, ul, lam);
         D = vsub(F, fp);
         cell = w0;
         fp = F;
@@ -765,22 +819,26 @@ struct Stage {
 };
 
 // Where a thread's pencil lives: field q of cell j is base[fo[q] + j * stride],
-// with fo = (0, M_axis, M_t1, M_t2) field offsets in elements.
-template <class R>
+// with fo = (0, M_axis, M_t1, M_t2[, R]) field offsets in elements.
+template <class R, bool CH = false>
 struct Pencil {
     const R *in;
     R *out;
     int fo1, fo2, fo3;    // offsets of the three momentum slots (E is at 0)
+    int fo4;              // offset of the charge (CH)
     int stride;
     int N;
 
-    __device__ __forceinline__ V4<R> load(int j) const {
+    __device__ __forceinline__ VS<R, CH> load(int j) const {
         const R *p = in + j * stride;
-        return v4<R>(__ldg(p), __ldg(p + fo1), __ldg(p + fo2), __ldg(p + fo3));
+        const V4<R> v = v4<R>(__ldg(p), __ldg(p + fo1), __ldg(p + fo2), __ldg(p + fo3));
+        if constexpr (CH) return with_r(v, __ldg(p + fo4));
+        else return v;
     }
-    __device__ __forceinline__ void store(int j, const V4<R> &v) const {
+    __device__ __forceinline__ void store(int j, const VS<R, CH> &v) const {
         R *p = out + j * stride;
         p[0] = v.e; p[fo1] = v.n; p[fo2] = v.t1; p[fo3] = v.t2;
+        if constexpr (CH) p[fo4] = v.r;
     }
 };
 
@@ -796,23 +854,23 @@ __device__ __forceinline__ int wrap_index(int j, int N, int bc) {
 // With outflow ends, ghost positions p < 0 take the output of cell 0 and
 // p >= N the output of cell N-1 (saved in `last`), as the ghost fill of a
 // stage input does.
-template <class R, int DEPTH>
-__device__ __forceinline__ V4<R> pick(const V4<R> (&q)[DEPTH], int newest, int p, int N, int bc,
-                                      const V4<R> &last) {
+template <class V, int DEPTH>
+__device__ __forceinline__ V pick(const V (&q)[DEPTH], int newest, int p, int N, int bc,
+                                  const V &last) {
     if (bc == BC_OUTFLOW) {
         if (p >= N) return last;
         if (p < 0) p = 0;
     }
     const int age = newest - p;
-    V4<R> x = q[DEPTH - 1];
+    V x = q[DEPTH - 1];
 #pragma unroll
     for (int a = 0; a < DEPTH - 1; ++a)
         if (age == a) x = q[a];
     return x;
 }
 
-template <class R, int DEPTH>
-__device__ __forceinline__ void shift_in(V4<R> (&q)[DEPTH], const V4<R> &v) {
+template <class V, int DEPTH>
+__device__ __forceinline__ void shift_in(V (&q)[DEPTH], const V &v) {
 #pragma unroll
     for (int a = DEPTH - 1; a > 0; --a) q[a] = q[a - 1];
     q[0] = v;
@@ -836,8 +894,9 @@ struct RateAcc {
 };
 
 template <class R, int RK, bool RATE, class PH>
-__device__ __forceinline__ void march(const PH &ph, const Pencil<R> &P, int s0, int L, int s_end,
-                                      int bc, R lam, bool do_store, RateAcc<R> &ra) {
+__device__ __forceinline__ void march(const PH &ph, const Pencil<R, PH::kCharge> &P, int s0, int L,
+                                      int s_end, int bc, R lam, bool do_store, RateAcc<R> &ra) {
+    using V = typename PH::V;
     const int N = P.N;
     if (!positive(lam)) {   // finished event: copy through
         if (do_store)
@@ -846,16 +905,16 @@ __device__ __forceinline__ void march(const PH &ph, const Pencil<R> &P, int s0, 
     }
     const bool rate_on = RATE && positive(ra.ih_n);
     const R third = R(1.0 / 3.0), two3 = R(2.0 / 3.0), q3 = R(0.75), q1c = R(0.25), half = R(0.5);
-    Stage<R> st1, st2, st3;
+    Stage<V> st1, st2, st3;
     st1.n = 0; st2.n = 0; st3.n = 0;
-    V4<R> cell, D;
+    V cell, D;
     constexpr int H = 2 * RK;                 // halo of the stage-1 input
     constexpr int T_EXTRA = RK == 1 ? 4 : (RK == 2 ? 10 : 16);
     const int T = L + T_EXTRA;
     const int js = s0 - H;
-    V4<R> qa[3];
-    V4<R> lastA = v4<R>(0, 0, 0, 0), lastB = lastA;
-    V4<R> nxt = P.load(wrap_index(js, N, bc));
+    V qa[3];
+    V lastA = vzero<V>(), lastB = lastA;
+    V nxt = P.load(wrap_index(js, N, bc));
     if constexpr (RK == 2) {
         // One loop body for every step: both engines push unchecked from t = 0
         // on zero-initialised windows.  Their outputs before the windows fill
@@ -863,7 +922,7 @@ __device__ __forceinline__ void march(const PH &ph, const Pencil<R> &P, int s0, 
         // (zero states take the vacuum branch, so they stay finite); every
         // stored cell is computed by the same instructions whatever the
         // segment layout, so results do not depend on the launch shape.
-        const V4<R> zero = v4<R>(R(0), R(0), R(0), R(0));
+        const V zero = vzero<V>();
         st1.w0 = st1.w1 = st1.w2 = st1.urp = st1.fp = zero;
         st2.w0 = st2.w1 = st2.w2 = st2.urp = st2.fp = zero;
         qa[0] = qa[1] = qa[2] = zero;
@@ -872,11 +931,11 @@ __device__ __forceinline__ void march(const PH &ph, const Pencil<R> &P, int s0, 
         // the cell reloaded for the RK combination, one step ahead like the input
         int on = wrap_index(s0 - 9, N, bc);
         int oc = s0 - 9;
-        V4<R> U0n = P.load(wrap_index(s0 - 10, N, bc));
+        V U0n = P.load(wrap_index(s0 - 10, N, bc));
 #pragma unroll 1
         for (int t = 0; t < T; ++t) {
-            const V4<R> V = nxt;
-            const V4<R> U0 = U0n;
+            const V Vc = nxt;
+            const V U0 = U0n;
             if (t + 1 < T) {
                 nxt = P.load(jn);
                 U0n = P.load(on);
@@ -885,25 +944,28 @@ __device__ __forceinline__ void march(const PH &ph, const Pencil<R> &P, int s0, 
             jn = (bc == BC_OUTFLOW) ? min(max(jc, 0), N - 1) : (jn + 1 == N ? 0 : jn + 1);
             ++oc;
             on = (bc == BC_OUTFLOW) ? min(max(oc, 0), N - 1) : (on + 1 == N ? 0 : on + 1);
-            st1.push_full(V, ph, lam, cell, D);
+            st1.push_full(Vc, ph, lam, cell, D);
             const int i = js + t - 2;                 // stage-1 output cell
-            const V4<R> X = vfma<R>(-lam, D, cell);   // U1 = U + dt L(U)
+            const V X = vfma<R>(-lam, D, cell);   // U1 = U + dt L(U)
             shift_in(qa, X);
             if (i == N - 1) lastA = X;
-            const V4<R> Y = pick(qa, i, t + s0 - 8, N, bc, lastA);
-            V4<R> c, Dl;
+            const V Y = pick(qa, i, t + s0 - 8, N, bc, lastA);
+            V c, Dl;
             st2.push_full(Y, ph, lam, c, Dl);
             const int o = t + s0 - 10;                // finished cell
             // Eq. 6: U^{n+1} = 1/2 (U + U1 + dt L(U1))
-            const V4<R> r = vmul<R>(half, vfma<R>(-lam, Dl, vadd(U0, c)));
+            const V r = vmul<R>(half, vfma<R>(-lam, Dl, vadd(U0, c)));
             const bool keep = do_store && o >= s0 && o < s_end;
             if constexpr (RATE) {
                 if (rate_on && keep) {
-                    const R rr = ph.rate(r, ra.ih_n, ra.ih_t1, ra.ih_t2, ra.iso);
+                    const R rr = ph.rate(head(r), ra.ih_n, ra.ih_t1, ra.ih_t2, ra.iso);
                     ra.m = (rr > ra.m || rr != rr) ? rr : ra.m;
                 }
             }
             if (keep) P.store(o, r);
+            // the steps before the first finished cell run on zero-filled
+            // windows: what they met is not a state of the grid
+            if (t < 10) ph.flags_ = 0;
         }
         return;
     }
@@ -912,21 +974,21 @@ __device__ __forceinline__ void march(const PH &ph, const Pencil<R> &P, int s0, 
         // zero-initialised windows; each stage reads the previous stage's
         // output two cells behind its newest (the 2 ghost cells of a stage).
         // Stage 1 outputs cell t+s0-8, stage 2 cell t+s0-12, stage 3 t+s0-16.
-        const V4<R> zero = v4<R>(R(0), R(0), R(0), R(0));
+        const V zero = vzero<V>();
         st1.w0 = st1.w1 = st1.w2 = st1.urp = st1.fp = zero;
         st2.w0 = st2.w1 = st2.w2 = st2.urp = st2.fp = zero;
         st3.w0 = st3.w1 = st3.w2 = st3.urp = st3.fp = zero;
-        V4<R> q1[3] = {zero, zero, zero}, q2[3] = {zero, zero, zero};
+        V q1[3] = {zero, zero, zero}, q2[3] = {zero, zero, zero};
         const int T3 = L + 16;
         int jn = wrap_index(js + 1, N, bc), jc = js + 1;
         // U^n of the stage-2 and stage-3 output cells, one step ahead
         int an = wrap_index(s0 - 11, N, bc), ac = s0 - 11;
         int bn = wrap_index(s0 - 15, N, bc), bcn = s0 - 15;
-        V4<R> Ua = P.load(wrap_index(s0 - 12, N, bc));
-        V4<R> Ub = P.load(wrap_index(s0 - 16, N, bc));
+        V Ua = P.load(wrap_index(s0 - 12, N, bc));
+        V Ub = P.load(wrap_index(s0 - 16, N, bc));
 #pragma unroll 1
         for (int t = 0; t < T3; ++t) {
-            const V4<R> V = nxt, U0 = Ua, U00 = Ub;
+            const V Vc = nxt, U0 = Ua, U00 = Ub;
             if (t + 1 < T3) {
                 nxt = P.load(jn);
                 Ua = P.load(an);
@@ -942,31 +1004,32 @@ __device__ __forceinline__ void march(const PH &ph, const Pencil<R> &P, int s0, 
                 an = an + 1 == N ? 0 : an + 1;
                 bn = bn + 1 == N ? 0 : bn + 1;
             }
-            st1.push_full(V, ph, lam, cell, D);
+            st1.push_full(Vc, ph, lam, cell, D);
             const int i = t + s0 - 8;                  // stage-1 output cell
-            const V4<R> X = vfma<R>(-lam, D, cell);    // U1 = U + dt L(U)
+            const V X = vfma<R>(-lam, D, cell);    // U1 = U + dt L(U)
             shift_in(q1, X);
             if (i == N - 1) lastA = X;
-            V4<R> c2, D2;
+            V c2, D2;
             st2.push_full(pick(q1, i, t + s0 - 10, N, bc, lastA), ph, lam, c2, D2);
             const int i2 = t + s0 - 12;                // stage-2 output cell
             // U2 = 3/4 U + 1/4 (U1 + dt L(U1))
-            const V4<R> Z = vfma<R>(q3, U0, vmul<R>(q1c, vfma<R>(-lam, D2, c2)));
+            const V Z = vfma<R>(q3, U0, vmul<R>(q1c, vfma<R>(-lam, D2, c2)));
             shift_in(q2, Z);
             if (i2 == N - 1) lastB = Z;
-            V4<R> c3, D3;
+            V c3, D3;
             st3.push_full(pick(q2, i2, t + s0 - 14, N, bc, lastB), ph, lam, c3, D3);
             const int o = t + s0 - 16;                 // finished cell
             // U^{n+1} = 1/3 U + 2/3 (U2 + dt L(U2))
-            const V4<R> r = vfma<R>(third, U00, vmul<R>(two3, vfma<R>(-lam, D3, c3)));
+            const V r = vfma<R>(third, U00, vmul<R>(two3, vfma<R>(-lam, D3, c3)));
             const bool keep = do_store && o >= s0 && o < s_end;
             if constexpr (RATE) {
                 if (rate_on && keep) {
-                    const R rr = ph.rate(r, ra.ih_n, ra.ih_t1, ra.ih_t2, ra.iso);
+                    const R rr = ph.rate(head(r), ra.ih_n, ra.ih_t1, ra.ih_t2, ra.iso);
                     ra.m = (rr > ra.m || rr != rr) ? rr : ra.m;
                 }
             }
             if (keep) P.store(o, r);
+            if (t < 16) ph.flags_ = 0;   // zero-filled windows (as for RK2)
         }
         return;
     }
@@ -974,14 +1037,14 @@ __device__ __forceinline__ void march(const PH &ph, const Pencil<R> &P, int s0, 
         // RK1 (plain MUSCL-Hancock with MUSTA-FORCE fluxes)
 #pragma unroll 1
         for (int t = 0; t < T; ++t) {
-            const V4<R> V = nxt;
+            const V Vc = nxt;
             if (t + 1 < T) nxt = P.load(wrap_index(js + t + 1, N, bc));
-            if (!st1.push(V, ph, lam, cell, D)) continue;
+            if (!st1.push(Vc, ph, lam, cell, D)) continue;
             const int i = js + t - 2;   // output cell
-            const V4<R> X = vfma<R>(-lam, D, cell);   // U + dt L(U)
+            const V X = vfma<R>(-lam, D, cell);   // U + dt L(U)
             if constexpr (RATE) {
                 if (rate_on) {
-                    const R rr = ph.rate(X, ra.ih_n, ra.ih_t1, ra.ih_t2, ra.iso);
+                    const R rr = ph.rate(head(X), ra.ih_n, ra.ih_t1, ra.ih_t2, ra.iso);
                     if (do_store && i < s_end) ra.m = (rr > ra.m || rr != rr) ? rr : ra.m;
                 }
             }
@@ -1014,16 +1077,30 @@ constexpr int kFlushUnroll = 8;
 constexpr int XO = 8;         // output ring: steps per row
 constexpr int XOS = XO + 1;
 
-template <class R>
+// fields of the rings: 4, or 5 with the charge
+template <class R, bool CH = false>
 __host__ __device__ constexpr int xstage_floats_per_warp() {
-    return 4 * 32 * XRS + 4 * 32 * XOS;
+    return (CH ? 5 : 4) * 32 * (XRS + XOS);
 }
 
+// HY_XFILL_L2 (build-time, 0/64/128/256): L2 prefetch size hint of the row copies
+#ifndef HY_XFILL_L2
+#define HY_XFILL_L2 0
+#endif
+#if HY_XFILL_L2 == 64
+#define HY_XFILL_HINT ".L2::64B"
+#elif HY_XFILL_L2 == 128
+#define HY_XFILL_HINT ".L2::128B"
+#elif HY_XFILL_L2 == 256
+#define HY_XFILL_HINT ".L2::256B"
+#else
+#define HY_XFILL_HINT ""
+#endif
 template <class R>
 __device__ __forceinline__ void cp_async_elem(R *dst, const R *src) {
     const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
-    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(d), "l"(src),
-                 "n"(int(sizeof(R))) : "memory");
+    asm volatile("cp.async.ca.shared.global" HY_XFILL_HINT " [%0], [%1], %2;\n" ::"r"(d),
+                 "l"(src), "n"(int(sizeof(R))) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() {
     asm volatile("cp.async.commit_group;\n" ::: "memory");
@@ -1032,13 +1109,15 @@ __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 }
 
-template <class R>
+template <class R, bool CH = false>
 struct XStage {
-    R *ring;            // [4][32][XRS]
-    R *oring;           // [4][32][XOS]
+    using V = VS<R, CH>;
+    R *ring;            // [NQ][32][XRS]
+    R *oring;           // [NQ][32][XOS]
     const R *in;        // event base (field 0, cell 0) of the input state
     R *out;
     int fo1, fo2, fo3;  // field offsets (E at 0)
+    int fo4;            // charge offset (CH)
     int N, bc, lane;
     int js;             // this lane's position at step 0
     int rowN;           // this lane's row start: row (pencil) index * N
@@ -1063,6 +1142,7 @@ struct XStage {
                 cp_async_elem(q + 32 * XRS, p + fo1);
                 cp_async_elem(q + 2 * 32 * XRS, p + fo2);
                 cp_async_elem(q + 3 * 32 * XRS, p + fo3);
+                if constexpr (CH) cp_async_elem(q + 4 * 32 * XRS, p + fo4);
             }
             cp_async_commit();
             return;
@@ -1080,16 +1160,20 @@ struct XStage {
             cp_async_elem(q + 32 * XRS, p + fo1);
             cp_async_elem(q + 2 * 32 * XRS, p + fo2);
             cp_async_elem(q + 3 * 32 * XRS, p + fo3);
+            if constexpr (CH) cp_async_elem(q + 4 * 32 * XRS, p + fo4);
         }
         cp_async_commit();
     }
-    __device__ __forceinline__ V4<R> get(int t) const {
+    __device__ __forceinline__ V get(int t) const {
         const R *q = ring + lane * XRS + (t & (XR - 1));
-        return v4<R>(q[0], q[32 * XRS], q[2 * 32 * XRS], q[3 * 32 * XRS]);
+        const V4<R> v = v4<R>(q[0], q[32 * XRS], q[2 * 32 * XRS], q[3 * 32 * XRS]);
+        if constexpr (CH) return with_r(v, q[4 * 32 * XRS]);
+        else return v;
     }
-    __device__ __forceinline__ void put(int t, const V4<R> &v) {
+    __device__ __forceinline__ void put(int t, const V &v) {
         R *q = oring + lane * XOS + (t & (XO - 1));
         q[0] = v.e; q[32 * XOS] = v.n; q[2 * 32 * XOS] = v.t1; q[3 * 32 * XOS] = v.t2;
+        if constexpr (CH) q[4 * 32 * XOS] = v.r;
     }
     // write the results of steps t1 - 7 .. t1 (position js + step - 6) whose
     // keep bits (bit step & 7, per row) are set; with RATE also fold their CFL
@@ -1116,6 +1200,7 @@ struct XStage {
                     p[fo1] = v.n;
                     p[fo2] = v.t1;
                     p[fo3] = v.t2;
+                    if constexpr (CH) p[fo4] = q[4 * 32 * XOS];
                     if (RATE && rate_on) {
                         const R rr = ph.rate(v, ra.ih_n, ra.ih_t1, ra.ih_t2, ra.iso);
                         ra.m = (rr > ra.m || rr != rr) ? rr : ra.m;
@@ -1138,6 +1223,7 @@ struct XStage {
                 p[fo1] = v.n;
                 p[fo2] = v.t1;
                 p[fo3] = v.t2;
+                if constexpr (CH) p[fo4] = q[4 * 32 * XOS];
                 if (RATE && rate_on) {
                     const R rr = ph.rate(v, ra.ih_n, ra.ih_t1, ra.ih_t2, ra.iso);
                     ra.m = (rr > ra.m || rr != rr) ? rr : ra.m;
@@ -1151,8 +1237,9 @@ struct XStage {
 // arithmetic, schedule and zero start as march() (Eq. 6), so stored cells
 // are bit-identical to it.  The whole warp must call it together.
 template <class R, bool RATE, class PH>
-__device__ __forceinline__ void march_x_rk2(const PH &ph, XStage<R> &X, int s0, int L, int s_end,
-                                            R lam, bool do_store, RateAcc<R> &ra) {
+__device__ __forceinline__ void march_x_rk2(const PH &ph, XStage<R, PH::kCharge> &X, int s0, int L,
+                                            int s_end, R lam, bool do_store, RateAcc<R> &ra) {
+    using V = typename PH::V;
     const int N = X.N, bc = X.bc;
     const bool rate_on = RATE && ra.ih_n > R(0);
     const R half = R(0.5);
@@ -1168,12 +1255,12 @@ __device__ __forceinline__ void march_x_rk2(const PH &ph, XStage<R> &X, int s0, 
     const int phi = (6 - js0) & 7;
     const int psi = (13 - js0) & 7;
     const int tf = phi == 0 ? 8 : phi;   // first fill step
-    Stage<R> st1, st2;
-    const V4<R> zero = v4<R>(R(0), R(0), R(0), R(0));
+    Stage<V> st1, st2;
+    const V zero = vzero<V>();
     st1.w0 = st1.w1 = st1.w2 = st1.urp = st1.fp = zero;
     st2.w0 = st2.w1 = st2.w2 = st2.urp = st2.fp = zero;
-    V4<R> qa[3] = {zero, zero, zero};
-    V4<R> lastA = zero, cell, D;
+    V qa[3] = {zero, zero, zero};
+    V lastA = zero, cell, D;
     __syncwarp();
     X.fill(tf - 14);
     X.fill(tf - 6);   // steps [tf - 14, tf + 2) cover [-6, tf + 2)
@@ -1182,27 +1269,28 @@ __device__ __forceinline__ void march_x_rk2(const PH &ph, XStage<R> &X, int s0, 
     unsigned keep = 0u;
     // the ring reads of a step (its input and the RK reload 6 steps behind)
     // are made at the end of the step before, so their latency overlaps it
-    V4<R> Vn = X.get(0), U0n = X.get(-6);
+    V Vn = X.get(0), U0n = X.get(-6);
 #pragma unroll 1
     for (int t = 0; t < T; ++t) {
         if (t >= tf && ((t - phi) & 7) == 0) {   // slots of steps < t - 6 are free
             __syncwarp();
             X.fill(t + 2);
         }
-        const V4<R> V = Vn, U0 = U0n;
-        st1.push_full(V, ph, lam, cell, D);
+        const V Vc = Vn, U0 = U0n;
+        st1.push_full(Vc, ph, lam, cell, D);
         const int i = js + t - 2;
-        const V4<R> Xv = vfma<R>(-lam, D, cell);   // U1 = U + dt L(U)
+        const V Xv = vfma<R>(-lam, D, cell);   // U1 = U + dt L(U)
         shift_in(qa, Xv);
         if (i == N - 1) lastA = Xv;
-        const V4<R> Y = pick(qa, i, t + s0 - 8, N, bc, lastA);
-        V4<R> c, Dl;
+        const V Y = pick(qa, i, t + s0 - 8, N, bc, lastA);
+        V c, Dl;
         st2.push_full(Y, ph, lam, c, Dl);
         const int o = t + s0 - 10;
-        const V4<R> r = vmul<R>(half, vfma<R>(-lam, Dl, vadd(U0, c)));
+        const V r = vmul<R>(half, vfma<R>(-lam, Dl, vadd(U0, c)));
         const bool kp = do_store && o >= s0 && o < s_end;
         X.put(t, r);
         keep |= (kp ? 1u : 0u) << (t & 7);
+        if (t < 10) ph.flags_ = 0;   // zero-filled windows (as in march)
         if (((t - psi) & 7) == 0 || t == T - 1) {
             __syncwarp();
             X.template flush<RATE>(t, keep, ph, ra, rate_on);

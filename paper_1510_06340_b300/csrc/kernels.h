@@ -18,6 +18,7 @@ struct SweepLaunch {
     Scheme sc;
     int rk;
     int threads, blocks;
+    int charge = 0;          // 1: the state carries the conserved charge as field 4
     int *counter;            // non-null: persistent grid pulling items from this counter
     EventClock *rate_clk;    // non-null: accumulate the CFL rate of the output state here
     int sms;
@@ -66,10 +67,14 @@ struct CellLaunch {
     int rate_sum = 0;     // launch_rate: sum over axes (unsplit scheme) instead of max
     long long jet_cells = 0;   // launch_jet: cells of the largest box around a jet
     int nevents = 0;
+    int nq = 4;           // conserved fields per cell: 4, or 5 with the charge
 };
 
+// with c.nq = 5 also R = n gamma from n (null: R = 0)
 cudaError_t launch_prim2cons(const CellLaunch &c, const void *e, const void *vx, const void *vy,
-                             const void *vz, void *U);
+                             const void *vz, const void *n, void *U);
+// n = R / gamma per cell (outputs indexed like launch_cons2prim's)
+cudaError_t launch_charge_density(const CellLaunch &c, const void *U, void *n);
 cudaError_t launch_cons2prim(const CellLaunch &c, const void *U, void *e, void *vx, void *vy,
                              void *vz);
 // max over cells of speed/dx, maximised (or with rate_sum summed) over the swept
@@ -78,10 +83,11 @@ cudaError_t launch_rate(const CellLaunch &c, const void *U, EventClock *clk, dou
 // per-event dt from rate_bits (resets it), t_step = t, t += dt
 cudaError_t launch_dt(EventClock *clk, const double *cfl_fixed, int nevents, cudaStream_t s);
 cudaError_t launch_jet(const CellLaunch &c, void *U, const EventClock *clk);
-// FP64 partial sums per work item: partial[item][4]
+// FP64 partial sums per work item: partial[item][nq]; per event out[event][nq]
 cudaError_t launch_sums(const CellLaunch &c, const void *U, double *partial);
 cudaError_t launch_sums_final(const WorkItem *items, int nitems, const double *partial,
-                              const EventGeo *ev, double *out, int nevents, cudaStream_t s);
+                              const EventGeo *ev, double *out, int nevents, int nq,
+                              cudaStream_t s);
 cudaError_t launch_hotspots(const CellLaunch &c, const double *spots, int nspots, double sigma,
                             double e_bg, void *U);
 cudaError_t launch_finite(const CellLaunch &c, const void *U, EventClock *clk);

@@ -22,12 +22,13 @@ namespace hy {
 #endif
 
 // XS: RK2 x sweep through the shared-memory row rings (march_x_rk2)
-template <class R, int PREC, int EOSK, int RK, int LIM, bool COUNT, bool RATE, bool XS>
+// CH: the conserved charge is carried as a fifth field (state [5][...])
+template <class R, int PREC, int EOSK, int RK, int LIM, bool COUNT, bool RATE, bool XS, bool CH>
 __device__ __forceinline__ void
 sweep_body(const R *__restrict__ in, R *__restrict__ out, const EventGeo *__restrict__ ev,
            const WorkItem *__restrict__ items, int nitems, int axis, double frac,
            const EventClock *__restrict__ clk, Scheme sc, int *counter, EventClock *rate_clk) {
-    Physics<R, PREC, EOSK, LIM, COUNT, RK != 3> ph;
+    Physics<R, PREC, EOSK, LIM, COUNT, RK != 3, CH> ph;
     ph.sc = sc;
     __shared__ int s_item;
     __shared__ R s_red[8];
@@ -69,12 +70,13 @@ sweep_body(const R *__restrict__ in, R *__restrict__ out, const EventGeo *__rest
             stride = (long long)nx * ny;
         }
         const int ta = axis == 0 ? 2 : 1, tb = axis == 2 ? 2 : 3;
-        Pencil<R> Pc;
+        Pencil<R, CH> Pc;
         Pc.in = in + g.off + base;
         Pc.out = out + g.off + base;
         Pc.fo1 = int((1 + axis) * cells);
         Pc.fo2 = int(ta * cells);
         Pc.fo3 = int(tb * cells);
+        Pc.fo4 = int(4 * cells);
         Pc.stride = int(stride);
         Pc.N = N;
         const R lam = R(frac * clk[w.event].dt / g.h[axis]);
@@ -96,13 +98,13 @@ sweep_body(const R *__restrict__ in, R *__restrict__ out, const EventGeo *__rest
         if (XS) {   // rows through the warp's shared-memory rings
             extern __shared__ __align__(16) unsigned char xs_raw[];
             R *base = reinterpret_cast<R *>(xs_raw) +
-                      (threadIdx.x >> 5) * xstage_floats_per_warp<R>();
-            XStage<R> X;
+                      (threadIdx.x >> 5) * xstage_floats_per_warp<R, CH>();
+            XStage<R, CH> X;
             X.ring = base;
-            X.oring = base + 4 * 32 * XRS;
+            X.oring = base + (CH ? 5 : 4) * 32 * XRS;
             X.in = in + g.off;
             X.out = out + g.off;
-            X.fo1 = Pc.fo1; X.fo2 = Pc.fo2; X.fo3 = Pc.fo3;
+            X.fo1 = Pc.fo1; X.fo2 = Pc.fo2; X.fo3 = Pc.fo3; X.fo4 = Pc.fo4;
             X.N = N;
             X.bc = g.bc[0];
             X.lane = threadIdx.x & 31;
@@ -144,9 +146,9 @@ sweep_body(const R *__restrict__ in, R *__restrict__ out, const EventGeo *__rest
         const EventClock *__restrict__ clk, Scheme sc, int *counter, EventClock *rate_clk
 #define HY_SWEEP_ARGS in, out, ev, items, nitems, axis, frac, clk, sc, counter, rate_clk
 
-template <class R, int PREC, int EOSK, int RK, int LIM, bool COUNT, bool RATE, bool XS>
+template <class R, int PREC, int EOSK, int RK, int LIM, bool COUNT, bool RATE, bool XS, bool CH>
 __global__ void HY_SWEEP_BOUNDS k_sweep(HY_SWEEP_PARAMS) {
-    sweep_body<R, PREC, EOSK, RK, LIM, COUNT, RATE, XS>(HY_SWEEP_ARGS);
+    sweep_body<R, PREC, EOSK, RK, LIM, COUNT, RATE, XS, CH>(HY_SWEEP_ARGS);
 }
 
 // The FP32 conformal RK3 sweep (three stages chained in registers) wants a
@@ -156,35 +158,36 @@ __global__ void HY_SWEEP_BOUNDS k_sweep(HY_SWEEP_PARAMS) {
 #ifndef HY_RK3_MAXNREG
 #define HY_RK3_MAXNREG 168
 #endif
-template <class R, int PREC, int EOSK, int RK, int LIM, bool COUNT, bool RATE, bool XS>
+template <class R, int PREC, int EOSK, int RK, int LIM, bool COUNT, bool RATE, bool XS, bool CH>
 __global__ void __maxnreg__(HY_RK3_MAXNREG) k_sweep_rk3(HY_SWEEP_PARAMS) {
-    sweep_body<R, PREC, EOSK, RK, LIM, COUNT, RATE, XS>(HY_SWEEP_ARGS);
+    sweep_body<R, PREC, EOSK, RK, LIM, COUNT, RATE, XS, CH>(HY_SWEEP_ARGS);
 }
 #undef HY_SWEEP_PARAMS
 #undef HY_SWEEP_ARGS
 
-template <class R, int PREC, int EOSK, int RK, int LIM, bool COUNT, bool RATE, bool XS>
+template <class R, int PREC, int EOSK, int RK, int LIM, bool COUNT, bool RATE, bool XS, bool CH>
 constexpr auto sweep_kernel() {
-    if constexpr (RK == 3 && PREC == PREC_F32 && EOSK == EOS_CONFORMAL && !COUNT)
-        return &k_sweep_rk3<R, PREC, EOSK, RK, LIM, COUNT, RATE, XS>;
+    if constexpr (RK == 3 && PREC == PREC_F32 && EOSK == EOS_CONFORMAL && !COUNT && !CH)
+        return &k_sweep_rk3<R, PREC, EOSK, RK, LIM, COUNT, RATE, XS, CH>;
     else
-        return &k_sweep<R, PREC, EOSK, RK, LIM, COUNT, RATE, XS>;
+        return &k_sweep<R, PREC, EOSK, RK, LIM, COUNT, RATE, XS, CH>;
 }
 
 template <class R, int PREC>
 cudaError_t launch_sweep_prec(const SweepLaunch &a) {
     const R *in = static_cast<const R *>(a.in);
     R *out = static_cast<R *>(a.out);
-#define HY_SWEEP(EOSK, RK, LIM, COUNT, RATE)                                                 \
+#define HY_SWEEP(EOSK, RK, LIM, COUNT, RATE) HY_SWEEP_CH(EOSK, RK, LIM, COUNT, RATE, false)
+#define HY_SWEEP_CH(EOSK, RK, LIM, COUNT, RATE, CH)                                          \
     {                                                                                       \
-        if (RK == 2 && a.axis == 0) HY_SWEEP_XS(EOSK, RK, LIM, COUNT, RATE, RK == 2)         \
-        else HY_SWEEP_XS(EOSK, RK, LIM, COUNT, RATE, false)                                 \
+        if (RK == 2 && a.axis == 0) HY_SWEEP_XS(EOSK, RK, LIM, COUNT, RATE, RK == 2, CH)     \
+        else HY_SWEEP_XS(EOSK, RK, LIM, COUNT, RATE, false, CH)                             \
     }
-#define HY_SWEEP_XS(EOSK, RK, LIM, COUNT, RATE, XS)                                          \
+#define HY_SWEEP_XS(EOSK, RK, LIM, COUNT, RATE, XS, CH)                                      \
     {                                                                                       \
-        auto kfn = sweep_kernel<R, PREC, EOSK, RK, LIM, COUNT, RATE, XS>();                 \
+        auto kfn = sweep_kernel<R, PREC, EOSK, RK, LIM, COUNT, RATE, XS, CH>();             \
         const size_t smem = XS                                                              \
-            ? size_t(a.threads / 32) * xstage_floats_per_warp<R>() * sizeof(R) : 0;          \
+            ? size_t(a.threads / 32) * xstage_floats_per_warp<R, CH>() * sizeof(R) : 0;      \
         if (smem > 0) {   /* opt in once per device, for 256 threads */                 \
             static std::atomic<unsigned long long> opted{0};                                \
             int dev_ = 0;                                                                   \
@@ -193,7 +196,7 @@ cudaError_t launch_sweep_prec(const SweepLaunch &a) {
             const unsigned long long bit_ = 1ull << (dev_ & 63);                            \
             if (!(opted.load() & bit_)) {                                                   \
                 e_ = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                          int(8 * xstage_floats_per_warp<R>() * sizeof(R)));\
+                                          int(8 * xstage_floats_per_warp<R, CH>() * sizeof(R)));\
                 if (e_ != cudaSuccess) return e_;                                           \
                 opted.fetch_or(bit_);                                                       \
             }                                                                               \
@@ -212,6 +215,20 @@ cudaError_t launch_sweep_prec(const SweepLaunch &a) {
         kfn<<<blocks, a.threads, smem, a.stream>>>(in, out, a.ev, a.items, a.nitems, a.axis, \
                                                 a.frac, a.clk, a.sc, a.counter, a.rate_clk); \
         return cudaGetLastError();                                                          \
+    }
+    // the conserved charge as a fifth field: runtime-limiter kernels with
+    // counters compiled in (the four-field kernels below are untouched)
+    if (a.charge) {
+        if (a.sc.eos_kind == EOS_CONFORMAL) {
+            if (a.rk == 1) HY_SWEEP_CH(EOS_CONFORMAL, 1, -1, true, true, true)
+            if (a.rk == 2) HY_SWEEP_CH(EOS_CONFORMAL, 2, -1, true, true, true)
+            if (a.rk == 3) HY_SWEEP_CH(EOS_CONFORMAL, 3, -1, true, true, true)
+        } else if (a.sc.seed != SEED_MLP) {
+            if (a.rk == 1) HY_SWEEP_CH(EOS_TABLE, 1, -1, true, true, true)
+            if (a.rk == 2) HY_SWEEP_CH(EOS_TABLE, 2, -1, true, true, true)
+            if (a.rk == 3) HY_SWEEP_CH(EOS_TABLE, 3, -1, true, true, true)
+        }
+        return cudaErrorInvalidValue;
     }
     // specialised kernels (limiter fixed at compile time, no counters) for the
     // conformal RK2 scheme; everything else takes the runtime-limiter kernel
@@ -267,6 +284,7 @@ cudaError_t launch_sweep_prec(const SweepLaunch &a) {
         if (a.rk == 3) HY_SWEEP(EOS_TABLE, 3, -1, true, true)
     }
 #undef HY_SWEEP
+#undef HY_SWEEP_CH
 #undef HY_SWEEP_XS
     return cudaErrorInvalidValue;
 }

@@ -37,7 +37,7 @@ class GridT(C.Structure):
                 ("x0", C.c_double), ("y0", C.c_double), ("z0", C.c_double),
                 ("bc", C.c_int * 3), ("prec", C.c_int), ("rk_order", C.c_int),
                 ("hancock", C.c_int), ("cfl", C.c_double), ("fixed_dt", C.c_double),
-                ("alpha", C.c_double), ("unsplit", C.c_int)]
+                ("alpha", C.c_double), ("unsplit", C.c_int), ("charge", C.c_int)]
 
 
 class EosT(C.Structure):
@@ -66,6 +66,11 @@ def lib():
             "hydro_set_stream": [H, vp],
             "hydro_set_primitives": [H, vp, vp, vp, vp, i],
             "hydro_set_conserved": [H, vp, i],
+            "hydro_set_primitives_charged": [H, vp, vp, vp, vp, vp, i],
+            "hydro_get_charge_density": [H, vp, i],
+            "hydro_charge_sum": [H, dp],
+            "hydro_batch_set_primitives_charged": [H, i, vp, vp, vp, vp, vp, i],
+            "hydro_batch_charge_sums": [H, dp],
             "hydro_get_conserved": [H, vp, i],
             "hydro_get_primitives": [H, vp, vp, vp, vp, i],
             "hydro_init_hotspots": [H, dp, i, d, d],
@@ -192,7 +197,7 @@ def _stream_ptr(stream):
 
 def make_grid(nx, ny=1, nz=1, dx=1.0, dy=None, dz=None, x0=0.0, y0=0.0, z0=0.0,
               bc="periodic", prec="fp64", rk_order=2, hancock=1, cfl=0.4, fixed_dt=0.0,
-              alpha=None, unsplit=False):
+              alpha=None, unsplit=False, charge=False):
     """hydro_grid_t; alpha defaults to 1 for split sweeps and 3 for the
     unsplit scheme (the paper's 3-D value)."""
     g = GridT()
@@ -210,6 +215,7 @@ def make_grid(nx, ny=1, nz=1, dx=1.0, dy=None, dz=None, x0=0.0, y0=0.0, z0=0.0,
     g.cfl, g.fixed_dt = cfl, fixed_dt
     g.alpha = (3.0 if unsplit else 1.0) if alpha is None else alpha
     g.unsplit = 1 if unsplit else 0
+    g.charge = 1 if charge else 0
     return g
 
 
@@ -261,7 +267,8 @@ class Hydro(_Base):
         _check(lib().hydro_create(C.byref(grid), C.byref(eos_t), lim, stages, C.byref(h)))
         self.h = h
         self._dtype = np.float64 if grid.prec == 0 else np.float32
-        self.shape = (4, grid.nz, grid.ny, grid.nx)
+        self.nq = 5 if grid.charge else 4
+        self.shape = (self.nq, grid.nz, grid.ny, grid.nx)
         if stream is not None:
             self.set_stream(stream)
 
@@ -279,20 +286,39 @@ class Hydro(_Base):
     def cells(self):
         return self.grid.nx * self.grid.ny * self.grid.nz
 
-    def set_primitives(self, e, vx, vy, vz):
-        args = [_arg(a, self._dtype, self.cells) for a in (e, vx, vy, vz)]
+    def set_primitives(self, e, vx, vy, vz, n=None):
+        """(e, v) and, on a charged handle, the rest-frame charge density n."""
+        fields = (e, vx, vy, vz) if n is None else (e, vx, vy, vz, n)
+        args = [_arg(a, self._dtype, self.cells) for a in fields]
         if len({a[1] for a in args}) != 1:
             raise ValueError("inputs must be all on the host or all on the device")
-        _check(lib().hydro_set_primitives(self.h, *[a[0] for a in args], args[0][1]))
+        if n is None:
+            _check(lib().hydro_set_primitives(self.h, *[a[0] for a in args], args[0][1]))
+        else:
+            _check(lib().hydro_set_primitives_charged(self.h, *[a[0] for a in args],
+                                                      args[0][1]))
+
+    def charge_density(self, out=None):
+        """n = R / gamma [nz][ny][nx] (charged handles)."""
+        if out is None:
+            out = np.empty(self.shape[1:], dtype=self._dtype)
+        p, dev, _ = _out_arg(out, self._dtype, self.cells)
+        _check(lib().hydro_get_charge_density(self.h, p, dev))
+        return out
+
+    def charge_sum(self):
+        out = C.c_double()
+        _check(lib().hydro_charge_sum(self.h, C.byref(out)))
+        return out.value
 
     def set_conserved(self, U):
-        p, dev, keep = _arg(U, self._dtype, 4 * self.cells)
+        p, dev, keep = _arg(U, self._dtype, self.nq * self.cells)
         _check(lib().hydro_set_conserved(self.h, p, dev))
 
     def get_conserved(self, out=None):
         if out is None:
             out = np.empty(self.shape, dtype=self._dtype)
-        p, dev, _ = _arg(out, self._dtype, 4 * self.cells)
+        p, dev, _ = _arg(out, self._dtype, self.nq * self.cells)
         if not dev and not (isinstance(out, np.ndarray) and out.flags["C_CONTIGUOUS"]):
             raise ValueError("host output must be a contiguous numpy array")
         _check(lib().hydro_get_conserved(self.h, p, dev))
@@ -406,6 +432,7 @@ class Batch(_Base):
         self.h = h
         self.nevents = len(grids)
         self._dtype = np.float64 if grids[0].prec == 0 else np.float32
+        self.nq = 5 if grids[0].charge else 4
         if stream is not None:
             self.set_stream(stream)
 
@@ -418,7 +445,7 @@ class Batch(_Base):
 
     def shape(self, event):
         g = self.grids[event]
-        return (4, g.nz, g.ny, g.nx)
+        return (self.nq, g.nz, g.ny, g.nx)
 
     def set_stream(self, stream):
         _check(lib().hydro_batch_set_stream(self.h, _stream_ptr(stream)))
@@ -449,13 +476,13 @@ class Batch(_Base):
         _check(lib().hydro_batch_step(self.h, nsteps, int(use_graph)))
 
     def set_conserved(self, event, U):
-        p, dev, keep = _arg(U, self._dtype, 4 * self._cells(event))
+        p, dev, keep = _arg(U, self._dtype, self.nq * self._cells(event))
         _check(lib().hydro_batch_set_conserved(self.h, event, p, dev))
 
     def get_conserved(self, event, out=None):
         if out is None:
             out = np.empty(self.shape(event), dtype=self._dtype)
-        p, dev, _ = _out_arg(out, self._dtype, 4 * self._cells(event))
+        p, dev, _ = _out_arg(out, self._dtype, self.nq * self._cells(event))
         _check(lib().hydro_batch_get_conserved(self.h, event, p, dev))
         return out
 
@@ -474,6 +501,18 @@ class Batch(_Base):
         out = (C.c_double * (4 * self.nevents))()
         _check(lib().hydro_batch_conservation_sums(self.h, out))
         return np.array(out[:]).reshape(self.nevents, 4)
+
+    def charge_sums(self):
+        out = (C.c_double * self.nevents)()
+        _check(lib().hydro_batch_charge_sums(self.h, out))
+        return np.array(out[:])
+
+    def set_primitives_charged(self, event, e, vx, vy, vz, n):
+        args = [_arg(a, self._dtype, self._cells(event)) for a in (e, vx, vy, vz, n)]
+        if len({a[1] for a in args}) != 1:
+            raise ValueError("inputs must be all on the host or all on the device")
+        _check(lib().hydro_batch_set_primitives_charged(self.h, event, *[a[0] for a in args],
+                                                        args[0][1]))
 
     def event_status(self):
         out = (C.c_int * self.nevents)()
