@@ -737,6 +737,72 @@ def run_learned(args):
     return 0
 
 
+def run_table(args):
+    """One 128^3 event (dx 0.1 fm) of 416 hot spots with flow |u| <= 0.5,
+    outflow, the tabulated non-conformal EOS (4096 nodes), FP32, minmod,
+    2 MUSTA stages, RK2 + Hancock, Strang; cons->prim by Newton from the
+    seed --seed (zero or conformal).  Metric: cell-updates/s; with the
+    Newton iterations per solve from a counting step."""
+    import torch
+    from paper_1510_06340_b300 import build, hydro
+    from paper_1510_06340_b300 import inputs as I
+    torch.cuda.set_device(0)
+    build.build(verbose=False)
+    n = 128
+    g = I.event_grid(n, 0.1)
+    spots = I.hotspots(0, flow_max=0.5)
+    tab = I.eos_table()
+    stream = torch.cuda.Stream()
+    grid = hydro.make_grid(n, n, n, dx=0.1, x0=g["x0"], y0=g["y0"], z0=g["z0"], bc="outflow",
+                           prec="fp32", cfl=0.4)
+    h = hydro.Hydro(grid, hydro.make_eos(tab, seed=args.seed), limiter="minmod", stages=2,
+                    stream=stream)
+    h.init_hotspots(spots, I.SPOT_SIGMA, I.E_BACKGROUND)
+    if args.launch:
+        th, sg = (int(x) for x in args.launch.split(","))
+        for ax in range(3):
+            h.force_launch(ax, th, sg)
+    h.step(args.warmup)
+    torch.cuda.synchronize()
+    h.set_kernel_timing(True)
+    h.kernel_timing()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with Clocks(0) as clk:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        h.step(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    (sweep_ms, other_ms), (n_sweep, n_other) = h.kernel_timing()
+    h.set_kernel_timing(False)
+    shapes = [h.get_launch(ax) for ax in range(3)]
+    h.enable_counters(True)
+    h.step(1)
+    c = h.counters()
+    cells = n ** 3
+    hbm, src = peaks()
+    avg = sweep_ms / max(n_sweep, 1)
+    bps = 2 * 4 * 4 * cells
+    line = {"metric": "cell_updates_per_s", "value": cells * args.steps / (ms * 1e-3),
+            "unit": "cell-updates/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "128^3 hot spots with flow |u| <= 0.5, outflow, tabulated EOS "
+                                   f"(4096 nodes), Newton seed {args.seed}, FP32, minmod, "
+                                   "2 MUSTA stages, RK2+Hancock, Strang", "cells": cells,
+                       "launch_threads_segments_xyz": shapes},
+            "roofline": {"bound": "hbm", "achieved": bps / (avg * 1e-3) / 1e9, "peak": hbm,
+                         "unit": "GB/s", "frac": bps / (avg * 1e-3) / 1e9 / hbm,
+                         "avg_launch_ms": avg, "peak_source": src},
+            "newton_iterations_per_solve": c["newton_iters"] / max(c["newton_calls"], 1),
+            "newton_solves_per_cell_sweep": c["newton_calls"] / (5 * cells),
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_mixed(args):
     """Single 512^3 event (dx 0.1 fm) of hot spots with random flow |u| <= 0.95,
     outflow, mixed precision (FP32 state and fluxes, FP64 cons->prim for
@@ -817,7 +883,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="blast256_fp32",
-                    choices=sorted(WORKLOADS) + ["batch512", "learned128", "mixed512"])
+                    choices=sorted(WORKLOADS) + ["batch512", "learned128", "mixed512",
+                                                 "table128"])
+    ap.add_argument("--seed", default="conformal", choices=["zero", "conformal"],
+                    help="Newton seed of the table128 workload")
     ap.add_argument("--events", type=int, default=512, help="events per GPU (batch512)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--launch", default="", help="force 'threads,segments' for every axis")
@@ -835,6 +904,8 @@ def main():
         return run_reference(args)
     if args.workload == "batch512":
         return run_batch(args)
+    if args.workload == "table128":
+        return run_table(args)
     if args.workload == "mixed512":
         return run_mixed(args)
     if args.workload == "learned128":

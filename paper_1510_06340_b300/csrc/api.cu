@@ -288,21 +288,29 @@ struct Solver {
             sc.lne_max = eos->lne_max;
             sc.inv_h = double(tn - 1) / (eos->lne_max - eos->lne_min);
             sc.e_max = std::exp(eos->lne_max);
-            std::vector<float> p32(tn), c32(tn);
+            // packed nodes (p_i, p_{i+1} - p_i, c2_i, c2_{i+1} - c2_i); each
+            // difference in its own precision, as the interpolation takes it
+            std::vector<double> t64(4 * (size_t)tn);
+            std::vector<float> t32(4 * (size_t)tn);
             for (int i = 0; i < tn; ++i) {
-                p32[i] = (float)eos->p_tab[i];
-                c32[i] = (float)eos->cs2_tab[i];
+                const int j = i + 1 < tn ? i + 1 : i;
+                t64[4 * i + 0] = eos->p_tab[i];
+                t64[4 * i + 1] = eos->p_tab[j] - eos->p_tab[i];
+                t64[4 * i + 2] = eos->cs2_tab[i];
+                t64[4 * i + 3] = eos->cs2_tab[j] - eos->cs2_tab[i];
+                const float p0 = (float)eos->p_tab[i], p1 = (float)eos->p_tab[j];
+                const float c0 = (float)eos->cs2_tab[i], c1 = (float)eos->cs2_tab[j];
+                t32[4 * i + 0] = p0;
+                t32[4 * i + 1] = p1 - p0;
+                t32[4 * i + 2] = c0;
+                t32[4 * i + 3] = c1 - c0;
             }
-            CK(cudaMalloc(&d_p64, tn * sizeof(double)));
-            CK(cudaMalloc(&d_c64, tn * sizeof(double)));
-            CK(cudaMalloc(&d_p32, tn * sizeof(float)));
-            CK(cudaMalloc(&d_c32, tn * sizeof(float)));
-            CK(cudaMemcpy(d_p64, eos->p_tab, tn * sizeof(double), cudaMemcpyHostToDevice));
-            CK(cudaMemcpy(d_c64, eos->cs2_tab, tn * sizeof(double), cudaMemcpyHostToDevice));
-            CK(cudaMemcpy(d_p32, p32.data(), tn * sizeof(float), cudaMemcpyHostToDevice));
-            CK(cudaMemcpy(d_c32, c32.data(), tn * sizeof(float), cudaMemcpyHostToDevice));
-            sc.p_tab64 = d_p64; sc.c2_tab64 = d_c64;
-            sc.p_tab32 = d_p32; sc.c2_tab32 = d_c32;
+            CK(cudaMalloc(&d_p64, t64.size() * sizeof(double)));
+            CK(cudaMalloc(&d_p32, t32.size() * sizeof(float)));
+            CK(cudaMemcpy(d_p64, t64.data(), t64.size() * sizeof(double), cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(d_p32, t32.data(), t32.size() * sizeof(float), cudaMemcpyHostToDevice));
+            sc.tab64 = d_p64;
+            sc.tab32 = d_p32;
             if (eos->mlp_params) {
                 CK(cudaMalloc(&d_mlp_f, MLP_NPARAM * sizeof(float)));
                 CK(cudaMalloc(&d_mlp_w, MLP_NPARAM * sizeof(__nv_bfloat16)));
@@ -537,12 +545,26 @@ struct Solver {
     // once untimed first (clocks and caches settle), then each is timed in two
     // passes over the list and keeps its faster pass, so a clock ramp during
     // tuning does not favour the candidates timed last.
+    // the staged x sweep (RK2) holds shared-memory rows per warp: the block
+    // sizes whose rings fit the per-block limit
+    int staged_max_threads(int axis) const {
+        if (axis != 0 || rk != 2 || unsplit) return 256;
+        int dev = 0, optin = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
+                cudaSuccess)
+            return 128;
+        const long long per_warp = (long long)nq * 32 * XSTAGE_STEPS_PER_ROW * (long long)elem;
+        return (int)std::min<long long>(256, 32 * (optin / per_warp));
+    }
+
     hydro_status tune(int axis) {
         if (forced[axis] || tuned[axis]) return HYDRO_OK;
         int maxN = 1;
         for (const EventGeo &g : geo) maxN = std::max(maxN, g.n[axis]);
         std::vector<LaunchShape> cand;
         for (int th : {64, 128, 256}) {
+            if (th > staged_max_threads(axis)) continue;
             LaunchShape s;
             s.threads = th;
             s.seg_len = 0;
@@ -1215,6 +1237,10 @@ hydro_status hydro_force_launch(hydro_t *h, int axis, int threads, int segments)
         return HYDRO_OK;
     }
     if (threads < 32 || threads > 256 || threads % 32) return fail(HYDRO_E_INVALID, "threads must be 32..256, multiple of 32");
+    if (threads > s.staged_max_threads(axis))
+        return fail(HYDRO_E_INVALID, "the staged x sweep of this handle fits at most " +
+                                         std::to_string(s.staged_max_threads(axis)) +
+                                         " threads per block");
     if (segments < 1) return fail(HYDRO_E_INVALID, "segments must be >= 1");
     LaunchShape sh;
     sh.threads = threads;

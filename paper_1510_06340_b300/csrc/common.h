@@ -16,6 +16,9 @@ enum { SEED_ZERO = 0, SEED_CONFORMAL = 1, SEED_MLP = 2 };
 enum { CNT_CAPPED = 0, CNT_FACE_FALLBACK = 1, CNT_NEWTON_CALLS = 2, CNT_NEWTON_ITERS = 3,
        CNT_NEWTON_FAIL = 4, CNT_F64_REDO = 5, NCOUNTERS = 6 };
 
+// elements per row and field of the staged x sweep's shared-memory rings
+// (input ring 16 + 1, output ring 8 + 1): a warp holds 32 rows of them
+constexpr int XSTAGE_STEPS_PER_ROW = 26;
 constexpr int NEWTON_MAX_IT = 50;   // default iteration cap of the Newton cons->prim solve
 // per-event status bits set on the device (sticky until the event's state is set again)
 enum { FLAG_NEWTON = 1,         // a Newton cons->prim solve hit its iteration cap
@@ -112,8 +115,11 @@ struct Scheme {
     double cs2;
     int tab_n;
     double lne_min, lne_max, inv_h, e_max;
-    const double *p_tab64, *c2_tab64;
-    const float *p_tab32, *c2_tab32;
+    // node i of the table, packed for one fetch per lookup:
+    // (p_i, p_{i+1} - p_i, c2_i, c2_{i+1} - c2_i), differences in the table's
+    // precision (zero at the last node)
+    const double *tab64;          // [n][4]
+    const float *tab32;           // [n][4]
     int seed;
     double tol;
     const void *mlp_w;            // bf16 W1 [32][2], W2 [32][32], W3 [32]

@@ -317,18 +317,24 @@ __device__ __forceinline__ double log_<double>(double x) { return log(x); }
 template <>
 __device__ __forceinline__ float log_<float>(float x) { return __logf(x); }
 
+// one fetch of node i: (p_i, dp_i, c2_i, dc2_i)
 template <class R>
-__device__ __forceinline__ const R *p_tab(const Scheme &sc);
-template <>
-__device__ __forceinline__ const double *p_tab<double>(const Scheme &sc) { return sc.p_tab64; }
-template <>
-__device__ __forceinline__ const float *p_tab<float>(const Scheme &sc) { return sc.p_tab32; }
+struct TabNode {
+    R p, dp, c, dc;
+};
 template <class R>
-__device__ __forceinline__ const R *c2_tab(const Scheme &sc);
+__device__ __forceinline__ TabNode<R> tab_node(const Scheme &sc, int i);
 template <>
-__device__ __forceinline__ const double *c2_tab<double>(const Scheme &sc) { return sc.c2_tab64; }
+__device__ __forceinline__ TabNode<float> tab_node<float>(const Scheme &sc, int i) {
+    const float4 t = __ldg(reinterpret_cast<const float4 *>(sc.tab32) + i);
+    return TabNode<float>{t.x, t.y, t.z, t.w};
+}
 template <>
-__device__ __forceinline__ const float *c2_tab<float>(const Scheme &sc) { return sc.c2_tab32; }
+__device__ __forceinline__ TabNode<double> tab_node<double>(const Scheme &sc, int i) {
+    const double2 a = __ldg(reinterpret_cast<const double2 *>(sc.tab64) + 2 * i);
+    const double2 b = __ldg(reinterpret_cast<const double2 *>(sc.tab64) + 2 * i + 1);
+    return TabNode<double>{a.x, a.y, b.x, b.y};
+}
 
 template <class R>
 __device__ __forceinline__ void eos_table(const Scheme &sc, R e, R &p, R &c2) {
@@ -338,18 +344,18 @@ __device__ __forceinline__ void eos_table(const Scheme &sc, R e, R &p, R &c2) {
     if (lne < k.lne_min) { p = e * R(1.0 / 3.0); c2 = R(1.0 / 3.0); return; }
     const R u = (lne - k.lne_min) * k.inv_h;
     const int n = sc.tab_n;
-    const R *pt = p_tab<R>(sc), *ct = c2_tab<R>(sc);
     if (u >= R(n - 1)) {
-        c2 = __ldg(ct + n - 1);
-        p = fma_(c2, e - k.e_max, __ldg(pt + n - 1));
+        const TabNode<R> t = tab_node<R>(sc, n - 1);
+        c2 = t.c;
+        p = fma_(c2, e - k.e_max, t.p);
         return;
     }
     const int i = int(u);   // u >= 0 here
     const R f = u - R(i);
-    const R p0 = __ldg(pt + i), p1 = __ldg(pt + i + 1);
-    const R c0 = __ldg(ct + i), c1 = __ldg(ct + i + 1);
-    p = fma_(f, p1 - p0, p0);
-    c2 = fma_(f, c1 - c0, c0);
+    // p_i + f (p_{i+1} - p_i), and the same for c2 (linear in ln e, R11)
+    const TabNode<R> t = tab_node<R>(sc, i);
+    p = fma_(f, t.dp, t.p);
+    c2 = fma_(f, t.dc, t.c);
 }
 
 }  // namespace hy
@@ -1077,30 +1083,18 @@ constexpr int kFlushUnroll = 8;
 constexpr int XO = 8;         // output ring: steps per row
 constexpr int XOS = XO + 1;
 
+static_assert(XRS + XOS == XSTAGE_STEPS_PER_ROW, "ring sizes known to the host");
 // fields of the rings: 4, or 5 with the charge
 template <class R, bool CH = false>
 __host__ __device__ constexpr int xstage_floats_per_warp() {
     return (CH ? 5 : 4) * 32 * (XRS + XOS);
 }
 
-// HY_XFILL_L2 (build-time, 0/64/128/256): L2 prefetch size hint of the row copies
-#ifndef HY_XFILL_L2
-#define HY_XFILL_L2 0
-#endif
-#if HY_XFILL_L2 == 64
-#define HY_XFILL_HINT ".L2::64B"
-#elif HY_XFILL_L2 == 128
-#define HY_XFILL_HINT ".L2::128B"
-#elif HY_XFILL_L2 == 256
-#define HY_XFILL_HINT ".L2::256B"
-#else
-#define HY_XFILL_HINT ""
-#endif
 template <class R>
 __device__ __forceinline__ void cp_async_elem(R *dst, const R *src) {
     const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
-    asm volatile("cp.async.ca.shared.global" HY_XFILL_HINT " [%0], [%1], %2;\n" ::"r"(d),
-                 "l"(src), "n"(int(sizeof(R))) : "memory");
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(d), "l"(src),
+                 "n"(int(sizeof(R))) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() {
     asm volatile("cp.async.commit_group;\n" ::: "memory");

@@ -188,16 +188,21 @@ cudaError_t launch_sweep_prec(const SweepLaunch &a) {
         auto kfn = sweep_kernel<R, PREC, EOSK, RK, LIM, COUNT, RATE, XS, CH>();             \
         const size_t smem = XS                                                              \
             ? size_t(a.threads / 32) * xstage_floats_per_warp<R, CH>() * sizeof(R) : 0;      \
-        if (smem > 0) {   /* opt in once per device, for 256 threads */                 \
+        if (smem > 0) {   /* opt in once per device, for the most warps that fit */     \
             static std::atomic<unsigned long long> opted{0};                                \
-            int dev_ = 0;                                                                   \
+            int dev_ = 0, optin_ = 0;                                                       \
             cudaError_t e_ = cudaGetDevice(&dev_);                                          \
             if (e_ != cudaSuccess) return e_;                                               \
             const unsigned long long bit_ = 1ull << (dev_ & 63);                            \
             if (!(opted.load() & bit_)) {                                                   \
-                e_ = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                          int(8 * xstage_floats_per_warp<R, CH>() * sizeof(R)));\
+                e_ = cudaDeviceGetAttribute(&optin_,                                        \
+                                            cudaDevAttrMaxSharedMemoryPerBlockOptin, dev_); \
                 if (e_ != cudaSuccess) return e_;                                           \
+                const int warp_ = int(xstage_floats_per_warp<R, CH>() * sizeof(R));         \
+                const int warps_ = optin_ / warp_ < 8 ? optin_ / warp_ : 8;                 \
+                e_ = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                          warps_ * warp_);                                  \
+                if (e_ != cudaSuccess) { cudaGetLastError(); return e_; }                   \
                 opted.fetch_or(bit_);                                                       \
             }                                                                               \
         }                                                                                   \
