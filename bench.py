@@ -619,36 +619,6 @@ def run_batch(args):
     return 0
 
 
-def train_seed_mlp(hydro, I, tab, n=65536, epochs=150, seed=13):
-    """Train the Newton-seed MLP on the GPU on (T^{0mu}, v) pairs made by the
-    solver itself (device prim->cons, then the plain Newton solve)."""
-    import torch
-    rng = np.random.default_rng(seed)
-    e = np.exp(rng.uniform(np.log(1e-3), np.log(1e2), n))
-    v = 0.95 * rng.uniform(0, 1, n) ** 0.5
-    d = rng.normal(size=(3, n))
-    d /= np.linalg.norm(d, axis=0)
-    h = hydro.Hydro(hydro.make_grid(n, dx=1.0, prec="fp64"), hydro.make_eos(tab, seed="zero"))
-    h.set_primitives(*[a.reshape(1, 1, n) for a in (e, v * d[0], v * d[1], v * d[2])])
-    U = torch.tensor(h.get_conserved().reshape(4, n), device="cuda")
-    vm = torch.empty(n, dtype=torch.float64, device="cuda")
-    it = torch.empty(n, dtype=torch.int32, device="cuda")
-    h.c2p_newton(U, "zero", vm, it)
-    Uh = U.cpu().numpy()
-    E, M = Uh[0], np.linalg.norm(Uh[1:], axis=0)
-    X = np.column_stack([np.log(E), M / E])
-    P = rng.normal(size=hydro.mlp_nparam()) * 0.3
-    P[-4:] = [X[:, 0].mean(), X[:, 0].std(), X[:, 1].mean(), X[:, 1].std()]
-    params = torch.tensor(P, dtype=torch.float32, device="cuda")
-    hist = torch.zeros(epochs, dtype=torch.float32, device="cuda")
-    t0 = time.perf_counter()
-    hydro.mlp_train(params, torch.tensor(X, dtype=torch.float32, device="cuda"),
-                    torch.tensor(vm.cpu().numpy(), dtype=torch.float32, device="cuda"),
-                    512, epochs, 3e-3, 7, hist)
-    torch.cuda.synchronize()
-    return params.cpu().numpy(), float(hist[-1].item()), time.perf_counter() - t0
-
-
 def run_learned(args):
     """Tabulated non-conformal EOS: 128 events on 128^3 hot-spot grids, FP32
     batch with cons->prim by Newton seeded by the trained MLP, against the
@@ -663,10 +633,25 @@ def run_learned(args):
         b = np.asarray(b, dtype=np.float64)
         fl = 1e-3 * np.abs(b[0]).sum()
         return [float(np.abs(a[q] - b[q]).sum() / max(np.abs(b[q]).sum(), fl)) for q in range(4)]
+    from paper_1510_06340_b300 import learned
     torch.cuda.set_device(0)
     build.build(verbose=False)
     tab = I.eos_table()
-    params, loss, train_s = train_seed_mlp(hydro, I, tab)
+    # the network is trained on cells of solver runs in its range (E above
+    # where the EOS departs from p = e/3), labelled by the plain Newton solve
+    t0 = time.perf_counter()
+    U_train, emin = learned.harvest_states(tab, n=64, events=(0, 1), steps=4)
+    X, Y, _ = learned.solver_pairs(tab, U_train)
+    params, hist = learned.train_seed(X, Y, epochs=150)
+    train_s = time.perf_counter() - t0
+    loss = float(hist[-1])
+    U_in, _ = learned.harvest_states(tab, n=64, events=(7,), steps=4)
+    U_all, _ = learned.harvest_states(tab, n=64, events=(7,), steps=4, keep_all=True)
+    iters_states = {"network_range": learned.seed_iterations(tab, params, U_in, "fp32")[0],
+                    "all_cells": learned.seed_iterations(tab, params, U_all, "fp32")[0],
+                    "states": f"cells of a 64^3 hot-spot event after 4 steps (event 7, not "
+                              f"trained on); network range E > {emin:.3g}: {U_in.shape[1]} "
+                              f"of {U_all.shape[1]} cells"}
     nev, n = args.events, 128
     g0 = I.event_grid(n, 0.1)
     spots = np.stack([I.hotspots(e) for e in range(nev)])
@@ -729,6 +714,9 @@ def run_learned(args):
                                    "Newton cons->prim seeded by the BF16 tensor-core MLP"},
             "events_per_s_by_seed": res,
             "newton_iterations_per_solve": iters,
+            "newton_iterations_on_run_states_fp32": iters_states,
+            "mlp_training": f"{U_train.shape[1]} cells of 2 hot-spot events after 4 steps, "
+                            "E in the network range, targets from the plain FP64 Newton solve",
             "fp64_per_event_events_per_s": 1.0 / fp64_event_s,
             "learned_fp32_vs_fp64_rel_l1": err,
             "mlp_final_loss": loss, "mlp_train_s": train_s,

@@ -72,7 +72,8 @@ typedef enum { HYDRO_EOS_CONFORMAL = 0, HYDRO_EOS_TABLE = 1 } hydro_eos_kind;
 typedef enum {
     HYDRO_SEED_ZERO = 0,      /* v0 = 0, the start of the paper's fixed-point iteration (Sec. 2.6) */
     HYDRO_SEED_CONFORMAL = 1, /* closed-form p = e/3 solution */
-    HYDRO_SEED_MLP = 2        /* BF16 tensor-core MLP (ln E, |M|/E) -> v0 */
+    HYDRO_SEED_MLP = 2        /* BF16 tensor-core MLP (ln E, |M|/E) -> v0 where the EOS is not
+                                 conformal (hydro_mlp_seed_emin), the closed form elsewhere */
 } hydro_seed;
 
 /* One Cartesian grid (one event). */
@@ -326,6 +327,10 @@ hydro_status hydro_mlp_train(float *params, const float *X, const float *Y, int 
                              int epochs, float lr, unsigned long long seed, float *loss_hist,
                              void *stream);
 
+/* The range of the MLP seed for the handle's tabulated EOS: states with
+ * E > *emin are seeded by the network, the others by the closed-form p = e/3
+ * root (below it the table departs from p = e/3 by less than 1e-4, and E >= e). */
+hydro_status hydro_mlp_seed_emin(hydro_t *h, double *emin);
 /* Tabulated-EOS cons->prim on an array of states with the handle's EOS:
  * U [4][n] (handle dtype), seed kind; outputs |v| [n] (handle dtype) and the
  * Newton iteration count per state (int [n]).  Device pointers. */

@@ -323,6 +323,23 @@ struct Solver {
         } else {
             return fail(HYDRO_E_INVALID, "unknown EOS kind");
         }
+        // the MLP seed's range: E above the first table node where p departs
+        // from e/3 by more than 1e-4 (half of it, as a margin); below, the
+        // closed-form p = e/3 root seeds Newton
+        sc.c64.mlp_emin = 0.0;
+        if (eos->kind == HYDRO_EOS_TABLE) {
+            const double hnode = (eos->lne_max - eos->lne_min) / double(eos->n - 1);
+            double emin = std::exp(eos->lne_max);
+            for (int i = 0; i < eos->n; ++i) {
+                const double e = std::exp(eos->lne_min + i * hnode);
+                if (std::fabs(eos->p_tab[i] - e / 3.0) > 1e-4 * (e / 3.0)) {
+                    emin = 0.5 * e;
+                    break;
+                }
+            }
+            sc.c64.mlp_emin = emin;
+        }
+        sc.c32.mlp_emin = float(sc.c64.mlp_emin);
         sc.c64.lne_min = sc.lne_min;
         sc.c64.inv_h = sc.inv_h;
         sc.c64.e_max = sc.e_max;
@@ -1256,6 +1273,13 @@ hydro_status hydro_get_launch(hydro_t *h, int axis, int *threads, int *segments)
     if (st != HYDRO_OK) return st;
     *threads = h->s.shape[axis].threads;
     *segments = h->s.geo[0].seg[axis];
+    return HYDRO_OK;
+}
+hydro_status hydro_mlp_seed_emin(hydro_t *h, double *emin) {
+    HANDLE(h);
+    if (!emin) return fail(HYDRO_E_INVALID, "null emin");
+    if (h->s.sc.eos_kind != HYDRO_EOS_TABLE) return fail(HYDRO_E_INVALID, "needs a table EOS");
+    *emin = h->s.sc.c64.mlp_emin;
     return HYDRO_OK;
 }
 hydro_status hydro_c2p_newton(hydro_t *h, const void *U, int n, int seed, void *vmag, int *iters) {

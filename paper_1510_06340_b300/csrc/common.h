@@ -105,6 +105,8 @@ struct SchemeConsts {
     R emin;    // vacuum threshold: E <= emin is vacuum (2^-500 FP64, 2^-60 FP32),
                // where E^2 is still a normal number
     R wmin;    // (1 + c^2)/2 emin: W = E + p at or below it means E <= emin
+    R mlp_emin;   // tabulated EOS with the MLP seed: below this E (>= e) the table is
+                  // p = e/3 to within 1e-4, and the closed-form p = e/3 root seeds Newton
 };
 
 struct Scheme {

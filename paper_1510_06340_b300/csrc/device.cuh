@@ -381,7 +381,14 @@ __device__ __forceinline__ R newton_speed(const Scheme &sc, R E, R M, R M2, int 
         disc = disc < R(0) ? R(0) : disc;
         v = M / (R(0.5) * (a + dsqrt_(disc)));
     } else if (seed == SEED_MLP) {
-        v = R(mlp_seed_scalar(sc, float(log(double(E))), float(M / E)));
+        if (E > consts<R>(sc).mlp_emin) {
+            v = R(mlp_seed_scalar(sc, float(log(double(E))), float(M / E)));
+        } else {   // p = e/3 there: the closed form (as SEED_CONFORMAL)
+            const R a = R(4.0 / 3.0) * E;
+            R disc = a * a - R(4.0 / 3.0) * M2;
+            disc = disc < R(0) ? R(0) : disc;
+            v = M / (R(0.5) * (a + dsqrt_(disc)));
+        }
     } else {
         v = R(0);
     }
@@ -433,12 +440,18 @@ __device__ __forceinline__ Prim<R> c2p_table(const V4<R> &U, R delta, const Sche
     const R E = U.e;
     const R M2f = fma_(U.t2, U.t2, fma_(U.t1, U.t1, U.n * U.n));
     if (MLP) {
-        // taken before any lane-dependent branch
-        const float Ef = E > R(0) ? float(E) : 1.0f;
-        float xf = E > R(0) ? float(dsqrt_(M2f) / E) : 0.0f;
-        xf = fminf(xf, 1.0f - float(delta));
-        given = R(mlp_seed_warp(sc, __logf(Ef), xf));
-        seed = SEED_GIVEN;
+        // taken before any lane-dependent branch.  The network seeds the
+        // states in the EOS's non-conformal range (E above mlp_emin); below it
+        // the table is p = e/3 and the closed-form root is the better seed,
+        // and a warp with no state above it skips the forward pass
+        const bool need = E > consts<R>(sc).mlp_emin;
+        if (__any_sync(0xffffffffu, need)) {
+            const float Ef = E > R(0) ? float(E) : 1.0f;
+            float xf = E > R(0) ? float(dsqrt_(M2f) / E) : 0.0f;
+            xf = fminf(xf, 1.0f - float(delta));
+            given = R(mlp_seed_warp(sc, __logf(Ef), xf));
+        }
+        seed = need ? SEED_GIVEN : SEED_CONFORMAL;
     }
     if (!(E > consts<R>(sc).emin)) {   // vacuum (R9, R18)
         q.vn = R(0); q.p = R(0); q.W = R(0); q.fe = R(0); vmag = R(0);

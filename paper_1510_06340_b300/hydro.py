@@ -93,6 +93,7 @@ def lib():
             "hydro_batch_get_kernel_timing": [H, dp, C.POINTER(C.c_longlong)],
             "hydro_get_launch": [H, i, ip, ip],
             "hydro_c2p_newton": [H, vp, i, i, vp, vp],
+            "hydro_mlp_seed_emin": [H, dp],
             "hydro_batch_create": [C.POINTER(GridT), i, C.POINTER(EosT), i, i, C.POINTER(H)],
             "hydro_batch_set_stream": [H, vp],
             "hydro_batch_init_hotspots": [H, dp, i, d, d],
@@ -408,6 +409,12 @@ class Hydro(_Base):
         t, s = C.c_int(), C.c_int()
         _check(lib().hydro_get_launch(self.h, axis, C.byref(t), C.byref(s)))
         return t.value, s.value
+
+    def mlp_seed_emin(self):
+        """E above which the MLP seeds Newton (tabulated EOS)."""
+        out = C.c_double()
+        _check(lib().hydro_mlp_seed_emin(self.h, C.byref(out)))
+        return out.value
 
     def c2p_newton(self, U, seed, vmag, iters):
         """Device tensors: U [4][n], vmag [n] (handle dtype), iters [n] int32."""
