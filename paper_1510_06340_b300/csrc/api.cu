@@ -346,6 +346,10 @@ struct Solver {
         sc.c32.lne_min = float(sc.lne_min);
         sc.c32.inv_h = float(sc.inv_h);
         sc.c32.e_max = float(sc.e_max);
+        sc.c64.l2_scale = std::log(2.0) * sc.inv_h;
+        sc.c64.l2_off = -sc.lne_min * sc.inv_h;
+        sc.c32.l2_scale = float(sc.c64.l2_scale);
+        sc.c32.l2_off = float(sc.c64.l2_off);
         // device memory
         const size_t bytes = (size_t)nq * total_cells * elem;
         CK(cudaMalloc(&d_state[0], bytes));

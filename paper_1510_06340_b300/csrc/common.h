@@ -102,6 +102,7 @@ struct SchemeConsts {
     R hapc;    // (1 + c^2) / 2
     R hapc2;   // ((1 + c^2) / 2)^2
     R lne_min, inv_h, e_max;   // tabulated EOS: first node, 1 / node spacing, last e
+    R l2_scale, l2_off;        // u = log2(e) l2_scale + l2_off: ln 2 / h and -ln e_0 / h
     R emin;    // vacuum threshold: E <= emin is vacuum (2^-500 FP64, 2^-60 FP32),
                // where E^2 is still a normal number
     R wmin;    // (1 + c^2)/2 emin: W = E + p at or below it means E <= emin

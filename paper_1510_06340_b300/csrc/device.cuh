@@ -310,12 +310,6 @@ __device__ __forceinline__ Prim<R> c2p_conformal(const V4<R> &U, const SchemeCon
 
 // Tabulated EOS (reading R11): linear interpolation in ln e.  The node
 // constants come from the scheme's constants in precision R.
-template <class R>
-__device__ __forceinline__ R log_(R x);
-template <>
-__device__ __forceinline__ double log_<double>(double x) { return log(x); }
-template <>
-__device__ __forceinline__ float log_<float>(float x) { return __logf(x); }
 
 // one fetch of node i: (p_i, dp_i, c2_i, dc2_i)
 template <class R>
@@ -336,13 +330,27 @@ __device__ __forceinline__ TabNode<double> tab_node<double>(const Scheme &sc, in
     return TabNode<double>{a.x, a.y, b.x, b.y};
 }
 
+// position of e in node units, u = (ln e - ln e_0) / h (e > 0).  FP32 takes
+// log2 from the hardware and folds ln 2 / h and the offset into one FMA
+template <class R>
+__device__ __forceinline__ R table_u(const SchemeConsts<R> &k, R e);
+template <>
+__device__ __forceinline__ double table_u<double>(const SchemeConsts<double> &k, double e) {
+    return (log(e) - k.lne_min) * k.inv_h;
+}
+template <>
+__device__ __forceinline__ float table_u<float>(const SchemeConsts<float> &k, float e) {
+    float l2;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l2) : "f"(e));
+    return fmaf(l2, k.l2_scale, k.l2_off);
+}
+
 template <class R>
 __device__ __forceinline__ void eos_table(const Scheme &sc, R e, R &p, R &c2) {
     const SchemeConsts<R> &k = consts<R>(sc);
     if (!(e > R(0))) { p = R(0); c2 = R(1.0 / 3.0); return; }
-    const R lne = log_<R>(e);
-    if (lne < k.lne_min) { p = e * R(1.0 / 3.0); c2 = R(1.0 / 3.0); return; }
-    const R u = (lne - k.lne_min) * k.inv_h;
+    const R u = table_u<R>(k, e);
+    if (u < R(0)) { p = e * R(1.0 / 3.0); c2 = R(1.0 / 3.0); return; }   // below the table
     const int n = sc.tab_n;
     if (u >= R(n - 1)) {
         const TabNode<R> t = tab_node<R>(sc, n - 1);
@@ -424,7 +432,10 @@ __device__ __forceinline__ R newton_speed(const Scheme &sc, R E, R M, R M2, int 
         count(sc, CNT_NEWTON_ITERS, (unsigned long long)it);
         if (!conv) count(sc, CNT_NEWTON_FAIL);
     }
-    eos_table<R>(sc, E - M * v, p, c2);
+    // p at the root.  A solve that stopped on |dv| <= tol keeps p of the last
+    // evaluated iterate, which lies within tol of the root (p changes by at
+    // most c2 M tol there); a solve that stopped on f = 0 evaluated it at v
+    if (!conv || M == R(0)) eos_table<R>(sc, E - M * v, p, c2);
     p_out = p;
     iters = it;
     return v;

@@ -162,18 +162,6 @@ template <class R, int PREC, int EOSK, int RK, int LIM, bool COUNT, bool RATE, b
 __global__ void __maxnreg__(HY_RK3_MAXNREG) k_sweep_rk3(HY_SWEEP_PARAMS) {
     sweep_body<R, PREC, EOSK, RK, LIM, COUNT, RATE, XS, CH>(HY_SWEEP_ARGS);
 }
-// The tabulated-EOS sweeps (Newton cons->prim inside every flux evaluation)
-// take all 255 registers when left alone, which leaves 8 warps per SM for
-// a kernel whose dependent chains (log, table fetch, reciprocal) need warps
-// to hide latency; capped at 168 the FP32 ones fit without spilling and keep
-// 12 (FP64 values take register pairs: capped, those spill hundreds of bytes).
-#ifndef HY_TAB_MAXNREG
-#define HY_TAB_MAXNREG 168
-#endif
-template <class R, int PREC, int EOSK, int RK, int LIM, bool COUNT, bool RATE, bool XS, bool CH>
-__global__ void __maxnreg__(HY_TAB_MAXNREG) k_sweep_tab(HY_SWEEP_PARAMS) {
-    sweep_body<R, PREC, EOSK, RK, LIM, COUNT, RATE, XS, CH>(HY_SWEEP_ARGS);
-}
 #undef HY_SWEEP_PARAMS
 #undef HY_SWEEP_ARGS
 
@@ -181,8 +169,6 @@ template <class R, int PREC, int EOSK, int RK, int LIM, bool COUNT, bool RATE, b
 constexpr auto sweep_kernel() {
     if constexpr (RK == 3 && PREC == PREC_F32 && EOSK == EOS_CONFORMAL && !COUNT && !CH)
         return &k_sweep_rk3<R, PREC, EOSK, RK, LIM, COUNT, RATE, XS, CH>;
-    else if constexpr (EOSK != EOS_CONFORMAL && !COUNT && PREC == PREC_F32)
-        return &k_sweep_tab<R, PREC, EOSK, RK, LIM, COUNT, RATE, XS, CH>;
     else
         return &k_sweep<R, PREC, EOSK, RK, LIM, COUNT, RATE, XS, CH>;
 }
