@@ -71,9 +71,9 @@ SWEEP_TRAFFIC = {(256, "fp32", 2, 2, False): 597.4e6}
 
 def bytes_per_cell_stage_unsplit(elem):
     """Algorithmic HBM bytes of one unsplit RK stage per cell: 6 faces written
-    and read, 3 interface fluxes written and read, the input state read, the
-    RK inputs read and the result written (4 fields each)."""
-    return (2 * 24 + 2 * 12 + 4 + 8 + 4) * elem
+    and read (the interface fluxes stay in shared memory), the input state
+    read, the RK inputs read and the result written (4 fields each)."""
+    return (2 * 24 + 4 + 8 + 4) * elem
 
 
 ALU_PEAK_TFLOPS = {"fp32": 148 * 128 * 2 * 2.032e9 / 1e12, "fp64": 1.25}
@@ -325,11 +325,11 @@ def run_ours(args):
     hbm, src = peaks()
     avg_sweep_ms = sweep_ms / max(n_sweep, 1)
     if unsplit:
-        # a timed group is one RK stage: faces, 3 flux launches, update
+        # a timed group is one RK stage: faces, then fluxes + update per tile
         bytes_per_sweep = bytes_per_cell_stage_unsplit(BYTES[prec]) * cells
         fpc = FLOPS_PER_CELL_STAGE_UNSPLIT.get((stages, rk))
-        launches = 5 * n_sweep + n_other
-        kernel_name = "unsplit RK stage (k_us_faces, 3 x k_us_flux, k_us_update)"
+        launches = 2 * n_sweep + n_other
+        kernel_name = "unsplit RK stage (k_us_faces, k_us_tile)"
     else:
         bytes_per_sweep = 2 * 4 * BYTES[prec] * cells      # read + write of 4 fields
         fpc = flops_cell_sweep

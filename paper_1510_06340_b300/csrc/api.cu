@@ -84,10 +84,10 @@ struct Solver {
     bool unsplit = false;
     std::vector<UnsplitGeo> ugeo;
     UnsplitGeo *d_ugeo = nullptr;
-    void *d_faces = nullptr, *d_fluxes = nullptr;
+    void *d_faces = nullptr;
     void *d_stage[2] = {nullptr, nullptr};
-    std::vector<WorkItem> us_face_items, us_flux_items[3];
-    WorkItem *d_us_face_items = nullptr, *d_us_flux_items[3] = {nullptr, nullptr, nullptr};
+    std::vector<WorkItem> us_face_items, us_tile_items;
+    WorkItem *d_us_face_items = nullptr, *d_us_tile_items = nullptr;
     // scheme
     Scheme sc{};
     double *d_p64 = nullptr, *d_c64 = nullptr;
@@ -139,9 +139,8 @@ struct Solver {
         void *ptrs[] = {d_geo, d_clk, d_clk_tune, d_state[0], d_state[1], d_cell_items,
                         d_sweep_items[0], d_sweep_items[1], d_sweep_items[2], d_partial, d_sums,
                         d_p64, d_c64, d_p32, d_c32, d_mlp_f, d_mlp_w, d_counters, d_flags,
-                        d_work_counter, d_ugeo, d_faces, d_fluxes, d_stage[0], d_stage[1],
-                        d_us_face_items, d_us_flux_items[0], d_us_flux_items[1],
-                        d_us_flux_items[2]};
+                        d_work_counter, d_ugeo, d_faces, d_stage[0], d_stage[1],
+                        d_us_face_items, d_us_tile_items};
         for (void *p : ptrs)
             if (p) cudaFree(p);
         d_geo = nullptr;
@@ -158,10 +157,10 @@ struct Solver {
         d_flags = nullptr;
         d_work_counter = nullptr;
         d_ugeo = nullptr;
-        d_faces = d_fluxes = nullptr;
+        d_faces = nullptr;
         d_stage[0] = d_stage[1] = nullptr;
         d_us_face_items = nullptr;
-        for (int a = 0; a < 3; ++a) d_us_flux_items[a] = nullptr;
+        d_us_tile_items = nullptr;
     }
 
     Scheme scheme() const {
@@ -401,32 +400,34 @@ struct Solver {
     // scratch and work lists of the unsplit scheme (R16)
     hydro_status init_unsplit() {
         ugeo.resize(nevents);
-        long long fo = 0, xo = 0;
+        long long fo = 0;
+        const int tdim[3] = {US_TX, US_TY, US_TZ};
         for (int e = 0; e < nevents; ++e) {
             const EventGeo &g = geo[e];
             UnsplitGeo &u = ugeo[e];
             memset(&u, 0, sizeof u);
+            long long tiles = 1;
             for (int a = 0; a < 3; ++a) {
                 u.g[a] = g.n[a] > 1 ? 1 : 0;
                 u.m[a] = g.n[a] + 2 * u.g[a];
+                const int T = std::min(g.n[a], tdim[a]);
+                tiles *= (g.n[a] + T - 1) / T;
             }
             u.gcells = (long long)u.m[0] * u.m[1] * u.m[2];
             u.fo = fo;
             fo += 24 * u.gcells;
-            for (int a = 0; a < 3; ++a) {
-                u.nint[a] = u.g[a] ? (g.cells / g.n[a]) * (long long)(g.n[a] + 1) : 0;
-                u.xo[a] = xo;
-                xo += 4 * u.nint[a];
-            }
             for (long long c = 0; c < u.gcells; c += US_ITEM) us_face_items.push_back(item(e, c, u.gcells));
-            for (int a = 0; a < 3; ++a)
-                for (long long c = 0; c < u.nint[a]; c += US_ITEM)
-                    us_flux_items[a].push_back(item(e, c, u.nint[a]));
+            for (long long t = 0; t < tiles; ++t) {
+                WorkItem w;
+                w.event = e;
+                w.first = t;
+                w.count = 1;
+                us_tile_items.push_back(w);
+            }
         }
         CK(cudaMalloc(&d_ugeo, nevents * sizeof(UnsplitGeo)));
         CK(cudaMemcpy(d_ugeo, ugeo.data(), nevents * sizeof(UnsplitGeo), cudaMemcpyHostToDevice));
         CK(cudaMalloc(&d_faces, (size_t)fo * elem));
-        CK(cudaMalloc(&d_fluxes, (size_t)std::max(xo, 1LL) * elem));
         const size_t bytes = (size_t)4 * total_cells * elem;
         CK(cudaMalloc(&d_stage[0], bytes));
         if (rk == 3) CK(cudaMalloc(&d_stage[1], bytes));
@@ -437,7 +438,7 @@ struct Solver {
             return cudaMemcpy(*d, v.data(), v.size() * sizeof(WorkItem), cudaMemcpyHostToDevice);
         };
         CK(upload(us_face_items, &d_us_face_items));
-        for (int a = 0; a < 3; ++a) CK(upload(us_flux_items[a], &d_us_flux_items[a]));
+        CK(upload(us_tile_items, &d_us_tile_items));
         return HYDRO_OK;
     }
 
@@ -455,17 +456,12 @@ struct Solver {
     cudaError_t enqueue_unsplit(bool cfl_dt) {
         UnsplitLaunch a;
         a.faces = d_faces;
-        a.fluxes = d_fluxes;
         a.ev = d_geo;
         a.ug = d_ugeo;
         a.face_items = d_us_face_items;
         a.n_face_items = (int)us_face_items.size();
-        for (int d = 0; d < 3; ++d) {
-            a.flux_items[d] = d_us_flux_items[d];
-            a.n_flux_items[d] = (int)us_flux_items[d].size();
-        }
-        a.cell_items = d_cell_items;
-        a.n_cell_items = (int)cell_items.size();
+        a.tile_items = d_us_tile_items;
+        a.n_tile_items = (int)us_tile_items.size();
         a.clk = d_clk;
         a.sc = scheme();
         a.rk = rk;

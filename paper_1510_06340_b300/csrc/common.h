@@ -67,17 +67,18 @@ struct EventClock {
 };
 
 // Per-event layout of the scratch of the unsplit scheme: evolved faces on the
-// box grown by one cell along each active axis, interface fluxes per axis.
+// box grown by one cell along each active axis.
 struct UnsplitGeo {
     long long fo;        // element offset of the event's faces: face (d, side, q) of
                          // grown cell gi at fo + ((2 d + side) 4 + q) gcells + gi
     long long gcells;    // cells of the grown box
-    long long xo[3];     // element offset of the axis-d interface fluxes:
-                         // field q of interface ii at xo[d] + q nint[d] + ii
-    long long nint[3];   // interfaces along axis d, (n_d + 1) cells / n_d (0: inactive)
     int g[3];            // 1 on active axes, else 0
     int m[3];            // grown box: n + 2 g
 };
+
+// Tiles of the unsplit scheme's flux-and-update kernel: at most US_TX x US_TY x
+// US_TZ cells (n_d on an axis with fewer); one work item per tile
+constexpr int US_TX = 32, US_TY = 8, US_TZ = 4;
 
 // A block's share of a launch: `count` consecutive units of one event
 // starting at `first` (pencil-segment tasks for sweeps, cells otherwise).

@@ -30,18 +30,18 @@ cudaError_t launch_sweep_f32(const SweepLaunch &a);
 cudaError_t launch_sweep_mixed(const SweepLaunch &a);
 
 // One RK stage of the unsplit scheme (Eq. 13 with all flux terms, reading
-// R16): evolved faces, MUSTA-FORCE fluxes per active axis, then the
-// divergence and the stage combination of Eq. 5-7.
+// R16): evolved faces, then per tile of cells the MUSTA-FORCE fluxes of every
+// active axis, the divergence and the stage combination of Eq. 5-7.
 struct UnsplitLaunch {
     const void *in;          // state the stage differentiates (U^n, U1 or U2)
     const void *u0;          // U^n
     const void *u1;          // U1 (stages 2-3), U2 (stage 3 of RK3)
     void *out;               // the stage result
-    void *faces, *fluxes;    // scratch laid out by UnsplitGeo
+    void *faces;             // scratch laid out by UnsplitGeo
     const EventGeo *ev;
     const UnsplitGeo *ug;
-    const WorkItem *face_items, *flux_items[3], *cell_items;
-    int n_face_items, n_flux_items[3], n_cell_items;
+    const WorkItem *face_items, *tile_items;
+    int n_face_items, n_tile_items;
     const EventClock *clk;
     Scheme sc;
     int rk, stage;           // stage 1..rk

@@ -3,14 +3,15 @@
 // terms, the FORCE alpha of Eq. 10-11 (3 in 3-D), the RK stages of Eq. 5-7 on
 // the whole field (reading R16).
 //
-// Three kernels per stage:
+// Two kernels per stage:
 //   k_us_faces   evolved faces of every cell of the box grown by one cell
-//                along each active axis (ghosts mapped by the BCs);
-//   k_us_flux    the MUSTA-FORCE flux of every interface, one launch per axis;
-//   k_us_update  dt L(U) = -sum_d dt/dx_d (F_d,i+1/2 - F_d,i-1/2) and the RK
-//                stage combination; on the last stage also the CFL rate
-//                (sum over axes, R16c) of the new state.
-// Faces and fluxes go through HBM scratch laid out by UnsplitGeo.
+//                along each active axis (ghosts mapped by the BCs), written to
+//                HBM scratch laid out by UnsplitGeo;
+//   k_us_tile    per tile of cells: the MUSTA-FORCE flux of every interface of
+//                the tile, axis by axis, in shared memory; dt L(U) =
+//                -sum_d dt/dx_d (F_d,i+1/2 - F_d,i-1/2); the RK stage
+//                combination; on the last stage also the CFL rate (sum over
+//                axes, R16c) of the new state.
 #pragma once
 #include "device.cuh"
 #include "kernels.h"
@@ -149,73 +150,43 @@ k_us_faces(const R *__restrict__ in, R *__restrict__ faces, const EventGeo *__re
     }
 }
 
-// Interfaces along axis d are numbered x fastest on the grid extended by one
-// cell along d: interface (x, y, z) lies between the cell one step before it
-// along d and the cell (x, y, z), so neighbouring threads touch neighbouring
-// memory for every axis.
-__device__ __forceinline__ unsigned us_iface_index(const EventGeo &g, int d, int x, int y, int z) {
-    const unsigned e0 = unsigned(g.n[0] + (d == 0)), e1 = unsigned(g.n[1] + (d == 1));
-    return unsigned(x) + e0 * (unsigned(y) + e1 * unsigned(z));
-}
-__device__ __forceinline__ void us_interface(const EventGeo &g, int d, unsigned ii, int x[3]) {
-    const unsigned e0 = unsigned(g.n[0] + (d == 0)), e1 = unsigned(g.n[1] + (d == 1));
-    const unsigned r = ii / e0;
-    x[0] = int(ii - r * e0);
-    x[1] = int(r % e1);
-    x[2] = int(r / e1);
-}
-
-template <class R, int PREC, int EOSK, bool COUNT>
-__global__ void __launch_bounds__(US_THREADS)
-k_us_flux(const R *__restrict__ faces, R *__restrict__ fluxes, const EventGeo *__restrict__ ev,
-          const UnsplitGeo *__restrict__ ugeo, const WorkItem *__restrict__ items, int nitems,
-          int d, const EventClock *__restrict__ clk, Scheme sc) {
-    Physics<R, PREC, EOSK, -1, COUNT> ph;
-    ph.sc = sc;
-    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
-        const WorkItem w = items[it];
-        const EventGeo &g = ev[w.event];
-        const UnsplitGeo &u = ugeo[w.event];
-        const bool valid = int(threadIdx.x) < w.count;
-        const unsigned ii = unsigned(w.first) + (valid ? threadIdx.x : 0u);
-        int x[3];
-        us_interface(g, d, ii, x);
-        // grown-box indices of the cells left (p - 1) and right (p) of the interface
-        const long long gr = (x[0] + u.g[0]) +
-                             (long long)u.m[0] * ((x[1] + u.g[1]) + (long long)u.m[1] * (x[2] + u.g[2]));
-        const long long step = d == 0 ? 1 : (d == 1 ? u.m[0] : (long long)u.m[0] * u.m[1]);
-        const long long gl = gr - step;
-        const R *fr = us_face(faces, u, d, 1, gl);   // right face of the left cell
-        const R *fl = us_face(faces, u, d, 0, gr);   // left face of the right cell
-        const V4<R> UL = v4<R>(fr[0], fr[u.gcells], fr[2 * u.gcells], fr[3 * u.gcells]);
-        const V4<R> UR = v4<R>(fl[0], fl[u.gcells], fl[2 * u.gcells], fl[3 * u.gcells]);
-        const R lam = R(clk[w.event].dt / g.h[d]);
-        ph.set_lam(lam);
-        // Sec. 2.4 steps 1-5 at this interface (R3)
-        const V4<R> F = from_axis(ph.musta(to_axis(UL, d), to_axis(UR, d), lam), d);
-        if (valid) {
-            R *o = fluxes + u.xo[d] + ii;
-            o[0] = F.e;
-            o[u.nint[d]] = F.n;
-            o[2 * u.nint[d]] = F.t1;
-            o[3 * u.nint[d]] = F.t2;
-        }
-        report_flags(sc, w.event, ph.flags_);
-    }
-}
-
 template <class R>
 __device__ __forceinline__ R us_max_nan(R a, R b) { return (b > a || b != b) ? b : a; }
 
-template <class R, int PREC, int EOSK, bool RATE>
+// Fluxes and update of one RK stage over tiles of cells, in one kernel: a
+// block takes a tile of at most US_TX x US_TY x US_TZ cells and, axis after
+// axis, evaluates the MUSTA-FORCE flux of every interface of the tile along
+// that axis (its two boundary planes included, which the neighbouring tile
+// evaluates too) into shared memory, then adds lambda_d (F_i+1/2 - F_i-1/2)
+// to the divergence its threads hold per cell, in the order of k_us_update.
+// The interface fluxes never travel through HBM.
+constexpr int US_TILE = US_TX * US_TY * US_TZ;
+constexpr int US_CPT = US_TILE / US_THREADS;                  // cells per thread
+constexpr int US_MAXINT = US_TX * US_TY * (US_TZ + 1) > (US_TX + 1) * US_TY * US_TZ
+                              ? (US_TX * (US_TY + 1) * US_TZ > US_TX * US_TY * (US_TZ + 1)
+                                     ? US_TX * (US_TY + 1) * US_TZ
+                                     : US_TX * US_TY * (US_TZ + 1))
+                              : (US_TX + 1) * US_TY * US_TZ;   // interfaces of a tile per axis
+
+// tile extents of an event (1 on an axis of one cell) and tiles per axis
+__device__ __forceinline__ void us_tile_shape(const EventGeo &g, int T[3], int nt[3]) {
+    const int full[3] = {US_TX, US_TY, US_TZ};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        T[d] = g.n[d] < full[d] ? g.n[d] : full[d];
+        nt[d] = (g.n[d] + T[d] - 1) / T[d];
+    }
+}
+
+template <class R, int PREC, int EOSK, bool COUNT, bool RATE>
 __global__ void __launch_bounds__(US_THREADS)
-k_us_update(const R *__restrict__ u0, const R *__restrict__ u1, R *__restrict__ out,
-            const R *__restrict__ fluxes, const EventGeo *__restrict__ ev,
-            const UnsplitGeo *__restrict__ ugeo, const WorkItem *__restrict__ items, int nitems,
-            const EventClock *__restrict__ clk, Scheme sc, int rk, int stage,
-            EventClock *rate_clk) {
-    Physics<R, PREC, EOSK, -1, false> ph;
+k_us_tile(const R *__restrict__ faces, const R *__restrict__ u0, const R *__restrict__ u1,
+          R *__restrict__ out, const EventGeo *__restrict__ ev, const UnsplitGeo *__restrict__ ugeo,
+          const WorkItem *__restrict__ items, int nitems, const EventClock *__restrict__ clk,
+          Scheme sc, int rk, int stage, EventClock *rate_clk) {
+    Physics<R, PREC, EOSK, -1, COUNT> ph;
     ph.sc = sc;
+    __shared__ R Fs[4][US_MAXINT];
     __shared__ R red[US_THREADS / 32];
     const R half = R(0.5), q3 = R(0.75), q1 = R(0.25), third = R(1.0 / 3.0), two3 = R(2.0 / 3.0);
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
@@ -223,49 +194,99 @@ k_us_update(const R *__restrict__ u0, const R *__restrict__ u1, R *__restrict__ 
         const EventGeo &g = ev[w.event];
         const UnsplitGeo &u = ugeo[w.event];
         const double dt = clk[w.event].dt;
-        R lam[3], ih[3];
+        int T[3], nt[3];
+        us_tile_shape(g, T, nt);
+        const int tile = int(w.first);
+        const int o[3] = {(tile % nt[0]) * T[0], ((tile / nt[0]) % nt[1]) * T[1],
+                          (tile / (nt[0] * nt[1])) * T[2]};
+        // cells of this tile (clipped to the grid)
+        int E[3];
 #pragma unroll
+        for (int d = 0; d < 3; ++d) E[d] = min(T[d], g.n[d] - o[d]);
+        const int ncell = E[0] * E[1] * E[2];
+        V4<R> D[US_CPT];
+#pragma unroll
+        for (int j = 0; j < US_CPT; ++j) D[j] = v4<R>(R(0), R(0), R(0), R(0));
+#pragma unroll 1
         for (int d = 0; d < 3; ++d) {
-            lam[d] = R(dt / g.h[d]);
-            ih[d] = R(g.inv_h[d]);
-        }
-        R m = R(0);
-        const unsigned n0 = unsigned(g.n[0]), n1 = unsigned(g.n[1]);
-        // unrolled so that the loads of consecutive cells are in flight together
-        // (412 -> 343 us per 256^3 stage)
-#pragma unroll 4
-        for (int k = threadIdx.x; k < w.count; k += blockDim.x) {
-            const long long c = w.first + k;
-            const unsigned cu = unsigned(c), row = cu / n0;
-            const int x = int(cu - row * n0), y = int(row % n1), z = int(row / n1);
-            // dt L(U) = -D, D = sum_d dt/dx_d (F_d,i+1/2 - F_d,i-1/2), axes in order
-            V4<R> D = v4<R>(R(0), R(0), R(0), R(0));
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                if (!u.g[d]) continue;
-                const unsigned im = us_iface_index(g, d, x, y, z);
-                const unsigned ip = us_iface_index(g, d, x + (d == 0), y + (d == 1), z + (d == 2));
-                const R *f = fluxes + u.xo[d];
-                const long long s = u.nint[d];
-                const V4<R> Fm = v4<R>(f[im], f[s + im], f[2 * s + im], f[3 * s + im]);
-                const V4<R> Fp = v4<R>(f[ip], f[s + ip], f[2 * s + ip], f[3 * s + ip]);
-                D = vfma<R>(lam[d], vsub(Fp, Fm), D);
+            if (!u.g[d]) continue;
+            // the tile's interfaces along d: E[d] + 1 planes of E[a] x E[b]
+            int I[3] = {E[0], E[1], E[2]};
+            I[d] += 1;
+            const int nint = I[0] * I[1] * I[2];
+            const R lam = R(dt / g.h[d]);
+            ph.set_lam(lam);
+            const long long step = d == 0 ? 1 : (d == 1 ? u.m[0] : (long long)u.m[0] * u.m[1]);
+            // every thread runs the same number of rounds (lanes past the end
+            // repeat interface 0 and store nothing): the MLP seed needs whole warps
+            const int rounds = (nint + US_THREADS - 1) / US_THREADS;
+#pragma unroll 1
+            for (int r = 0; r < rounds; ++r) {
+                const int k = r * US_THREADS + int(threadIdx.x);
+                const bool valid = k < nint;
+                const int kk = valid ? k : 0;
+                const int l0 = kk % I[0], l1 = (kk / I[0]) % I[1], l2 = kk / (I[0] * I[1]);
+                const int x0 = o[0] + l0, x1 = o[1] + l1, x2 = o[2] + l2;
+                // grown-box index of the cell right of the interface, and left of it
+                const long long gr = (x0 + u.g[0]) +
+                                     (long long)u.m[0] * ((x1 + u.g[1]) + (long long)u.m[1] * (x2 + u.g[2]));
+                const long long gl = gr - step;
+                const R *fr = us_face(faces, u, d, 1, gl);   // right face of the left cell
+                const R *fl = us_face(faces, u, d, 0, gr);   // left face of the right cell
+                const V4<R> UL = v4<R>(fr[0], fr[u.gcells], fr[2 * u.gcells], fr[3 * u.gcells]);
+                const V4<R> UR = v4<R>(fl[0], fl[u.gcells], fl[2 * u.gcells], fl[3 * u.gcells]);
+                // Sec. 2.4 steps 1-5 at this interface (R3)
+                const V4<R> F = from_axis(ph.musta(to_axis(UL, d), to_axis(UR, d), lam), d);
+                if (valid) {
+                    Fs[0][k] = F.e;
+                    Fs[1][k] = F.n;
+                    Fs[2][k] = F.t1;
+                    Fs[3][k] = F.t2;
+                }
             }
-            const V4<R> U0 = us_load(u0, g, c);
+            __syncthreads();
+#pragma unroll
+            for (int j = 0; j < US_CPT; ++j) {
+                const int c = j * US_THREADS + int(threadIdx.x);
+                if (c >= ncell) continue;
+                int l[3] = {c % E[0], (c / E[0]) % E[1], c / (E[0] * E[1])};
+                const int im = l[0] + I[0] * (l[1] + I[1] * l[2]);
+                l[d] += 1;
+                const int ip = l[0] + I[0] * (l[1] + I[1] * l[2]);
+                const V4<R> Fm = v4<R>(Fs[0][im], Fs[1][im], Fs[2][im], Fs[3][im]);
+                const V4<R> Fp = v4<R>(Fs[0][ip], Fs[1][ip], Fs[2][ip], Fs[3][ip]);
+                D[j] = vfma<R>(lam, vsub(Fp, Fm), D[j]);
+            }
+            __syncthreads();
+        }
+        report_flags(sc, w.event, ph.flags_);
+        // the RK stage combination of Eq. 5-7 (as k_us_update)
+        R m = R(0);
+        R ih[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) ih[d] = R(g.inv_h[d]);
+#pragma unroll
+        for (int j = 0; j < US_CPT; ++j) {
+            const int c = j * US_THREADS + int(threadIdx.x);
+            if (c >= ncell) continue;
+            const int x0 = o[0] + c % E[0], x1 = o[1] + (c / E[0]) % E[1],
+                      x2 = o[2] + c / (E[0] * E[1]);
+            const long long cc = x0 + (long long)g.n[0] * (x1 + (long long)g.n[1] * x2);
+            const V4<R> U0 = us_load(u0, g, cc);
             V4<R> r;
             if (stage == 1) {
-                r = vsub(U0, D);                             // U + dt L(U)
+                r = vsub(U0, D[j]);                          // U + dt L(U)
             } else if (rk == 2) {
-                const V4<R> U1 = us_load(u1, g, c);          // Eq. 6
-                r = vmul<R>(half, vsub(vadd(U0, U1), D));
+                const V4<R> U1 = us_load(u1, g, cc);         // Eq. 6
+                r = vmul<R>(half, vsub(vadd(U0, U1), D[j]));
             } else if (stage == 2) {
-                const V4<R> U1 = us_load(u1, g, c);          // Eq. 7, U2
-                r = vadd(vmul<R>(q3, U0), vmul<R>(q1, vsub(U1, D)));
+                const V4<R> U1 = us_load(u1, g, cc);         // Eq. 7, U2
+                r = vadd(vmul<R>(q3, U0), vmul<R>(q1, vsub(U1, D[j])));
             } else {
-                const V4<R> U2 = us_load(u1, g, c);          // Eq. 7, U^{n+1}
-                r = vadd(vmul<R>(third, U0), vmul<R>(two3, vsub(U2, D)));
+                const V4<R> U2 = us_load(u1, g, cc);         // Eq. 7, U^{n+1}
+                r = vadd(vmul<R>(third, U0), vmul<R>(two3, vsub(U2, D[j])));
             }
-            us_store(out, g, c, r);
+            us_store(out, g, cc, r);
             if (RATE && rate_clk) {   // R16c: sum over the active axes
                 R rr = R(0);
 #pragma unroll
@@ -274,9 +295,9 @@ k_us_update(const R *__restrict__ u0, const R *__restrict__ u1, R *__restrict__ 
                 m = us_max_nan(m, rr);
             }
         }
-        if (RATE && rate_clk) {   // block max, one atomic per work item
+        if (RATE && rate_clk) {   // block max, one atomic per tile
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) m = us_max_nan(m, __shfl_xor_sync(0xffffffffu, m, o));
+            for (int s = 16; s > 0; s >>= 1) m = us_max_nan(m, __shfl_xor_sync(0xffffffffu, m, s));
             if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
             __syncthreads();
             if (threadIdx.x == 0) {
@@ -294,7 +315,6 @@ template <class R, int PREC>
 cudaError_t launch_unsplit_prec(const UnsplitLaunch &a) {
     const R *in = static_cast<const R *>(a.in);
     R *faces = static_cast<R *>(a.faces);
-    R *fluxes = static_cast<R *>(a.fluxes);
     auto blocks = [&](int nitems) {
         const int b = a.sms * 8;
         return nitems < b ? (nitems < 1 ? 1 : nitems) : b;
@@ -312,37 +332,28 @@ cudaError_t launch_unsplit_prec(const UnsplitLaunch &a) {
                                                    a.stream>>>(in, faces, a.ev, a.ug,            \
                                                                a.face_items, a.n_face_items,     \
                                                                a.clk, a.sc);                     \
-        for (int d = 0; d < 3; ++d) {                                                            \
-            if (a.n_flux_items[d] == 0) continue;                                                \
-            if (a.sc.counters)                                                                   \
-                k_us_flux<R, PREC, EOSK, true><<<blocks(a.n_flux_items[d]), US_THREADS, 0,      \
-                                                 a.stream>>>(faces, fluxes, a.ev, a.ug,          \
-                                                             a.flux_items[d], a.n_flux_items[d], \
-                                                             d, a.clk, a.sc);                    \
+        if (a.sc.counters) {                                                                     \
+            if (a.rate_clk)                                                                      \
+                HY_US_TILE(EOSK, true, true)                                                     \
             else                                                                                 \
-                k_us_flux<R, PREC, EOSK, false><<<blocks(a.n_flux_items[d]), US_THREADS, 0,     \
-                                                  a.stream>>>(faces, fluxes, a.ev, a.ug,         \
-                                                              a.flux_items[d],                   \
-                                                              a.n_flux_items[d], d, a.clk,       \
-                                                              a.sc);                             \
+                HY_US_TILE(EOSK, true, false)                                                    \
+        } else {                                                                                 \
+            if (a.rate_clk)                                                                      \
+                HY_US_TILE(EOSK, false, true)                                                    \
+            else                                                                                 \
+                HY_US_TILE(EOSK, false, false)                                                   \
         }                                                                                        \
-        if (a.rate_clk)                                                                          \
-            k_us_update<R, PREC, EOSK, true><<<blocks(a.n_cell_items), US_THREADS, 0,           \
-                                              a.stream>>>(                                       \
-                static_cast<const R *>(a.u0), static_cast<const R *>(a.u1),                     \
-                static_cast<R *>(a.out), fluxes, a.ev, a.ug, a.cell_items, a.n_cell_items,       \
-                a.clk, a.sc, a.rk, a.stage, a.rate_clk);                                         \
-        else                                                                                     \
-            k_us_update<R, PREC, EOSK, false><<<blocks(a.n_cell_items), US_THREADS, 0,          \
-                                               a.stream>>>(                                      \
-                static_cast<const R *>(a.u0), static_cast<const R *>(a.u1),                     \
-                static_cast<R *>(a.out), fluxes, a.ev, a.ug, a.cell_items, a.n_cell_items,       \
-                a.clk, a.sc, a.rk, a.stage, nullptr);                                            \
     }
+#define HY_US_TILE(EOSK, COUNT, RATE)                                                            \
+    k_us_tile<R, PREC, EOSK, COUNT, RATE><<<blocks(a.n_tile_items), US_THREADS, 0, a.stream>>>(  \
+        faces, static_cast<const R *>(a.u0), static_cast<const R *>(a.u1),                      \
+        static_cast<R *>(a.out), a.ev, a.ug, a.tile_items, a.n_tile_items, a.clk, a.sc, a.rk,    \
+        a.stage, a.rate_clk);
     if (a.sc.eos_kind == EOS_CONFORMAL) HY_US_FACES(EOS_CONFORMAL)
     else if (mlp) HY_US_FACES(EOS_TABLE_MLP)
     else HY_US_FACES(EOS_TABLE)
 #undef HY_US_FACES
+#undef HY_US_TILE
     return cudaGetLastError();
 }
 
