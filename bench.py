@@ -66,7 +66,13 @@ def flops_per_cell_sweep(rk=2, stages=2, limiter="minmod"):
 # DRAM bytes read + written per sweep launch, mean over the five sweeps of one
 # step, from an ncu capture of the current kernels (the sweep profile summary
 # under profiles/); None where no capture of the current kernels exists
-SWEEP_TRAFFIC = {(256, "fp32", 2, 2, False): 597.4e6}
+SWEEP_TRAFFIC = {(256, "fp32", 2, 2, False): 598.0e6}
+# the event batch (FP32, minmod, k = 2, RK2): DRAM bytes per cell and sweep
+# launch, the mean over one step's five sweeps of an ncu capture of 64 events
+# of the batch recipe (1.10e8 cells, 3.3 GB held on the device), scaled by
+# cells to the full batch (the profile summary of the batch sweep under
+# profiles/); 32 B per cell is algorithmic
+BATCH_TRAFFIC_PER_CELL = 45.60
 
 
 def bytes_per_cell_stage_unsplit(elem):
@@ -506,7 +512,8 @@ def batch_measure(nev, steps, warmup, stream, gpu, no_cpu=False):
                       "steps_note": "a reduced number of the 100 steps of an event; events/s "
                                     "scales the measured steps to 100"},
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                        "frac": achieved / hbm, "traffic": None,
+                        "frac": achieved / hbm, "traffic": BATCH_TRAFFIC_PER_CELL * cells,
+                        "traffic_note": "scaled by cells from an ncu capture of 64 events",
                         "kernel": "k_sweep over all events (persistent grid)",
                         "algorithmic_bytes_per_launch": bytes_per_sweep, "avg_launch_ms": avg,
                         "peak_source": src},

@@ -13,6 +13,8 @@
 //                combination; on the last stage also the CFL rate (sum over
 //                axes, R16c) of the new state.
 #pragma once
+#include <atomic>
+
 #include "device.cuh"
 #include "kernels.h"
 
@@ -154,11 +156,11 @@ template <class R>
 __device__ __forceinline__ R us_max_nan(R a, R b) { return (b > a || b != b) ? b : a; }
 
 // Fluxes and update of one RK stage over tiles of cells, in one kernel: a
-// block takes a tile of at most US_TX x US_TY x US_TZ cells and, axis after
-// axis, evaluates the MUSTA-FORCE flux of every interface of the tile along
-// that axis (its two boundary planes included, which the neighbouring tile
-// evaluates too) into shared memory, then adds lambda_d (F_i+1/2 - F_i-1/2)
-// to the divergence its threads hold per cell, in the order of k_us_update.
+// block takes a tile of at most US_TX x US_TY x US_TZ cells, evaluates the
+// MUSTA-FORCE flux of every interface of the tile along every active axis
+// (its boundary planes included, which the neighbouring tile evaluates too)
+// into shared memory, then adds lambda_d (F_i+1/2 - F_i-1/2) per axis, in
+// axis order, to the divergence its threads hold per cell.
 // The interface fluxes never travel through HBM.
 constexpr int US_TILE = US_TX * US_TY * US_TZ;
 constexpr int US_CPT = US_TILE / US_THREADS;                  // cells per thread
@@ -186,7 +188,8 @@ k_us_tile(const R *__restrict__ faces, const R *__restrict__ u0, const R *__rest
           Scheme sc, int rk, int stage, EventClock *rate_clk) {
     Physics<R, PREC, EOSK, -1, COUNT> ph;
     ph.sc = sc;
-    __shared__ R Fs[4][US_MAXINT];
+    extern __shared__ __align__(16) unsigned char us_fs_raw[];
+    R *Fs = reinterpret_cast<R *>(us_fs_raw);   // [3 axes][4 fields][US_MAXINT]
     __shared__ R red[US_THREADS / 32];
     const R half = R(0.5), q3 = R(0.75), q1 = R(0.25), third = R(1.0 / 3.0), two3 = R(2.0 / 3.0);
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
@@ -204,61 +207,87 @@ k_us_tile(const R *__restrict__ faces, const R *__restrict__ u0, const R *__rest
 #pragma unroll
         for (int d = 0; d < 3; ++d) E[d] = min(T[d], g.n[d] - o[d]);
         const int ncell = E[0] * E[1] * E[2];
+        // the tile's interfaces along each axis: E[d] + 1 planes of E[a] x E[b]
+        // (none on an inactive axis), numbered axis after axis in one range
+        int nint[3], I[3][3];
+        R lam[3], al[3], hclf[3];
+        long long stepd[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) I[d][a] = E[a] + (a == d);
+            nint[d] = u.g[d] ? I[d][0] * I[d][1] * I[d][2] : 0;
+            lam[d] = R(dt / g.h[d]);
+            al[d] = ph.K().alpha * lam[d];      // as Physics::set_lam
+            hclf[d] = R(0.25) / al[d];
+            stepd[d] = d == 0 ? 1 : (d == 1 ? u.m[0] : (long long)u.m[0] * u.m[1]);
+        }
+        const int ntot = nint[0] + nint[1] + nint[2];
+        // every thread runs the same number of rounds (lanes past the end
+        // repeat the first interface and store nothing): the MLP seed needs
+        // whole warps
+        const int rounds = (ntot + US_THREADS - 1) / US_THREADS;
+#pragma unroll 1
+        for (int r = 0; r < rounds; ++r) {
+            const int k = r * US_THREADS + int(threadIdx.x);
+            const bool valid = k < ntot;
+            int kk = valid ? k : 0;
+            int d = 0;
+            if (kk >= nint[0]) {
+                kk -= nint[0];
+                d = 1;
+                if (kk >= nint[1]) {
+                    kk -= nint[1];
+                    d = 2;
+                }
+            }
+            const int i0 = I[d][0], i1 = I[d][1];
+            const int x0 = o[0] + kk % i0, x1 = o[1] + (kk / i0) % i1, x2 = o[2] + kk / (i0 * i1);
+            // grown-box index of the cell right of the interface, and left of it
+            const long long gr = (x0 + u.g[0]) +
+                                 (long long)u.m[0] * ((x1 + u.g[1]) + (long long)u.m[1] * (x2 + u.g[2]));
+            const long long gl = gr - stepd[d];
+            const R *fr = us_face(faces, u, d, 1, gl);   // right face of the left cell
+            const R *fl = us_face(faces, u, d, 0, gr);   // left face of the right cell
+            const V4<R> UL = v4<R>(fr[0], fr[u.gcells], fr[2 * u.gcells], fr[3 * u.gcells]);
+            const V4<R> UR = v4<R>(fl[0], fl[u.gcells], fl[2 * u.gcells], fl[3 * u.gcells]);
+            ph.al_ = al[d];
+            ph.hclf_ = hclf[d];
+            // Sec. 2.4 steps 1-5 at this interface (R3)
+            const V4<R> F = from_axis(ph.musta(to_axis(UL, d), to_axis(UR, d), lam[d]), d);
+            if (valid) {
+                R *f = Fs + d * 4 * US_MAXINT + kk;
+                f[0] = F.e;
+                f[US_MAXINT] = F.n;
+                f[2 * US_MAXINT] = F.t1;
+                f[3 * US_MAXINT] = F.t2;
+            }
+        }
+        __syncthreads();
+        // dt L(U) = -D, D = sum_d dt/dx_d (F_d,i+1/2 - F_d,i-1/2), axes in order
         V4<R> D[US_CPT];
 #pragma unroll
         for (int j = 0; j < US_CPT; ++j) D[j] = v4<R>(R(0), R(0), R(0), R(0));
-#pragma unroll 1
+#pragma unroll
         for (int d = 0; d < 3; ++d) {
-            if (!u.g[d]) continue;
-            // the tile's interfaces along d: E[d] + 1 planes of E[a] x E[b]
-            int I[3] = {E[0], E[1], E[2]};
-            I[d] += 1;
-            const int nint = I[0] * I[1] * I[2];
-            const R lam = R(dt / g.h[d]);
-            ph.set_lam(lam);
-            const long long step = d == 0 ? 1 : (d == 1 ? u.m[0] : (long long)u.m[0] * u.m[1]);
-            // every thread runs the same number of rounds (lanes past the end
-            // repeat interface 0 and store nothing): the MLP seed needs whole warps
-            const int rounds = (nint + US_THREADS - 1) / US_THREADS;
-#pragma unroll 1
-            for (int r = 0; r < rounds; ++r) {
-                const int k = r * US_THREADS + int(threadIdx.x);
-                const bool valid = k < nint;
-                const int kk = valid ? k : 0;
-                const int l0 = kk % I[0], l1 = (kk / I[0]) % I[1], l2 = kk / (I[0] * I[1]);
-                const int x0 = o[0] + l0, x1 = o[1] + l1, x2 = o[2] + l2;
-                // grown-box index of the cell right of the interface, and left of it
-                const long long gr = (x0 + u.g[0]) +
-                                     (long long)u.m[0] * ((x1 + u.g[1]) + (long long)u.m[1] * (x2 + u.g[2]));
-                const long long gl = gr - step;
-                const R *fr = us_face(faces, u, d, 1, gl);   // right face of the left cell
-                const R *fl = us_face(faces, u, d, 0, gr);   // left face of the right cell
-                const V4<R> UL = v4<R>(fr[0], fr[u.gcells], fr[2 * u.gcells], fr[3 * u.gcells]);
-                const V4<R> UR = v4<R>(fl[0], fl[u.gcells], fl[2 * u.gcells], fl[3 * u.gcells]);
-                // Sec. 2.4 steps 1-5 at this interface (R3)
-                const V4<R> F = from_axis(ph.musta(to_axis(UL, d), to_axis(UR, d), lam), d);
-                if (valid) {
-                    Fs[0][k] = F.e;
-                    Fs[1][k] = F.n;
-                    Fs[2][k] = F.t1;
-                    Fs[3][k] = F.t2;
-                }
-            }
-            __syncthreads();
+            if (!nint[d]) continue;
+            const R *f = Fs + d * 4 * US_MAXINT;
 #pragma unroll
             for (int j = 0; j < US_CPT; ++j) {
                 const int c = j * US_THREADS + int(threadIdx.x);
                 if (c >= ncell) continue;
                 int l[3] = {c % E[0], (c / E[0]) % E[1], c / (E[0] * E[1])};
-                const int im = l[0] + I[0] * (l[1] + I[1] * l[2]);
+                const int im = l[0] + I[d][0] * (l[1] + I[d][1] * l[2]);
                 l[d] += 1;
-                const int ip = l[0] + I[0] * (l[1] + I[1] * l[2]);
-                const V4<R> Fm = v4<R>(Fs[0][im], Fs[1][im], Fs[2][im], Fs[3][im]);
-                const V4<R> Fp = v4<R>(Fs[0][ip], Fs[1][ip], Fs[2][ip], Fs[3][ip]);
-                D[j] = vfma<R>(lam, vsub(Fp, Fm), D[j]);
+                const int ip = l[0] + I[d][0] * (l[1] + I[d][1] * l[2]);
+                const V4<R> Fm = v4<R>(f[im], f[US_MAXINT + im], f[2 * US_MAXINT + im],
+                                       f[3 * US_MAXINT + im]);
+                const V4<R> Fp = v4<R>(f[ip], f[US_MAXINT + ip], f[2 * US_MAXINT + ip],
+                                       f[3 * US_MAXINT + ip]);
+                D[j] = vfma<R>(lam[d], vsub(Fp, Fm), D[j]);
             }
-            __syncthreads();
         }
+        __syncthreads();   // Fs is refilled by the next tile
         report_flags(sc, w.event, ph.flags_);
         // the RK stage combination of Eq. 5-7 (as k_us_update)
         R m = R(0);
@@ -311,8 +340,30 @@ k_us_tile(const R *__restrict__ faces, const R *__restrict__ u0, const R *__rest
     }
 }
 
+// the tile kernel's flux buffer exceeds the default 48 KB of shared memory:
+// opt in once per kernel instantiation and device (the template arguments key
+// the flag: the instantiations share one function-pointer type) and clear the
+// error state of a failed opt-in
+template <class R, int PREC, int EOSK, bool COUNT, bool RATE, class K>
+cudaError_t us_tile_optin(K kfn, size_t bytes) {
+    static std::atomic<unsigned long long> opted{0};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (opted.load() & bit) return cudaSuccess;
+    e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return e;
+    }
+    opted.fetch_or(bit);
+    return cudaSuccess;
+}
+
 template <class R, int PREC>
 cudaError_t launch_unsplit_prec(const UnsplitLaunch &a) {
+    const size_t tile_smem = size_t(3 * 4 * US_MAXINT) * sizeof(R);
     const R *in = static_cast<const R *>(a.in);
     R *faces = static_cast<R *>(a.faces);
     auto blocks = [&](int nitems) {
@@ -345,10 +396,15 @@ cudaError_t launch_unsplit_prec(const UnsplitLaunch &a) {
         }                                                                                        \
     }
 #define HY_US_TILE(EOSK, COUNT, RATE)                                                            \
-    k_us_tile<R, PREC, EOSK, COUNT, RATE><<<blocks(a.n_tile_items), US_THREADS, 0, a.stream>>>(  \
-        faces, static_cast<const R *>(a.u0), static_cast<const R *>(a.u1),                      \
-        static_cast<R *>(a.out), a.ev, a.ug, a.tile_items, a.n_tile_items, a.clk, a.sc, a.rk,    \
-        a.stage, a.rate_clk);
+    {                                                                                            \
+        auto kfn = &k_us_tile<R, PREC, EOSK, COUNT, RATE>;                                      \
+        cudaError_t e_ = us_tile_optin<R, PREC, EOSK, COUNT, RATE>(kfn, tile_smem);              \
+        if (e_ != cudaSuccess) return e_;                                                        \
+        kfn<<<blocks(a.n_tile_items), US_THREADS, tile_smem, a.stream>>>(                        \
+            faces, static_cast<const R *>(a.u0), static_cast<const R *>(a.u1),                  \
+            static_cast<R *>(a.out), a.ev, a.ug, a.tile_items, a.n_tile_items, a.clk, a.sc,      \
+            a.rk, a.stage, a.rate_clk);                                                          \
+    }
     if (a.sc.eos_kind == EOS_CONFORMAL) HY_US_FACES(EOS_CONFORMAL)
     else if (mlp) HY_US_FACES(EOS_TABLE_MLP)
     else HY_US_FACES(EOS_TABLE)
