@@ -370,14 +370,6 @@ __device__ __forceinline__ void eos_table(const Scheme &sc, R e, R &p, R &c2) {
 #include "mlp_device.cuh"
 namespace hy {
 
-// HY_NEWTON_NOINLINE (build-time): keep the Newton solve a called function
-// instead of inlining it into every flux evaluation
-#ifdef HY_NEWTON_NOINLINE
-#define HY_NEWTON_ATTR __device__ __noinline__
-#else
-#define HY_NEWTON_ATTR __device__ __forceinline__
-#endif
-
 // Safeguarded Newton on f(v) = v - M / (E + p(E - M v)) in [0, M/E] (R11).
 // Returns |v|; iters receives the iteration count.
 enum { SEED_GIVEN = 100 };   // internal: start from the value passed in
@@ -385,7 +377,7 @@ enum { SEED_GIVEN = 100 };   // internal: start from the value passed in
 // RCP: take 1/W and 1/f' as one reciprocal each (the FP32 sweeps) instead of
 // three divisions
 template <class R, bool RCP = false>
-HY_NEWTON_ATTR R newton_speed(const Scheme &sc, R E, R M, R M2, int seed, R given,
+__device__ __forceinline__ R newton_speed(const Scheme &sc, R E, R M, R M2, int seed, R given,
                                           R &p_out, int &iters, unsigned *flags = nullptr) {
     R lo = R(0), hi = M / E;
     R v;
