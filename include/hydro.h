@@ -305,7 +305,7 @@ hydro_status hydro_get_launch(hydro_t *h, int axis, int *threads, int *segments)
 int hydro_mlp_nparam(void);
 
 /* Forward on the device: X [n][2] = (ln E, |M|/E) float, out [n] float seed
- * velocities.  BF16 weights and layer-2 inputs, FP32 accumulation on the
+ * velocities (n = 0: nothing to do, HYDRO_OK).  BF16 weights and layer-2 inputs, FP32 accumulation on the
  * tensor cores (mma.sync m16n8k16).  All pointers device memory. */
 hydro_status hydro_mlp_forward(const float *params, const float *X, int n, float *out,
                                void *stream);
@@ -333,7 +333,8 @@ hydro_status hydro_mlp_train(float *params, const float *X, const float *Y, int 
 hydro_status hydro_mlp_seed_emin(hydro_t *h, double *emin);
 /* Tabulated-EOS cons->prim on an array of states with the handle's EOS:
  * U [4][n] (handle dtype), seed kind; outputs |v| [n] (handle dtype) and the
- * Newton iteration count per state (int [n]).  Device pointers. */
+ * Newton iteration count per state (int [n]).  Device pointers; n = 0 is a
+ * no-op. */
 hydro_status hydro_c2p_newton(hydro_t *h, const void *U, int n, int seed, void *vmag,
                               int *iters);
 

@@ -1284,6 +1284,7 @@ hydro_status hydro_mlp_seed_emin(hydro_t *h, double *emin) {
 }
 hydro_status hydro_c2p_newton(hydro_t *h, const void *U, int n, int seed, void *vmag, int *iters) {
     HANDLE(h);
+    if (n == 0) return HYDRO_OK;
     if (!U || !vmag || !iters || n < 0) return fail(HYDRO_E_INVALID, "bad argument");
     if (h->s.sc.eos_kind != HYDRO_EOS_TABLE) return fail(HYDRO_E_INVALID, "needs a table EOS");
     if (seed < 0 || seed > 2) return fail(HYDRO_E_INVALID, "unknown seed");
@@ -1397,6 +1398,7 @@ int hydro_mlp_nparam(void) { return MLP_NPARAM; }
 
 hydro_status hydro_mlp_forward(const float *params, const float *X, int n, float *out,
                                void *stream) {
+    if (n == 0) return HYDRO_OK;
     if (!params || !X || !out || n < 0) return fail(HYDRO_E_INVALID, "bad argument");
     CK(launch_mlp_forward(params, X, n, out, (cudaStream_t)stream));
     CK(cudaStreamSynchronize((cudaStream_t)stream));
@@ -1405,6 +1407,7 @@ hydro_status hydro_mlp_forward(const float *params, const float *X, int n, float
 
 hydro_status hydro_mlp_hidden(const float *params, const float *X, int n, float *H1,
                               void *stream) {
+    if (n == 0) return HYDRO_OK;
     if (!params || !X || !H1 || n < 0) return fail(HYDRO_E_INVALID, "bad argument");
     CK(launch_mlp_hidden(params, X, n, H1, (cudaStream_t)stream));
     CK(cudaStreamSynchronize((cudaStream_t)stream));

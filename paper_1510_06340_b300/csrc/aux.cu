@@ -558,6 +558,7 @@ cudaError_t launch_finite(const CellLaunch &c, const void *U, EventClock *clk) {
 
 cudaError_t launch_c2p_newton(int prec, const Scheme &sc, const void *U, long long n, int seed,
                               void *vmag, int *iters, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
     const int th = 128;
     const long long bl = (n + th - 1) / th;
     HY_DISPATCH(prec,

@@ -399,6 +399,36 @@ def test_invalid_configurations_are_rejected(H):
         H.Hydro(H.make_grid(8, dx=0.1), stages=0)
     with pytest.raises(H.HydroError):
         H.Hydro(H.make_grid(8, dx=0.1, rk_order=4))
+    # the largest grids: 536,870,911 cells (32-bit field offsets), 429,496,729
+    # with the charge; refused before any state is allocated
+    with pytest.raises(H.HydroError) as ei:
+        H.Hydro(H.make_grid(1024, 1024, 513, dx=0.1))
+    assert "536,870,911" in str(ei.value)
+    with pytest.raises(H.HydroError) as ei:
+        H.Hydro(H.make_grid(1024, 1024, 410, dx=0.1, charge=True))
+    assert "429,496,729" in str(ei.value)
+    # a non-positive cell size on an axis of more than one cell
+    with pytest.raises(H.HydroError):
+        H.Hydro(H.make_grid(8, 8, 1, dx=0.1, dy=0.0))
+
+
+def test_empty_inputs_are_no_ops(H):
+    """Zero samples for the network and the Newton hook launch nothing and
+    succeed; a zero-step call leaves the state as it is."""
+    import torch
+    P = torch.zeros(H.mlp_nparam(), dtype=torch.float32, device="cuda")
+    X = torch.zeros((0, 2), dtype=torch.float32, device="cuda")
+    out = torch.zeros(0, dtype=torch.float32, device="cuda")
+    H.mlp_forward(P, X, out)
+    H.mlp_hidden(P, X, torch.zeros((0, 32), dtype=torch.float32, device="cuda"))
+    h = H.Hydro(H.make_grid(8, dx=0.1), H.make_eos(I.eos_table()))
+    U = torch.zeros((4, 0), dtype=torch.float64, device="cuda")
+    h.c2p_newton(U, "zero", torch.zeros(0, dtype=torch.float64, device="cuda"),
+                 torch.zeros(0, dtype=torch.int32, device="cuda"))
+    g, prim = I.spherical_blast(8)
+    hb, _, U0 = pair(H, g, prim)
+    hb.step(0)
+    assert np.array_equal(hb.get_conserved(), U0)
 
 
 # ------------------------------------------------------------------ the paper's own settings
