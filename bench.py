@@ -64,9 +64,12 @@ def flops_per_cell_sweep(rk=2, stages=2, limiter="minmod"):
 # FP32 (non-tensor) peak from unit counts and clock: 148 SMs x 128 FP32 lanes x
 # 2 flop per FMA x 2.032 GHz; FP64 from the B300's nominal 1.25 TFLOP/s.
 # DRAM bytes read + written per sweep launch, mean over the five sweeps of one
-# step, from an ncu capture of the current kernels (the sweep profile summary
-# under profiles/); None where no capture of the current kernels exists
-SWEEP_TRAFFIC = {(256, "fp32", 2, 2, False): 598.0e6}
+# step (for the unsplit scheme: per RK stage, faces + tile kernel, mean over
+# the two stages of a step), from ncu captures of the current kernels (the
+# sweep and unsplit profile summaries under profiles/); None where no capture
+# of the current kernels exists
+SWEEP_TRAFFIC = {(256, "fp32", 2, 2, False): 598.0e6,
+                 (256, "fp32", 2, 2, True): 4733.5e6}
 # the event batch (FP32, minmod, k = 2, RK2): DRAM bytes per cell and sweep
 # launch, the mean over one step's five sweeps of an ncu capture of 64 events
 # of the batch recipe (1.10e8 cells, 3.3 GB held on the device), scaled by
