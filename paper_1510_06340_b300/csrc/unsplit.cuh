@@ -180,6 +180,22 @@ __device__ __forceinline__ void us_tile_shape(const EventGeo &g, int T[3], int n
     }
 }
 
+// k / d by a multiply-high with the rounded-up reciprocal m = ceil(2^32 / d)
+// (d = 1 taken apart). With k = q d + r and m d = 2^32 + e, 0 <= e < d:
+// k m / 2^32 = q + (r + k e / 2^32) / d, whose floor is q while k d < 2^32,
+// which holds for every index of a tile (k < 2^11, d <= 33).
+struct UsDiv {
+    unsigned m;
+    bool one;
+    __device__ __forceinline__ void init(int d) {
+        one = d == 1;
+        m = one ? 0u : 0xffffffffu / unsigned(d) + 1u;
+    }
+    __device__ __forceinline__ int q(int k) const {
+        return one ? k : int(__umulhi(unsigned(k), m));
+    }
+};
+
 template <class R, int PREC, int EOSK, bool COUNT, bool RATE>
 __global__ void __launch_bounds__(US_THREADS)
 k_us_tile(const R *__restrict__ faces, const R *__restrict__ u0, const R *__restrict__ u1,
@@ -210,12 +226,15 @@ k_us_tile(const R *__restrict__ faces, const R *__restrict__ u0, const R *__rest
         // the tile's interfaces along each axis: E[d] + 1 planes of E[a] x E[b]
         // (none on an inactive axis), numbered axis after axis in one range
         int nint[3], I[3][3];
+        UsDiv dv[3][2];
         R lam[3], al[3], hclf[3];
         long long stepd[3];
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
 #pragma unroll
             for (int a = 0; a < 3; ++a) I[d][a] = E[a] + (a == d);
+            dv[d][0].init(I[d][0]);
+            dv[d][1].init(I[d][1]);
             nint[d] = u.g[d] ? I[d][0] * I[d][1] * I[d][2] : 0;
             lam[d] = R(dt / g.h[d]);
             al[d] = ph.K().alpha * lam[d];      // as Physics::set_lam
@@ -241,8 +260,9 @@ k_us_tile(const R *__restrict__ faces, const R *__restrict__ u0, const R *__rest
                     d = 2;
                 }
             }
-            const int i0 = I[d][0], i1 = I[d][1];
-            const int x0 = o[0] + kk % i0, x1 = o[1] + (kk / i0) % i1, x2 = o[2] + kk / (i0 * i1);
+            // (kk mod i0, (kk / i0) mod i1, kk / (i0 i1)) of the interface planes
+            const int qi = dv[d][0].q(kk), qj = dv[d][1].q(qi);
+            const int x0 = o[0] + kk - qi * I[d][0], x1 = o[1] + qi - qj * I[d][1], x2 = o[2] + qj;
             // grown-box index of the cell right of the interface, and left of it
             const long long gr = (x0 + u.g[0]) +
                                  (long long)u.m[0] * ((x1 + u.g[1]) + (long long)u.m[1] * (x2 + u.g[2]));
@@ -264,32 +284,15 @@ k_us_tile(const R *__restrict__ faces, const R *__restrict__ u0, const R *__rest
             }
         }
         __syncthreads();
-        // dt L(U) = -D, D = sum_d dt/dx_d (F_d,i+1/2 - F_d,i-1/2), axes in order
-        V4<R> D[US_CPT];
-#pragma unroll
-        for (int j = 0; j < US_CPT; ++j) D[j] = v4<R>(R(0), R(0), R(0), R(0));
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            if (!nint[d]) continue;
-            const R *f = Fs + d * 4 * US_MAXINT;
-#pragma unroll
-            for (int j = 0; j < US_CPT; ++j) {
-                const int c = j * US_THREADS + int(threadIdx.x);
-                if (c >= ncell) continue;
-                int l[3] = {c % E[0], (c / E[0]) % E[1], c / (E[0] * E[1])};
-                const int im = l[0] + I[d][0] * (l[1] + I[d][1] * l[2]);
-                l[d] += 1;
-                const int ip = l[0] + I[d][0] * (l[1] + I[d][1] * l[2]);
-                const V4<R> Fm = v4<R>(f[im], f[US_MAXINT + im], f[2 * US_MAXINT + im],
-                                       f[3 * US_MAXINT + im]);
-                const V4<R> Fp = v4<R>(f[ip], f[US_MAXINT + ip], f[2 * US_MAXINT + ip],
-                                       f[3 * US_MAXINT + ip]);
-                D[j] = vfma<R>(lam[d], vsub(Fp, Fm), D[j]);
-            }
-        }
-        __syncthreads();   // Fs is refilled by the next tile
         report_flags(sc, w.event, ph.flags_);
-        // the RK stage combination of Eq. 5-7 (as k_us_update)
+        // per cell of the tile: dt L(U) = -D, D = sum_d dt/dx_d (F_d,i+1/2 -
+        // F_d,i-1/2) with the axes in order, then the RK stage combination of
+        // Eq. 5-7 (as k_us_update)
+        UsDiv de0, de1;
+        de0.init(E[0]);
+        de1.init(E[1]);
+        // flux-plane offset of the interface past the cell along each axis
+        const int sp[3] = {1, I[1][0], I[2][0] * I[2][1]};
         R m = R(0);
         R ih[3];
 #pragma unroll
@@ -298,22 +301,36 @@ k_us_tile(const R *__restrict__ faces, const R *__restrict__ u0, const R *__rest
         for (int j = 0; j < US_CPT; ++j) {
             const int c = j * US_THREADS + int(threadIdx.x);
             if (c >= ncell) continue;
-            const int x0 = o[0] + c % E[0], x1 = o[1] + (c / E[0]) % E[1],
-                      x2 = o[2] + c / (E[0] * E[1]);
-            const long long cc = x0 + (long long)g.n[0] * (x1 + (long long)g.n[1] * x2);
+            const int qa = de0.q(c), qb = de1.q(qa);
+            const int l0 = c - qa * E[0], l1 = qa - qb * E[1], l2 = qb;
+            V4<R> D = v4<R>(R(0), R(0), R(0), R(0));
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                if (!nint[d]) continue;
+                const R *f = Fs + d * 4 * US_MAXINT;
+                const int im = l0 + I[d][0] * (l1 + I[d][1] * l2);
+                const int ip = im + sp[d];
+                const V4<R> Fm = v4<R>(f[im], f[US_MAXINT + im], f[2 * US_MAXINT + im],
+                                       f[3 * US_MAXINT + im]);
+                const V4<R> Fp = v4<R>(f[ip], f[US_MAXINT + ip], f[2 * US_MAXINT + ip],
+                                       f[3 * US_MAXINT + ip]);
+                D = vfma<R>(lam[d], vsub(Fp, Fm), D);
+            }
+            const long long cc =
+                (o[0] + l0) + (long long)g.n[0] * ((o[1] + l1) + (long long)g.n[1] * (o[2] + l2));
             const V4<R> U0 = us_load(u0, g, cc);
             V4<R> r;
             if (stage == 1) {
-                r = vsub(U0, D[j]);                          // U + dt L(U)
+                r = vsub(U0, D);                             // U + dt L(U)
             } else if (rk == 2) {
                 const V4<R> U1 = us_load(u1, g, cc);         // Eq. 6
-                r = vmul<R>(half, vsub(vadd(U0, U1), D[j]));
+                r = vmul<R>(half, vsub(vadd(U0, U1), D));
             } else if (stage == 2) {
                 const V4<R> U1 = us_load(u1, g, cc);         // Eq. 7, U2
-                r = vadd(vmul<R>(q3, U0), vmul<R>(q1, vsub(U1, D[j])));
+                r = vadd(vmul<R>(q3, U0), vmul<R>(q1, vsub(U1, D)));
             } else {
                 const V4<R> U2 = us_load(u1, g, cc);         // Eq. 7, U^{n+1}
-                r = vadd(vmul<R>(third, U0), vmul<R>(two3, vsub(U2, D[j])));
+                r = vadd(vmul<R>(third, U0), vmul<R>(two3, vsub(U2, D)));
             }
             us_store(out, g, cc, r);
             if (RATE && rate_clk) {   // R16c: sum over the active axes
@@ -324,6 +341,7 @@ k_us_tile(const R *__restrict__ faces, const R *__restrict__ u0, const R *__rest
                 m = us_max_nan(m, rr);
             }
         }
+        __syncthreads();   // Fs is refilled by the next tile
         if (RATE && rate_clk) {   // block max, one atomic per tile
 #pragma unroll
             for (int s = 16; s > 0; s >>= 1) m = us_max_nan(m, __shfl_xor_sync(0xffffffffu, m, s));
