@@ -72,10 +72,20 @@ k_us_faces(const R *__restrict__ in, R *__restrict__ faces, const EventGeo *__re
     Physics<R, PREC, EOSK, LIM, COUNT> ph;
     ph.sc = sc;
     const R half = R(0.5);
+    // half dt / dx_d of the event of the last item: recomputed only when the
+    // event changes (FP64 divisions issue at a small fraction of the FP32 rate)
+    int cur = -1;
+    R hlam[3] = {R(0), R(0), R(0)};
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
         const WorkItem w = items[it];
         const EventGeo &g = ev[w.event];
         const UnsplitGeo &u = ugeo[w.event];
+        if (w.event != cur) {
+            cur = w.event;
+            const double dt = clk[cur].dt;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) hlam[d] = half * R(dt / g.h[d]);
+        }
         // lanes past the item's end repeat its first unit and store nothing,
         // so a warp stays converged (the MLP Newton seed needs that)
         const bool valid = int(threadIdx.x) < w.count;
@@ -84,7 +94,6 @@ k_us_faces(const R *__restrict__ in, R *__restrict__ faces, const EventGeo *__re
         const unsigned m0 = unsigned(u.m[0]), m1 = unsigned(u.m[1]);
         const unsigned r = gi / m0;
         const int x[3] = {int(gi - r * m0) - u.g[0], int(r % m1) - u.g[1], int(r / m1) - u.g[2]};
-        const double dt = clk[w.event].dt;
         // a coordinate at most 2 cells outside [0, n): one wrap or clamp
         auto fold = [&](int j, int a) {
             const int n = g.n[a];
@@ -116,10 +125,9 @@ k_us_faces(const R *__restrict__ in, R *__restrict__ faces, const EventGeo *__re
             UL[d] = vfma<R>(-half, sl, V0);
             UR[d] = vfma<R>(half, sl, V0);
             if (sc.hancock) {   // Eq. 13: the axis-d term of the half step (R16a)
-                const R lam = R(dt / g.h[d]);
                 const V4<R> FL = from_axis(ph.flux(to_axis(UL[d], d)), d);
                 const V4<R> FR = from_axis(ph.flux(to_axis(UR[d], d)), d);
-                h = vfma<R>(half * lam, vsub(FL, FR), h);
+                h = vfma<R>(hlam[d], vsub(FL, FR), h);
             }
         }
         bool ok = true;
@@ -208,11 +216,24 @@ k_us_tile(const R *__restrict__ faces, const R *__restrict__ u0, const R *__rest
     R *Fs = reinterpret_cast<R *>(us_fs_raw);   // [3 axes][4 fields][US_MAXINT]
     __shared__ R red[US_THREADS / 32];
     const R half = R(0.5), q3 = R(0.75), q1 = R(0.25), third = R(1.0 / 3.0), two3 = R(2.0 / 3.0);
+    // dt / dx_d, alpha dt / dx_d and 1 / (4 alpha dt / dx_d) of the event of
+    // the last tile, recomputed only when the event changes
+    int cur = -1;
+    R lam[3], al[3], hclf[3];
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
         const WorkItem w = items[it];
         const EventGeo &g = ev[w.event];
         const UnsplitGeo &u = ugeo[w.event];
-        const double dt = clk[w.event].dt;
+        if (w.event != cur) {
+            cur = w.event;
+            const double dt = clk[cur].dt;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                lam[d] = R(dt / g.h[d]);
+                al[d] = ph.K().alpha * lam[d];      // as Physics::set_lam
+                hclf[d] = R(0.25) / al[d];
+            }
+        }
         int T[3], nt[3];
         us_tile_shape(g, T, nt);
         const int tile = int(w.first);
@@ -227,7 +248,6 @@ k_us_tile(const R *__restrict__ faces, const R *__restrict__ u0, const R *__rest
         // (none on an inactive axis), numbered axis after axis in one range
         int nint[3], I[3][3];
         UsDiv dv[3][2];
-        R lam[3], al[3], hclf[3];
         long long stepd[3];
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
@@ -236,9 +256,6 @@ k_us_tile(const R *__restrict__ faces, const R *__restrict__ u0, const R *__rest
             dv[d][0].init(I[d][0]);
             dv[d][1].init(I[d][1]);
             nint[d] = u.g[d] ? I[d][0] * I[d][1] * I[d][2] : 0;
-            lam[d] = R(dt / g.h[d]);
-            al[d] = ph.K().alpha * lam[d];      // as Physics::set_lam
-            hclf[d] = R(0.25) / al[d];
             stepd[d] = d == 0 ? 1 : (d == 1 ? u.m[0] : (long long)u.m[0] * u.m[1]);
         }
         const int ntot = nint[0] + nint[1] + nint[2];
