@@ -61,11 +61,22 @@ __device__ __forceinline__ R *us_face(R *faces, const UnsplitGeo &u, int d, int 
     return faces + u.fo + (long long)((2 * d + side) * 4) * u.gcells + gi;
 }
 
-// FP32: bounded to 64 registers, which keeps 32 warps per SM instead of 24
-// (20 bytes of spill); the load and MUFU latencies of this kernel need the
-// warps more than the registers (1143 -> 1037 us per 256^3 stage)
+// Blocks of US_THREADS per SM the two kernels are compiled for. FP32 with the
+// conformal EOS: four (64 registers, 32 warps per SM); the load latencies of
+// these kernels need the warps more than the registers. The tabulated EOS's
+// Newton solve needs more registers (two blocks, 128), FP64 more still.
+template <class R, int PREC, int EOSK>
+constexpr int us_faces_blocks() {
+    return sizeof(R) == 8 ? 1 : (EOSK == EOS_CONFORMAL ? 4 : 2);
+}
+template <class R, int PREC, int EOSK>
+constexpr int us_tile_blocks() {
+    return sizeof(R) == 8 ? (EOSK == EOS_CONFORMAL ? 2 : 1)
+                          : (EOSK == EOS_CONFORMAL ? (PREC == PREC_MIXED ? 3 : 4) : 2);
+}
+
 template <class R, int PREC, int EOSK, int LIM, bool COUNT>
-__global__ void __launch_bounds__(US_THREADS, sizeof(R) == 4 ? 4 : 1)
+__global__ void __launch_bounds__(US_THREADS, us_faces_blocks<R, PREC, EOSK>())
 k_us_faces(const R *__restrict__ in, R *__restrict__ faces, const EventGeo *__restrict__ ev,
            const UnsplitGeo *__restrict__ ugeo, const WorkItem *__restrict__ items, int nitems,
            const EventClock *__restrict__ clk, Scheme sc) {
@@ -172,11 +183,19 @@ __device__ __forceinline__ R us_max_nan(R a, R b) { return (b > a || b != b) ? b
 // The interface fluxes never travel through HBM.
 constexpr int US_TILE = US_TX * US_TY * US_TZ;
 constexpr int US_CPT = US_TILE / US_THREADS;                  // cells per thread
-constexpr int US_MAXINT = US_TX * US_TY * (US_TZ + 1) > (US_TX + 1) * US_TY * US_TZ
-                              ? (US_TX * (US_TY + 1) * US_TZ > US_TX * US_TY * (US_TZ + 1)
-                                     ? US_TX * (US_TY + 1) * US_TZ
-                                     : US_TX * US_TY * (US_TZ + 1))
-                              : (US_TX + 1) * US_TY * US_TZ;   // interfaces of a tile per axis
+// interfaces of a full tile along x, y and z, and the flux buffer
+// [axis][4 fields][interfaces of the axis] packed without padding, so that
+// four blocks of the FP32 kernel fit the 228 KB of shared memory of an SM
+constexpr int US_NI0 = (US_TX + 1) * US_TY * US_TZ;
+constexpr int US_NI1 = US_TX * (US_TY + 1) * US_TZ;
+constexpr int US_NI2 = US_TX * US_TY * (US_TZ + 1);
+constexpr int US_FLUX_FLOATS = 4 * (US_NI0 + US_NI1 + US_NI2);
+__host__ __device__ constexpr int us_fbase(int d) {
+    return d == 0 ? 0 : (d == 1 ? 4 * US_NI0 : 4 * (US_NI0 + US_NI1));
+}
+__host__ __device__ constexpr int us_fstride(int d) {
+    return d == 0 ? US_NI0 : (d == 1 ? US_NI1 : US_NI2);
+}
 
 // tile extents of an event (1 on an axis of one cell) and tiles per axis
 __device__ __forceinline__ void us_tile_shape(const EventGeo &g, int T[3], int nt[3]) {
@@ -205,7 +224,7 @@ struct UsDiv {
 };
 
 template <class R, int PREC, int EOSK, bool COUNT, bool RATE>
-__global__ void __launch_bounds__(US_THREADS)
+__global__ void __launch_bounds__(US_THREADS, us_tile_blocks<R, PREC, EOSK>())
 k_us_tile(const R *__restrict__ faces, const R *__restrict__ u0, const R *__restrict__ u1,
           R *__restrict__ out, const EventGeo *__restrict__ ev, const UnsplitGeo *__restrict__ ugeo,
           const WorkItem *__restrict__ items, int nitems, const EventClock *__restrict__ clk,
@@ -213,7 +232,7 @@ k_us_tile(const R *__restrict__ faces, const R *__restrict__ u0, const R *__rest
     Physics<R, PREC, EOSK, -1, COUNT> ph;
     ph.sc = sc;
     extern __shared__ __align__(16) unsigned char us_fs_raw[];
-    R *Fs = reinterpret_cast<R *>(us_fs_raw);   // [3 axes][4 fields][US_MAXINT]
+    R *Fs = reinterpret_cast<R *>(us_fs_raw);   // US_FLUX_FLOATS
     __shared__ R red[US_THREADS / 32];
     const R half = R(0.5), q3 = R(0.75), q1 = R(0.25), third = R(1.0 / 3.0), two3 = R(2.0 / 3.0);
     // dt / dx_d, alpha dt / dx_d and 1 / (4 alpha dt / dx_d) of the event of
@@ -293,11 +312,12 @@ k_us_tile(const R *__restrict__ faces, const R *__restrict__ u0, const R *__rest
             // Sec. 2.4 steps 1-5 at this interface (R3)
             const V4<R> F = from_axis(ph.musta(to_axis(UL, d), to_axis(UR, d), lam[d]), d);
             if (valid) {
-                R *f = Fs + d * 4 * US_MAXINT + kk;
+                const int st = us_fstride(d);
+                R *f = Fs + us_fbase(d) + kk;
                 f[0] = F.e;
-                f[US_MAXINT] = F.n;
-                f[2 * US_MAXINT] = F.t1;
-                f[3 * US_MAXINT] = F.t2;
+                f[st] = F.n;
+                f[2 * st] = F.t1;
+                f[3 * st] = F.t2;
             }
         }
         __syncthreads();
@@ -324,13 +344,14 @@ k_us_tile(const R *__restrict__ faces, const R *__restrict__ u0, const R *__rest
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
                 if (!nint[d]) continue;
-                const R *f = Fs + d * 4 * US_MAXINT;
+                const R *f = Fs + us_fbase(d);
+                constexpr int st[3] = {US_NI0, US_NI1, US_NI2};
                 const int im = l0 + I[d][0] * (l1 + I[d][1] * l2);
                 const int ip = im + sp[d];
-                const V4<R> Fm = v4<R>(f[im], f[US_MAXINT + im], f[2 * US_MAXINT + im],
-                                       f[3 * US_MAXINT + im]);
-                const V4<R> Fp = v4<R>(f[ip], f[US_MAXINT + ip], f[2 * US_MAXINT + ip],
-                                       f[3 * US_MAXINT + ip]);
+                const V4<R> Fm = v4<R>(f[im], f[st[d] + im], f[2 * st[d] + im],
+                                       f[3 * st[d] + im]);
+                const V4<R> Fp = v4<R>(f[ip], f[st[d] + ip], f[2 * st[d] + ip],
+                                       f[3 * st[d] + ip]);
                 D = vfma<R>(lam[d], vsub(Fp, Fm), D);
             }
             const long long cc =
@@ -398,7 +419,7 @@ cudaError_t us_tile_optin(K kfn, size_t bytes) {
 
 template <class R, int PREC>
 cudaError_t launch_unsplit_prec(const UnsplitLaunch &a) {
-    const size_t tile_smem = size_t(3 * 4 * US_MAXINT) * sizeof(R);
+    const size_t tile_smem = size_t(US_FLUX_FLOATS) * sizeof(R);
     const R *in = static_cast<const R *>(a.in);
     R *faces = static_cast<R *>(a.faces);
     auto blocks = [&](int nitems) {
