@@ -366,6 +366,28 @@ __device__ __forceinline__ void eos_table(const Scheme &sc, R e, R &p, R &c2) {
     c2 = fma_(f, t.dc, t.c);
 }
 
+// eos_table without branches: every case is evaluated from one node fetch
+// (clamped to the table) and the result is selected, giving the same values
+template <class R>
+__device__ __forceinline__ void eos_table_sel(const Scheme &sc, R e, R &p, R &c2) {
+    const SchemeConsts<R> &k = consts<R>(sc);
+    const int n = sc.tab_n;
+    const bool pos = e > R(0);
+    const R u = table_u<R>(k, pos ? e : R(1));
+    const bool below = u < R(0), above = u >= R(n - 1);
+    const int i = below ? 0 : (above ? n - 1 : int(u));
+    const TabNode<R> t = tab_node<R>(sc, i);
+    const R f = u - R(i);
+    const R third = R(1.0 / 3.0);
+    R pp = fma_(f, t.dp, t.p), cc = fma_(f, t.dc, t.c);
+    pp = above ? fma_(t.c, e - k.e_max, t.p) : pp;
+    cc = above ? t.c : cc;
+    pp = below ? e * third : pp;
+    cc = below ? third : cc;
+    p = pos ? pp : R(0);
+    c2 = pos ? cc : third;
+}
+
 }  // namespace hy
 #include "mlp_device.cuh"
 namespace hy {
@@ -376,10 +398,10 @@ enum { SEED_GIVEN = 100 };   // internal: start from the value passed in
 
 // RCP: take 1/W and 1/f' as one reciprocal each (the FP32 sweeps) instead of
 // three divisions
-template <class R, bool RCP = false>
-__device__ __forceinline__ R newton_speed(const Scheme &sc, R E, R M, R M2, int seed, R given,
-                                          R &p_out, int &iters, unsigned *flags = nullptr) {
-    R lo = R(0), hi = M / E;
+// the first iterate of the Newton solve, clamped to the bracket [0, hi]
+template <class R>
+__device__ __forceinline__ R newton_seed(const Scheme &sc, R E, R M, R M2, int seed, R given,
+                                         R hi) {
     R v;
     if (seed == SEED_GIVEN) {
         v = given;
@@ -400,8 +422,16 @@ __device__ __forceinline__ R newton_speed(const Scheme &sc, R E, R M, R M2, int 
     } else {
         v = R(0);
     }
-    v = v < lo ? lo : v;
+    v = v < R(0) ? R(0) : v;
     v = v > hi ? hi : v;
+    return v;
+}
+
+template <class R, bool RCP = false>
+__device__ __forceinline__ R newton_speed(const Scheme &sc, R E, R M, R M2, int seed, R given,
+                                          R &p_out, int &iters, unsigned *flags = nullptr) {
+    R lo = R(0), hi = M / E;
+    R v = newton_seed<R>(sc, E, M, M2, seed, given, hi);
     R p = R(0), c2 = R(0);
     int it = 0;
     bool conv = false;
@@ -439,6 +469,82 @@ __device__ __forceinline__ R newton_speed(const Scheme &sc, R E, R M, R M2, int 
     p_out = p;
     iters = it;
     return v;
+}
+
+// Two independent solves of newton_speed in one loop. Each state keeps its own
+// iterate, bracket, last p and exit iteration, so the results, iteration
+// counts and flags equal those of two newton_speed calls; the loop body has no
+// branch per state (the table lookup selects its case), so the two dependent
+// chains of table fetch, reciprocal and Newton step interleave. A state with
+// skip set takes no iteration and leaves its outputs untouched.
+template <class R, bool RCP = false>
+__device__ __forceinline__ void newton_speed2(const Scheme &sc, const R E[2], const R M[2],
+                                              const R M2[2], const int seed[2], const R given[2],
+                                              const bool skip[2], R v[2], R p_out[2],
+                                              int iters[2], unsigned *flags = nullptr) {
+    R lo[2], hi[2], p[2], c2[2];
+    int it_s[2];
+    bool conv[2], done[2];
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        lo[s] = R(0);
+        hi[s] = M[s] / E[s];
+        v[s] = newton_seed<R>(sc, E[s], M[s], M2[s], seed[s], given[s], hi[s]);
+        p[s] = R(0);
+        c2[s] = R(0);
+        it_s[s] = 0;
+        conv[s] = false;
+        done[s] = skip[s];
+        if (!skip[s] && M[s] == R(0)) {
+            v[s] = R(0);
+            conv[s] = true;
+            done[s] = true;
+        }
+    }
+    const int max_it = sc.newton_max_it;
+    for (int it = 1; it <= max_it; ++it) {
+        if (done[0] && done[1]) break;
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            R pn, cn;
+            eos_table_sel<R>(sc, E[s] - M[s] * v[s], pn, cn);
+            const R W = E[s] + pn;
+            const R iw = RCP ? rcp_(W) : R(1);
+            const R f = RCP ? v[s] - M[s] * iw : v[s] - M[s] / W;
+            const bool act = !done[s];
+            const bool hit = act && f == R(0);
+            const R nlo = f > R(0) ? lo[s] : v[s];
+            const R nhi = f > R(0) ? v[s] : hi[s];
+            const R fp = RCP ? R(1) - (cn * M2[s]) * (iw * iw) : R(1) - cn * M2[s] / (W * W);
+            R vn = RCP ? v[s] - f * rcp_(fp) : v[s] - f / fp;
+            if (!(vn > nlo && vn < nhi)) vn = R(0.5) * (nlo + nhi);
+            const R dv = vn - v[s];
+            const bool step = act && !hit;
+            p[s] = act ? pn : p[s];
+            c2[s] = act ? cn : c2[s];
+            lo[s] = step ? nlo : lo[s];
+            hi[s] = step ? nhi : hi[s];
+            v[s] = step ? vn : v[s];
+            const bool fin = hit || (step && fabs_(dv) <= R(sc.tol));
+            conv[s] = conv[s] || fin;
+            it_s[s] = fin ? it : it_s[s];
+            done[s] = done[s] || fin;
+        }
+    }
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        if (skip[s]) continue;
+        if (!conv[s]) it_s[s] = max_it;
+        if (!conv[s] && flags) *flags |= FLAG_NEWTON;
+        if (sc.counters) {
+            count(sc, CNT_NEWTON_CALLS);
+            count(sc, CNT_NEWTON_ITERS, (unsigned long long)it_s[s]);
+            if (!conv[s]) count(sc, CNT_NEWTON_FAIL);
+        }
+        if (!conv[s] || M[s] == R(0)) eos_table<R>(sc, E[s] - M[s] * v[s], p[s], c2[s]);
+        p_out[s] = p[s];
+        iters[s] = it_s[s];
+    }
 }
 
 // MLP: seed from the warp-wide tensor-core MLP (the whole warp must be
@@ -486,6 +592,65 @@ __device__ __forceinline__ Prim<R> c2p_table(const V4<R> &U, R delta, const Sche
     q.W = E + p;
     q.fe = q.W * q.vn;
     return q;
+}
+
+// c2p_table for two states whose Newton solves run in one loop (newton_speed2):
+// the same results as two c2p_table calls (the MLP seeds, warp-wide, are taken
+// one after the other before any lane-dependent branch)
+template <class R, bool MLP, bool RCP = false>
+__device__ __forceinline__ void c2p_table2(const V4<R> U[2], R delta, const Scheme &sc, int seed0,
+                                           Prim<R> q[2], R vmag[2], unsigned *flags = nullptr) {
+    R E[2], M2f[2], given[2] = {R(0), R(0)};
+    int seed[2] = {seed0, seed0};
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        E[s] = U[s].e;
+        M2f[s] = fma_(U[s].t2, U[s].t2, fma_(U[s].t1, U[s].t1, U[s].n * U[s].n));
+    }
+    if (MLP) {
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            const bool need = E[s] > consts<R>(sc).mlp_emin;
+            if (__any_sync(0xffffffffu, need)) {
+                const float Ef = E[s] > R(0) ? float(E[s]) : 1.0f;
+                float xf = E[s] > R(0) ? float(dsqrt_(M2f[s]) / E[s]) : 0.0f;
+                xf = fminf(xf, 1.0f - float(delta));
+                given[s] = R(mlp_seed_warp(sc, __logf(Ef), xf));
+            }
+            seed[s] = need ? SEED_GIVEN : SEED_CONFORMAL;
+        }
+    }
+    bool vac[2];
+    R M[2], M2[2], Mfull[2];
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        vac[s] = !(E[s] > consts<R>(sc).emin);   // vacuum (R9, R18)
+        const R cap = (R(1) - delta) * E[s];
+        Mfull[s] = dsqrt_(M2f[s]);
+        M2[s] = M2f[s];
+        M[s] = Mfull[s];
+        if (!vac[s] && M2f[s] > cap * cap) {
+            M2[s] = cap * cap;
+            M[s] = cap;
+            count(sc, CNT_CAPPED);
+            if (flags) *flags |= FLAG_UNPHYSICAL;
+        }
+    }
+    R v[2], p[2];
+    int it[2];
+    newton_speed2<R, RCP>(sc, E, M, M2, seed, given, vac, v, p, it, flags);
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        if (vac[s]) {
+            q[s].vn = R(0); q[s].p = R(0); q[s].W = R(0); q[s].fe = R(0); vmag[s] = R(0);
+        } else {
+            vmag[s] = v[s];
+            q[s].vn = Mfull[s] > R(0) ? U[s].n * (v[s] / Mfull[s]) : R(0);
+            q[s].p = p[s];
+            q[s].W = E[s] + p[s];
+            q[s].fe = q[s].W * q[s].vn;
+        }
+    }
 }
 
 // Precision policy of a sweep: storage/flux type R and the cons->prim rule.
@@ -538,31 +703,69 @@ struct Physics {
             constexpr bool F32 = sizeof(R) == 4;
             Prim<R> q = c2p_table<R, EOSK == EOS_TABLE_MLP, F32>(U, K().delta, sc, sc.seed, R(0),
                                                                  vmag, &flags_);
-            if (PREC == PREC_MIXED) {
-                if (vmag > R(0.99)) {   // redo in double, seeded by the float root
-                    V4<double> D = v4<double>(U.e, U.n, U.t1, U.t2);
-                    double vd;
-                    Prim<double> qd = c2p_table<double, false>(D, DELTA_F64, sc, SEED_GIVEN,
-                                                        double(vmag), vd, &flags_);
-                    q.vn = R(qd.vn);
-                    q.p = R(qd.p);
-                    q.W = R(qd.W);
-                    q.fe = R(qd.fe);
-                    count(sc, CNT_F64_REDO);
-                }
-            }
+            if (PREC == PREC_MIXED) table_redo(U, vmag, q);
             return q;
+        }
+    }
+    // mixed precision, tabulated EOS: |v| > 0.99 is redone in double, seeded
+    // by the float root
+    __device__ __forceinline__ void table_redo(const V4<R> &U, R vmag, Prim<R> &q) const {
+        if (vmag > R(0.99)) {
+            V4<double> D = v4<double>(U.e, U.n, U.t1, U.t2);
+            double vd;
+            Prim<double> qd = c2p_table<double, false>(D, DELTA_F64, sc, SEED_GIVEN,
+                                                       double(vmag), vd, &flags_);
+            q.vn = R(qd.vn);
+            q.p = R(qd.p);
+            q.W = R(qd.W);
+            q.fe = R(qd.fe);
+            count(sc, CNT_F64_REDO);
+        }
+    }
+    // prim() of two states; with the tabulated EOS their Newton solves share
+    // one loop (c2p_table2), with the same results
+    __device__ __forceinline__ void prim2(const V4<R> &A, const V4<R> &B, Prim<R> &qa,
+                                          Prim<R> &qb) const {
+        if constexpr (EOSK == EOS_CONFORMAL) {
+            qa = prim(A);
+            qb = prim(B);
+        } else {
+            constexpr bool F32 = sizeof(R) == 4;
+            const V4<R> U[2] = {A, B};
+            Prim<R> q[2];
+            R vmag[2];
+            c2p_table2<R, EOSK == EOS_TABLE_MLP, F32>(U, K().delta, sc, sc.seed, q, vmag, &flags_);
+            if (PREC == PREC_MIXED) {
+                table_redo(A, vmag[0], q[0]);
+                table_redo(B, vmag[1], q[1]);
+            }
+            qa = q[0];
+            qb = q[1];
         }
     }
 
     // Eq. 3 along the sweep axis
-    __device__ __forceinline__ V flux(const V &U) const {
-        const V4<R> U4 = head(U);
-        const Prim<R> q = prim(U4);
-        // Eq. 3 along the axis: ((E + p) v_n, M_n v_n + p, M_t1 v_n, M_t2 v_n, R v_n)
+    __device__ __forceinline__ V flux(const V &U) const { return flux_of(U, prim(head(U))); }
+    // Eq. 3 along the axis from the primitives q of U:
+    // ((E + p) v_n, M_n v_n + p, M_t1 v_n, M_t2 v_n, R v_n)
+    __device__ __forceinline__ static V flux_of(const V &U, const Prim<R> &q) {
         R t1, t2;
-        tmul<R>(q.vn, U4, t1, t2);
+        tmul<R>(q.vn, head(U), t1, t2);
         return make(v4<R>(q.fe, fma_(U.n, q.vn, q.p), t1, t2), U, q.vn);
+    }
+    // flux() of two states (the pairs of Hancock faces and of MUSTA-FORCE
+    // interface states); with the tabulated EOS their cons->prim solves
+    // interleave (prim2)
+    __device__ __forceinline__ void flux2(const V &A, const V &B, V &FA, V &FB) const {
+        if constexpr (EOSK == EOS_CONFORMAL) {
+            FA = flux(A);
+            FB = flux(B);
+        } else {
+            Prim<R> qa, qb;
+            prim2(head(A), head(B), qa, qb);
+            FA = flux_of(A, qa);
+            FB = flux_of(B, qb);
+        }
     }
     // the four energy-momentum components, with the charge flux R v_n when carried
     __device__ __forceinline__ static V make(const V4<R> &f, const V &U, R vn) {
@@ -727,8 +930,7 @@ struct Physics {
                 FR = flux_uncapped(ur, capped);
                 if (capped) { FL = flux(ul); FR = flux(ur); }
             } else {
-                FL = flux(ul);
-                FR = flux(ur);
+                flux2(ul, ur, FL, FR);
             }
             const V d = vsub(FL, FR);
             const R hl = half * lam;
@@ -783,7 +985,13 @@ struct Physics {
         const int k = sc.stages;
 #pragma unroll 1
         for (int l = 0; l < k; ++l) {
-            const V FL = flux_g<UNCAPPED>(UL, capped), FR = flux_g<UNCAPPED>(UR, capped);
+            V FL, FR;
+            if constexpr (UNCAPPED) {
+                FL = flux_uncapped(UL, capped);
+                FR = flux_uncapped(UR, capped);
+            } else {
+                flux2(UL, UR, FL, FR);
+            }
             // F = 1/2 F_lw + 1/2 F_lf = 1/2 F_lw + 1/4 (F_L + F_R) - (clf/2) (U_R - U_L)
             const V Flf = vfma<R>(-hclf, vsub(UR, UL), vmul<R>(q4, vadd(FL, FR)));
             if (EOSK == EOS_CONFORMAL) {
