@@ -376,13 +376,43 @@ template <class R>
 __global__ void k_hotspots(const EventGeo *__restrict__ ev, const WorkItem *__restrict__ items,
                            int nitems, const double *__restrict__ spots, int nspots, double sigma,
                            double e_bg, R *__restrict__ U, Scheme sc, int nq) {
+    // the event's spots, converted to R once per block and event (a
+    // conversion from FP64 per cell and spot issues at the FP64 rate); larger
+    // spot lists are read from global memory
+    constexpr int HS_MAX = 28672 / int(7 * sizeof(R));
+    __shared__ R s_sp[7 * HS_MAX];
+    const bool staged = nspots <= HS_MAX;
+    int cur = -1;
     const R inv = R(1.0 / (2.0 * sigma * sigma));
     const R cut = R(9.0 * sigma);
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
         const WorkItem w = items[it];
         const EventGeo &g = ev[w.event];
         const double *sp = spots + (long long)w.event * nspots * 7;
+        if (staged && w.event != cur) {   // block-uniform
+            __syncthreads();              // the previous event's spots are no longer read
+            for (int j = threadIdx.x; j < 7 * nspots; j += blockDim.x) s_sp[j] = R(sp[j]);
+            __syncthreads();
+            cur = w.event;
+        }
         const int nx = g.n[0], ny = g.n[1];
+        // e, M of the cell at (px, py, pz) from spot component j of spot s
+        auto cell_sum = [&](R px, R py, R pz, auto get, R &e, R &mx, R &my, R &mz) {
+            for (int s = 0; s < nspots; ++s) {
+                const R dz = pz - get(s, 2);
+                if (fabs_(dz) > cut) continue;
+                const R dy = py - get(s, 1);
+                if (fabs_(dy) > cut) continue;
+                const R dx = px - get(s, 0);
+                if (fabs_(dx) > cut) continue;
+                // the separable Gaussian as one exponential of the summed squares
+                const R a = get(s, 3) * exp(-(dx * dx + dy * dy + dz * dz) * inv);
+                e += a;
+                mx += a * get(s, 4);
+                my += a * get(s, 5);
+                mz += a * get(s, 6);
+            }
+        };
         for (int k = threadIdx.x; k < w.count; k += blockDim.x) {
             const long long c = w.first + k;
             const int x = int(c % nx);
@@ -392,21 +422,10 @@ __global__ void k_hotspots(const EventGeo *__restrict__ ev, const WorkItem *__re
             const R py = R(g.lo[1] + (y + 0.5) * g.h[1]);
             const R pz = R(g.lo[2] + (z + 0.5) * g.h[2]);
             R e = R(e_bg), mx = R(0), my = R(0), mz = R(0);
-            for (int s = 0; s < nspots; ++s) {
-                const double *q = sp + 7 * s;
-                const R dz = pz - R(q[2]);
-                if (fabs_(dz) > cut) continue;
-                const R dy = py - R(q[1]);
-                if (fabs_(dy) > cut) continue;
-                const R dx = px - R(q[0]);
-                if (fabs_(dx) > cut) continue;
-                const R a = R(q[3]) * exp(-(dz * dz) * inv) * exp(-(dy * dy) * inv) *
-                            exp(-(dx * dx) * inv);
-                e += a;
-                mx += a * R(q[4]);
-                my += a * R(q[5]);
-                mz += a * R(q[6]);
-            }
+            if (staged)
+                cell_sum(px, py, pz, [&](int s, int j) { return s_sp[7 * s + j]; }, e, mx, my, mz);
+            else
+                cell_sum(px, py, pz, [&](int s, int j) { return R(sp[7 * s + j]); }, e, mx, my, mz);
             const R vx = mx / e, vy = my / e, vz = mz / e;
             R p, c2;
             eos_pc2<R>(sc, e, p, c2);
