@@ -75,6 +75,10 @@ struct Solver {
     // work lists
     std::vector<WorkItem> cell_items;
     WorkItem *d_cell_items = nullptr;
+    // the FP64 sums' work list: larger chunks, so that each thread adds many
+    // cells before the block reduction (FP64 adds issue slowly on this GPU)
+    std::vector<WorkItem> sum_items;
+    WorkItem *d_sum_items = nullptr;
     std::vector<WorkItem> sweep_items[3];
     WorkItem *d_sweep_items[3] = {nullptr, nullptr, nullptr};
     size_t sweep_cap[3] = {0, 0, 0};
@@ -140,13 +144,13 @@ struct Solver {
                         d_sweep_items[0], d_sweep_items[1], d_sweep_items[2], d_partial, d_sums,
                         d_p64, d_c64, d_p32, d_c32, d_mlp_f, d_mlp_w, d_counters, d_flags,
                         d_work_counter, d_ugeo, d_faces, d_stage[0], d_stage[1],
-                        d_us_face_items, d_us_tile_items};
+                        d_us_face_items, d_us_tile_items, d_sum_items};
         for (void *p : ptrs)
             if (p) cudaFree(p);
         d_geo = nullptr;
         d_clk = d_clk_tune = nullptr;
         d_state[0] = d_state[1] = nullptr;
-        d_cell_items = nullptr;
+        d_cell_items = d_sum_items = nullptr;
         for (int a = 0; a < 3; ++a) d_sweep_items[a] = nullptr;
         d_partial = d_sums = nullptr;
         d_p64 = d_c64 = nullptr;
@@ -387,7 +391,20 @@ struct Solver {
         CK(cudaMalloc(&d_cell_items, cell_items.size() * sizeof(WorkItem)));
         CK(cudaMemcpy(d_cell_items, cell_items.data(), cell_items.size() * sizeof(WorkItem),
                       cudaMemcpyHostToDevice));
-        CK(cudaMalloc(&d_partial, cell_items.size() * nq * sizeof(double)));
+        // sums work list: chunks of 32768 cells of one event (128 per thread)
+        const int schunk = 32768;
+        for (int e = 0; e < n; ++e)
+            for (long long c = 0; c < geo[e].cells; c += schunk) {
+                WorkItem w;
+                w.event = e;
+                w.first = c;
+                w.count = (int)std::min<long long>(schunk, geo[e].cells - c);
+                sum_items.push_back(w);
+            }
+        CK(cudaMalloc(&d_sum_items, sum_items.size() * sizeof(WorkItem)));
+        CK(cudaMemcpy(d_sum_items, sum_items.data(), sum_items.size() * sizeof(WorkItem),
+                      cudaMemcpyHostToDevice));
+        CK(cudaMalloc(&d_partial, sum_items.size() * nq * sizeof(double)));
         CK(cudaMalloc(&d_sums, (size_t)n * nq * sizeof(double)));
         if (n > 1) CK(cudaMalloc(&d_work_counter, sizeof(int)));
         if (unsplit) {
@@ -897,8 +914,11 @@ struct Solver {
     hydro_status sums(double *out, double *charge = nullptr) {
         if (charge && nq != 5) return fail(HYDRO_E_INVALID, "the handle carries no charge");
         CellLaunch c = cell_launch();
+        c.items = d_sum_items;
+        c.nitems = (int)sum_items.size();
+        c.blocks = (int)std::min<size_t>(sum_items.size(), (size_t)sms * 8);
         CK(launch_sums(c, d_state[cur], d_partial));
-        CK(launch_sums_final(d_cell_items, (int)cell_items.size(), d_partial, d_geo, d_sums,
+        CK(launch_sums_final(d_sum_items, (int)sum_items.size(), d_partial, d_geo, d_sums,
                              nevents, nq, stream));
         std::vector<double> h((size_t)nevents * nq);
         CK(cudaMemcpyAsync(h.data(), d_sums, h.size() * sizeof(double), cudaMemcpyDeviceToHost,

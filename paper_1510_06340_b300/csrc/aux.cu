@@ -4,6 +4,7 @@
 #include <cuda_bf16.h>
 
 #include "device.cuh"
+#include "widen.cuh"
 #include "kernels.h"
 
 namespace hy {
@@ -306,16 +307,18 @@ __global__ void k_sums(const EventGeo *__restrict__ ev, const WorkItem *__restri
         for (int k = threadIdx.x; k < w.count; k += blockDim.x) {
             const R *u = U + g.off + w.first + k;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) s[q] += double(u[q * g.cells]);
-            if (nq == 5) s[4] += double(u[4 * g.cells]);
+            for (int q = 0; q < 4; ++q) s[q] += widen(u[q * g.cells]);
+            if (nq == 5) s[4] += widen(u[4 * g.cells]);
         }
 #pragma unroll
-        for (int q = 0; q < 5; ++q)
+        for (int q = 0; q < 5; ++q) {
+            if (q == 4 && nq < 5) break;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) s[q] += __shfl_xor_sync(0xffffffffu, s[q], o);
+        }
         const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
         if (lane == 0)
-            for (int q = 0; q < 5; ++q) red[q][wid] = s[q];
+            for (int q = 0; q < nq; ++q) red[q][wid] = s[q];
         __syncthreads();
         if (int(threadIdx.x) < nq) {
             double t = 0.0;

@@ -14,6 +14,7 @@
 
 #include "../../include/hydro.h"
 #include "kernels.h"
+#include "widen.cuh"
 
 namespace {
 
@@ -40,7 +41,7 @@ k_na_partial(const R *__restrict__ U, long long cells, double *__restrict__ scra
     double s[4] = {0.0, 0.0, 0.0, 0.0};
     for (long long c = lo + threadIdx.x; c < hi; c += NA_THREADS)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) s[q] += double(U[q * cells + c]);
+        for (int q = 0; q < 4; ++q) s[q] += widen(U[q * cells + c]);
 #pragma unroll
     for (int q = 0; q < 4; ++q)
 #pragma unroll

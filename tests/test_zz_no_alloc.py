@@ -77,3 +77,33 @@ def test_noalloc_rejects_grids_over_its_limit_and_bad_cell_sizes(H):
     assert "limit" in H.lib().hydro_last_error().decode()
     assert _raw_call(H, U, 0, 2, 2, 1, 0.1, 0.0, 0.1) == 1
     assert _raw_call(H, U, 0, 2, 2, 1, float("nan"), 0.1, 0.1) == 1
+
+
+def test_fp32_sums_widen_every_float_class_exactly(H):
+    """The FP32 sums widen each value to FP64 from its bit layout. Values
+    spread over the whole normal exponent range, signed zeros and subnormals
+    must sum as their exact FP64 values do (math.fsum of the same doubles;
+    the kernel's own order differs, so the bound is a few ulps of the
+    summed magnitudes, and a subnormal, below 1.2e-38, is invisible at it);
+    an infinity and a NaN must come through."""
+    import math
+    import torch
+    rng = np.random.default_rng(11)
+    n = 4096
+    mant = rng.uniform(1.0, 2.0, size=(4, n))
+    expo = rng.integers(-126, 100, size=(4, n))
+    sign = rng.choice([-1.0, 1.0], size=(4, n))
+    U = (sign * np.ldexp(mant, expo)).astype(np.float32)
+    U[1, :8] = np.array([0.0, -0.0, 1e-40, -1e-41, 1.1754944e-38, -1.1754944e-38,
+                         3.4028235e38, -3.4028235e38], dtype=np.float32)
+    U[2, 5] = np.nan
+    U[3, 7] = np.inf
+    dev = torch.from_numpy(U.reshape(4, 1, 1, n)).cuda()
+    got = H.conservation_sums_noalloc(dev, "fp32", n, 1, 1, 1.0, 0.0, 0.0)
+    for q in (0, 1):
+        vals = U[q].astype(np.float64)
+        want = math.fsum(vals)
+        scale = float(np.abs(vals).sum())
+        assert abs(got[q] - want) <= 1e-14 * scale, (q, got[q], want)
+    assert math.isnan(got[2])
+    assert got[3] == math.inf
