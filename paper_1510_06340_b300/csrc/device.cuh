@@ -789,7 +789,10 @@ struct Physics {
         const R M2 = fma_(U.t2, U.t2, fma_(U.t1, U.t1, U.n * U.n));
         const R E2 = E * E;
         const R cap2 = k.capf * E2;
-        const R M2c = fmin_(M2, cap2);
+        // a state over the cap sends the group to the capped redo, so outside
+        // the mixed test below M^2 needs no clamp: where the cap does not act,
+        // min(M^2, cap^2) = M^2
+        const R M2c = PREC == PREC_MIXED ? fmin_(M2, cap2) : M2;
         const R W = fma_(k.hapc, E, dsqrt_(fma_(-k.cs2, M2c, k.hapc2 * E2)));
         const bool live = W > k.wmin;
         const R inv = live ? rcp_(W) : R(0);
