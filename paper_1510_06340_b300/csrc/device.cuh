@@ -777,8 +777,9 @@ struct Physics {
     // evaluations instead of per evaluation: the group runs without it and
     // only records whether any state exceeded the cap (one predicate-or per
     // evaluation); a lane that recorded one redoes the group with the capped
-    // flux.  Where the cap does not act the two give the same bits, so the
-    // results are those of flux() throughout.  Counting runs keep flux().
+    // flux; so does a lane that met a vacuum state (W <= wmin).  Where neither
+    // applies the two give the same bits, so the results are those of flux()
+    // throughout.  Counting runs keep flux().
     // The mixed sweeps group their FP64 redo the same way: a group is redone
     // through flux() where a state's FP32 recovery gives |v| > 0.99.
     static constexpr bool CAP_GROUPS = EOSK == EOS_CONFORMAL && !COUNT;
@@ -795,14 +796,17 @@ struct Physics {
         const R M2c = PREC == PREC_MIXED ? fmin_(M2, cap2) : M2;
         const R W = fma_(k.hapc, E, dsqrt_(fma_(-k.cs2, M2c, k.hapc2 * E2)));
         const bool live = W > k.wmin;
-        const R inv = live ? rcp_(W) : R(0);
-        R fe;
+        R fe, inv;
         if constexpr (PREC == PREC_MIXED) {   // c2p_conformal<R, false> and prim()'s test
+            inv = live ? rcp_(W) : R(0);
             fe = live ? U.n : R(0);
             capped = capped || M2c > R(0.9801) * W * W;
         } else {
+            // a vacuum state (W <= wmin) also sends the group to the redo,
+            // whose cons->prim guards it; here 1/W needs no guard
+            inv = rcp_(W);
             fe = U.n;
-            capped = capped || M2 > cap2;
+            capped = capped || M2 > cap2 || !live;
         }
         const R vn = U.n * inv;
         R t1, t2;
