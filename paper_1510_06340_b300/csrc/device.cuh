@@ -798,9 +798,10 @@ struct Physics {
         const bool live = W > k.wmin;
         R fe, inv;
         if constexpr (PREC == PREC_MIXED) {   // c2p_conformal<R, false> and prim()'s test
-            inv = live ? rcp_(W) : R(0);
-            fe = live ? U.n : R(0);
-            capped = capped || M2c > R(0.9801) * W * W;
+            // a vacuum state goes to the redo (as below)
+            inv = rcp_(W);
+            fe = U.n;
+            capped = capped || M2c > R(0.9801) * W * W || !live;
         } else {
             // a vacuum state (W <= wmin) also sends the group to the redo,
             // whose cons->prim guards it; here 1/W needs no guard
