@@ -1163,12 +1163,14 @@ __device__ __forceinline__ void march(const PH &ph, const Pencil<R, PH::kCharge>
     V nxt = P.load(wrap_index(js, N, bc));
     if constexpr (RK == 2) {
         // One loop body for every step: both engines push unchecked from t = 0
-        // on zero-initialised windows.  Their outputs before the windows fill
-        // (t < 4 for stage 1, t < 10 for stage 2) are never used or stored
-        // (zero states take the vacuum branch, so they stay finite); every
-        // stored cell is computed by the same instructions whatever the
-        // segment layout, so results do not depend on the launch shape.
-        const V zero = vzero<V>();
+        // on windows filled with a state at rest (E = 1, M = 0).  Their outputs
+        // before the windows fill (t < 4 for stage 1, t < 10 for stage 2) are
+        // never used or stored; every stored cell is
+        // computed by the same instructions whatever the segment layout, so
+        // results do not depend on the launch shape.  (A zero fill would be
+        // vacuum, which sends the grouped flux evaluations to their redo.)
+        V zero = vzero<V>();
+        zero.e = R(1);
         st1.w0 = st1.w1 = st1.w2 = st1.urp = st1.fp = zero;
         st2.w0 = st2.w1 = st2.w2 = st2.urp = st2.fp = zero;
         qa[0] = qa[1] = qa[2] = zero;
@@ -1209,7 +1211,7 @@ __device__ __forceinline__ void march(const PH &ph, const Pencil<R, PH::kCharge>
                 }
             }
             if (keep) P.store(o, r);
-            // the steps before the first finished cell run on zero-filled
+            // the steps before the first finished cell run on at-rest-filled
             // windows: what they met is not a state of the grid
             if (t < 10) ph.flags_ = 0;
         }
@@ -1217,10 +1219,12 @@ __device__ __forceinline__ void march(const PH &ph, const Pencil<R, PH::kCharge>
     }
     if constexpr (RK == 3) {
         // The same uniform loop for Eq. 7: three engines push from step 0 on
-        // zero-initialised windows; each stage reads the previous stage's
-        // output two cells behind its newest (the 2 ghost cells of a stage).
+        // windows filled with a state at rest (as for RK2); each stage reads
+        // the previous stage's output two cells behind its newest (the 2
+        // ghost cells of a stage).
         // Stage 1 outputs cell t+s0-8, stage 2 cell t+s0-12, stage 3 t+s0-16.
-        const V zero = vzero<V>();
+        V zero = vzero<V>();
+        zero.e = R(1);
         st1.w0 = st1.w1 = st1.w2 = st1.urp = st1.fp = zero;
         st2.w0 = st2.w1 = st2.w2 = st2.urp = st2.fp = zero;
         st3.w0 = st3.w1 = st3.w2 = st3.urp = st3.fp = zero;
@@ -1275,7 +1279,7 @@ __device__ __forceinline__ void march(const PH &ph, const Pencil<R, PH::kCharge>
                 }
             }
             if (keep) P.store(o, r);
-            if (t < 16) ph.flags_ = 0;   // zero-filled windows (as for RK2)
+            if (t < 16) ph.flags_ = 0;   // windows not yet filled (as for RK2)
         }
         return;
     }
@@ -1468,7 +1472,7 @@ struct XStage {
 };
 
 // RK2 march of x-rows through the warp's shared-memory rings; the same
-// arithmetic, schedule and zero start as march() (Eq. 6), so stored cells
+// arithmetic, schedule and at-rest start as march() (Eq. 6), so stored cells
 // are bit-identical to it.  The whole warp must call it together.
 template <class R, bool RATE, class PH>
 __device__ __forceinline__ void march_x_rk2(const PH &ph, XStage<R, PH::kCharge> &X, int s0, int L,
@@ -1490,7 +1494,8 @@ __device__ __forceinline__ void march_x_rk2(const PH &ph, XStage<R, PH::kCharge>
     const int psi = (13 - js0) & 7;
     const int tf = phi == 0 ? 8 : phi;   // first fill step
     Stage<V> st1, st2;
-    const V zero = vzero<V>();
+    V zero = vzero<V>();   // windows start at rest (as in march)
+    zero.e = R(1);
     st1.w0 = st1.w1 = st1.w2 = st1.urp = st1.fp = zero;
     st2.w0 = st2.w1 = st2.w2 = st2.urp = st2.fp = zero;
     V qa[3] = {zero, zero, zero};
@@ -1524,7 +1529,7 @@ __device__ __forceinline__ void march_x_rk2(const PH &ph, XStage<R, PH::kCharge>
         const bool kp = do_store && o >= s0 && o < s_end;
         X.put(t, r);
         keep |= (kp ? 1u : 0u) << (t & 7);
-        if (t < 10) ph.flags_ = 0;   // zero-filled windows (as in march)
+        if (t < 10) ph.flags_ = 0;   // windows not yet filled (as in march)
         if (((t - psi) & 7) == 0 || t == T - 1) {
             __syncwarp();
             X.template flush<RATE>(t, keep, ph, ra, rate_on);
