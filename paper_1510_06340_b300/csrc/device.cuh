@@ -783,6 +783,10 @@ struct Physics {
     // The mixed sweeps group their FP64 redo the same way: a group is redone
     // through flux() where a state's FP32 recovery gives |v| > 0.99.
     static constexpr bool CAP_GROUPS = EOSK == EOS_CONFORMAL && !COUNT;
+    // The kernels with the limiter fixed at compile time are launched only
+    // with the Hancock step on and, where MUSTA2 writes out two stages, with
+    // k = 2; their loop tests neither.
+    static constexpr bool FIXED = LIM >= 0;
 
     __device__ __forceinline__ V flux_uncapped(const V &U, bool &capped) const {
         const SchemeConsts<R> &k = K();
@@ -930,7 +934,7 @@ struct Physics {
         else sl = sl4;
         ul = vfma<R>(-half, sl, v0);
         ur = vfma<R>(half, sl, v0);
-        if (sc.hancock) {
+        if (FIXED || sc.hancock) {
             V FL, FR;
             if constexpr (CAP_GROUPS) {
                 bool capped = false;
@@ -957,7 +961,7 @@ struct Physics {
         bool capped = false;
         if constexpr (CAP_GROUPS) {
             V F;
-            if (MUSTA2 && sc.stages == 2) {
+            if (MUSTA2 && (FIXED || sc.stages == 2)) {
                 // two stages written out, so that the predicted states take
                 // fresh registers while the inputs stay for a redo
                 V FL, FR;

@@ -235,9 +235,11 @@ cudaError_t launch_sweep_prec(const SweepLaunch &a) {
         }
         return cudaErrorInvalidValue;
     }
-    // specialised kernels (limiter fixed at compile time, no counters) for the
-    // conformal RK2 scheme; everything else takes the runtime-limiter kernel
-    if (a.sc.eos_kind == EOS_CONFORMAL && a.rk == 2 && !a.sc.counters) {
+    // specialised kernels (limiter fixed at compile time, no counters, the
+    // Hancock step on; with two MUSTA stages for the conformal RK2 scheme);
+    // everything else takes the runtime-limiter kernel
+    if (a.sc.eos_kind == EOS_CONFORMAL && a.rk == 2 && !a.sc.counters && a.sc.hancock &&
+        a.sc.stages == 2) {
         // the CFL rate is compiled in only for the last sweep of a step
         if (a.rate_clk) {
             switch (a.sc.limiter) {
@@ -258,14 +260,14 @@ cudaError_t launch_sweep_prec(const SweepLaunch &a) {
         }
     }
     // the paper's production settings (RK3), Minbee specialised
-    if (a.sc.eos_kind == EOS_CONFORMAL && a.rk == 3 && !a.sc.counters &&
+    if (a.sc.eos_kind == EOS_CONFORMAL && a.rk == 3 && !a.sc.counters && a.sc.hancock &&
         a.sc.limiter == LIM_MINMOD) {
         if (a.rate_clk) HY_SWEEP(EOS_CONFORMAL, 3, LIM_MINMOD, false, true)
         else HY_SWEEP(EOS_CONFORMAL, 3, LIM_MINMOD, false, false)
     }
     // tabulated EOS: Minbee RK2 specialised (plain Newton seeds, or the MLP seed)
     const bool mlp = a.sc.eos_kind == EOS_TABLE && a.sc.seed == SEED_MLP;
-    if (a.sc.eos_kind == EOS_TABLE && a.rk == 2 && !a.sc.counters &&
+    if (a.sc.eos_kind == EOS_TABLE && a.rk == 2 && !a.sc.counters && a.sc.hancock &&
         a.sc.limiter == LIM_MINMOD) {
         if (mlp) {
             if (a.rate_clk) HY_SWEEP(EOS_TABLE_MLP, 2, LIM_MINMOD, false, true)
