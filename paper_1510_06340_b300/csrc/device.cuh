@@ -783,10 +783,12 @@ struct Physics {
     // The mixed sweeps group their FP64 redo the same way: a group is redone
     // through flux() where a state's FP32 recovery gives |v| > 0.99.
     static constexpr bool CAP_GROUPS = EOSK == EOS_CONFORMAL && !COUNT;
-    // The kernels with the limiter fixed at compile time are launched only
-    // with the Hancock step on and, where MUSTA2 writes out two stages, with
-    // k = 2; their loop tests neither.
-    static constexpr bool FIXED = LIM >= 0;
+    // The RK2 kernels with the limiter fixed at compile time are launched
+    // only with the Hancock step on and, where the MUSTA-FORCE stages are
+    // written out (conformal EOS), with k = 2; their loop tests neither.  (The
+    // register-capped RK3 kernels keep the tests: without the branch their
+    // schedule spills.)
+    static constexpr bool FIXED = LIM >= 0 && MUSTA2;
 
     __device__ __forceinline__ V flux_uncapped(const V &U, bool &capped) const {
         const SchemeConsts<R> &k = K();

@@ -260,7 +260,7 @@ cudaError_t launch_sweep_prec(const SweepLaunch &a) {
         }
     }
     // the paper's production settings (RK3), Minbee specialised
-    if (a.sc.eos_kind == EOS_CONFORMAL && a.rk == 3 && !a.sc.counters && a.sc.hancock &&
+    if (a.sc.eos_kind == EOS_CONFORMAL && a.rk == 3 && !a.sc.counters &&
         a.sc.limiter == LIM_MINMOD) {
         if (a.rate_clk) HY_SWEEP(EOS_CONFORMAL, 3, LIM_MINMOD, false, true)
         else HY_SWEEP(EOS_CONFORMAL, 3, LIM_MINMOD, false, false)
