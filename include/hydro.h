@@ -337,6 +337,18 @@ hydro_status hydro_mlp_seed_emin(hydro_t *h, double *emin);
  * no-op. */
 hydro_status hydro_c2p_newton(hydro_t *h, const void *U, int n, int seed, void *vmag,
                               int *iters);
+/* A check of the tabulated-EOS sweeps' paired Newton solve (Sec. 2.6 with the
+ * table of reading R11): two states' solves share one loop there and must
+ * give what two single solves give.  U [4][n] (handle dtype, device), n even:
+ * state i is paired with state i + n/2.  Outputs (device): vmag and p
+ * [2][n] (handle dtype) and iters [2][n] (int) -- row 0 from single solves,
+ * row 1 from the paired solve, with the handle's EOS, Newton iteration cap and
+ * tolerance; E <= 0 gives zeros.  seed: HYDRO_SEED_ZERO or
+ * HYDRO_SEED_CONFORMAL; rcp != 0 takes 1/W and 1/f' as reciprocals (the
+ * FP32 sweeps' form), 0 divides.  n = 0 is a no-op; an odd n, a missing
+ * pointer or a handle without a table EOS is HYDRO_E_INVALID. */
+hydro_status hydro_c2p_newton_pairs(hydro_t *h, const void *U, int n, int seed, int rcp,
+                                    void *vmag, void *p, int *iters);
 
 #ifdef __cplusplus
 }

@@ -1314,6 +1314,20 @@ hydro_status hydro_c2p_newton(hydro_t *h, const void *U, int n, int seed, void *
     CK(cudaStreamSynchronize(h->s.stream));
     return HYDRO_OK;
 }
+hydro_status hydro_c2p_newton_pairs(hydro_t *h, const void *U, int n, int seed, int rcp,
+                                    void *vmag, void *p, int *iters) {
+    HANDLE(h);
+    if (n == 0) return HYDRO_OK;
+    if (!U || !vmag || !p || !iters || n < 0 || n % 2)
+        return fail(HYDRO_E_INVALID, "bad argument (n must be even)");
+    if (h->s.sc.eos_kind != HYDRO_EOS_TABLE) return fail(HYDRO_E_INVALID, "needs a table EOS");
+    if (seed != HYDRO_SEED_ZERO && seed != HYDRO_SEED_CONFORMAL)
+        return fail(HYDRO_E_INVALID, "seed must be zero or conformal");
+    CK(launch_c2p_newton_pairs(h->s.prec == HYDRO_FP64 ? 0 : 1, h->s.scheme(), U, n, seed,
+                               rcp ? 1 : 0, vmag, p, iters, h->s.stream));
+    CK(cudaStreamSynchronize(h->s.stream));
+    return HYDRO_OK;
+}
 
 // ---------------------------------------------------------------- batch
 hydro_status hydro_batch_create(const hydro_grid_t *grids, int nevents, const hydro_eos_t *eos,

@@ -479,6 +479,54 @@ __global__ void k_c2p_newton(Scheme sc, const R *__restrict__ U, long long n, in
     iters[i] = it;
 }
 
+// The paired Newton solve of the tabulated-EOS sweeps (newton_speed2) beside
+// two single solves (newton_speed) of the same states, for checking that the
+// pair changes nothing: thread i takes states i and i + n/2 (n even) and
+// writes |v|, p and the iteration count of the single solves to [0][.] and
+// of the paired one to [1][.]; E <= 0 gives zeros (the vacuum of c2p_table).
+template <class R, bool RCP>
+__global__ void k_c2p_newton_pairs(Scheme sc, const R *__restrict__ U, long long n, int seed,
+                                   R *__restrict__ vmag, R *__restrict__ pres,
+                                   int *__restrict__ iters) {
+    const long long h = n / 2;
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= h) return;
+    R E[2], M[2], M2[2], given[2] = {R(0), R(0)};
+    bool skip[2];
+    int sd[2] = {seed, seed};
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        const long long c = i + s * h;
+        E[s] = U[c];
+        const R mx = U[n + c], my = U[2 * n + c], mz = U[3 * n + c];
+        M2[s] = mx * mx + my * my + mz * mz;
+        skip[s] = !(E[s] > R(0));
+        const R cap = (R(1) - R(sc.delta)) * E[s];
+        if (M2[s] > cap * cap) M2[s] = cap * cap;
+        M[s] = dsqrt_(M2[s]);
+    }
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        const long long c = i + s * h;
+        R p = R(0), v = R(0);
+        int it = 0;
+        if (!skip[s]) v = newton_speed<R, RCP>(sc, E[s], M[s], M2[s], seed, R(0), p, it);
+        vmag[c] = v;
+        pres[c] = p;
+        iters[c] = it;
+    }
+    R v[2], p[2];
+    int it[2];
+    newton_speed2<R, RCP>(sc, E, M, M2, sd, given, skip, v, p, it);
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        const long long c = n + i + s * h;
+        vmag[c] = skip[s] ? R(0) : v[s];
+        pres[c] = skip[s] ? R(0) : p[s];
+        iters[c] = skip[s] ? 0 : it[s];
+    }
+}
+
 // ------------------------------------------------------------------ launchers
 #define HY_DISPATCH(prec, call_d, call_f) \
     do {                                  \
@@ -575,6 +623,27 @@ cudaError_t launch_finite(const CellLaunch &c, const void *U, EventClock *clk) {
             (const double *)U, clk, c.nq)),
         (k_finite<float><<<c.blocks, c.threads, 0, c.stream>>>(c.ev, c.items, c.nitems,
             (const float *)U, clk, c.nq)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_c2p_newton_pairs(int prec, const Scheme &sc, const void *U, long long n,
+                                    int seed, int rcp, void *vmag, void *pres, int *iters,
+                                    cudaStream_t s) {
+    const long long h = n / 2;
+    if (h <= 0) return cudaSuccess;
+    const int th = 128;
+    const unsigned bl = (unsigned)((h + th - 1) / th);
+#define HY_PAIRS(R, RCP)                                                                      \
+    k_c2p_newton_pairs<R, RCP><<<bl, th, 0, s>>>(sc, (const R *)U, n, seed, (R *)vmag,        \
+                                                 (R *)pres, iters)
+    if (prec == 0) {
+        if (rcp) HY_PAIRS(double, true);
+        else HY_PAIRS(double, false);
+    } else {
+        if (rcp) HY_PAIRS(float, true);
+        else HY_PAIRS(float, false);
+    }
+#undef HY_PAIRS
     return cudaGetLastError();
 }
 

@@ -91,6 +91,9 @@ cudaError_t launch_sums_final(const WorkItem *items, int nitems, const double *p
 cudaError_t launch_hotspots(const CellLaunch &c, const double *spots, int nspots, double sigma,
                             double e_bg, void *U);
 cudaError_t launch_finite(const CellLaunch &c, const void *U, EventClock *clk);
+cudaError_t launch_c2p_newton_pairs(int prec, const Scheme &sc, const void *U, long long n,
+                                    int seed, int rcp, void *vmag, void *pres, int *iters,
+                                    cudaStream_t s);
 cudaError_t launch_c2p_newton(int prec, const Scheme &sc, const void *U, long long n, int seed,
                               void *vmag, int *iters, cudaStream_t s);
 

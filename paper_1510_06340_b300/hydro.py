@@ -93,6 +93,7 @@ def lib():
             "hydro_batch_get_kernel_timing": [H, dp, C.POINTER(C.c_longlong)],
             "hydro_get_launch": [H, i, ip, ip],
             "hydro_c2p_newton": [H, vp, i, i, vp, vp],
+            "hydro_c2p_newton_pairs": [H, vp, i, i, i, vp, vp, vp],
             "hydro_mlp_seed_emin": [H, dp],
             "hydro_batch_create": [C.POINTER(GridT), i, C.POINTER(EosT), i, i, C.POINTER(H)],
             "hydro_batch_set_stream": [H, vp],
@@ -424,6 +425,18 @@ class Hydro(_Base):
         pi = _dev(iters, np.int32, n, "iters")
         _check(lib().hydro_c2p_newton(self.h, pU, n,
                                       SEEDS[seed] if isinstance(seed, str) else seed, pv, pi))
+
+    def c2p_newton_pairs(self, U, seed, rcp, vmag, p, iters):
+        """Device tensors: U [4][n] (n even), vmag and p [2][n] (handle dtype),
+        iters [2][n] int32; row 0 single solves, row 1 the paired solve."""
+        n = U.shape[-1]
+        pU = _dev(U, self._dtype, 4 * n, "U")
+        pv = _dev(vmag, self._dtype, 2 * n, "vmag")
+        pp = _dev(p, self._dtype, 2 * n, "p")
+        pi = _dev(iters, np.int32, 2 * n, "iters")
+        _check(lib().hydro_c2p_newton_pairs(self.h, pU, n,
+                                            SEEDS[seed] if isinstance(seed, str) else seed,
+                                            int(rcp), pv, pp, pi))
 
 
 class Batch(_Base):

@@ -339,6 +339,53 @@ def test_table_eos_fp64(H, seed):
     check(h, U, "fp64")
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("max_iter", [0, 1])
+def test_paired_newton_solves_equal_single_solves(H, prec, max_iter):
+    """The tabulated-EOS sweeps run the cons->prim Newton solves of two flux
+    evaluations in one loop; each state must get the |v|, p and iteration
+    count of its own solve, bit for bit: both seeds, both reciprocal forms,
+    states below, inside and above the table, at rest, at the |M| cap and in
+    vacuum, with the default iteration cap and with a cap of one that leaves
+    most solves unconverged. The single solves with divisions must also be
+    those of hydro_c2p_newton."""
+    import torch
+    tab = I.eos_table()
+    grid = H.make_grid(4, 4, 4, dx=0.1, prec=prec)
+    h = H.Hydro(grid, H.make_eos(tab, newton_max_iter=max_iter))
+    rng = np.random.default_rng(21)
+    n = 4096
+    E = np.exp(rng.uniform(np.log(1e-7), np.log(1e5), n))
+    x = rng.uniform(0.0, 0.9999, n)
+    d = rng.normal(size=(3, n))
+    d /= np.linalg.norm(d, axis=0)
+    E[:4] = [0.0, -1.0, 1e-30, 1e-12]
+    x[8:24] = 0.0
+    x[24:40] = 1.0
+    U = np.stack([E, *(x * E * d)]).astype(h.dtype)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    Ut = torch.from_numpy(U).cuda()
+    bits = torch.int64 if prec == "fp64" else torch.int32
+    for seed in ("zero", "conformal"):
+        for rcp in (0, 1):
+            v = torch.zeros((2, n), dtype=dt, device="cuda")
+            p = torch.zeros((2, n), dtype=dt, device="cuda")
+            it = torch.zeros((2, n), dtype=torch.int32, device="cuda")
+            h.c2p_newton_pairs(Ut, seed, rcp, v, p, it)
+            assert torch.equal(v[0].view(bits), v[1].view(bits)), (seed, rcp)
+            assert torch.equal(p[0].view(bits), p[1].view(bits)), (seed, rcp)
+            assert torch.equal(it[0], it[1]), (seed, rcp)
+            assert torch.isfinite(v).all() and torch.isfinite(p).all()
+            if max_iter == 1:
+                assert int((it[0] == 1).sum()) > n // 2
+            if rcp == 0:
+                vs = torch.zeros(n, dtype=dt, device="cuda")
+                its = torch.zeros(n, dtype=torch.int32, device="cuda")
+                h.c2p_newton(Ut, seed, vs, its)
+                assert torch.equal(vs.view(bits), v[0].view(bits))
+                assert torch.equal(its, it[0])
+
+
 def test_table_eos_fp32(H):
     tab = I.eos_table()
     g = I.event_grid(16, 0.1)
