@@ -5,9 +5,9 @@ baseline leg of ``bench.py`` are the only callers.  Nothing here imports the
 CUDA package; the oracle shares no code with it.  Arithmetic lives in the C
 file; this module only marshals numpy arrays through ctypes.
 
-Parity unpinned: the MLP seed used inside the Newton solve (it only changes
-the iteration count, never the converged root; its gradients are pinned by
-finite differences in the tests).
+Every function here is pinned by a CPU test; the MLP forward pass through
+special cases that reduce to matrix products, its gradient by finite
+differences.
 """
 from __future__ import annotations
 

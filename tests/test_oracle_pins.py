@@ -509,6 +509,62 @@ def test_mlp_gradient_matches_finite_differences():
     assert not G[-4:].any()
 
 
+def _mlp_pack(W1, b1, W2, b2, W3, b3, nrm):
+    """Parameters in the network's layout: W1[32][2] b1 W2[32][32] b2 W3 b3 mu0 s0 mu1 s1."""
+    return np.concatenate([W1.ravel(), b1, W2.ravel(), b2, W3, [b3], nrm])
+
+
+def _conformal_root(x):
+    """|v| of the p = e/3 state with |M|/E = x: for that EOS x = 4v / (3 + v^2),
+    so v is the root in [0, 1] of x v^2 - 4 v + 3 x = 0 (library polynomial roots)."""
+    out = []
+    for xi in x:
+        r = np.roots([xi, -4.0, 3.0 * xi]) if xi > 0 else np.array([0.0])
+        out.append(min(float(np.real(t)) for t in r if -1e-12 <= np.real(t) <= 1.0 + 1e-12))
+    return np.array(out)
+
+
+def test_mlp_forward_reduces_to_matrix_products():
+    """The Newton seed network's forward pass (FP64, unquantised) pinned to
+    special cases that a matrix product gives: with the weights of layers 1
+    and 2 zero it is v0 = vc + (x - vc) sigmoid(W3 . tanh(b2) + b3) exactly;
+    with zero biases and layer-1 and layer-2 weights scaled by 1e-3, tanh and
+    the sigmoid linearise and 4 (v0 - (vc + x) / 2) / (x - vc) = 1e-6 W3 . (B (A s))
+    to a relative O(1e-6), s the standardised inputs; with layer 1 zero, the
+    same with tanh(b1) for A s.  vc, the closed-form p = e/3 root, comes from
+    the polynomial its defining relation gives.  A transposed weight matrix,
+    a wrong parameter offset, a dropped bias or a wrong standardisation fails
+    one of them."""
+    H = 32
+    rng = np.random.default_rng(41)
+    nrm = np.array([0.7, 2.5, 0.45, 0.3])
+    n = 64
+    X = np.column_stack([rng.uniform(-6, 6, n), rng.uniform(0.2, 0.95, n)])
+    x = X[:, 1]
+    s = np.column_stack([(X[:, 0] - nrm[0]) / nrm[1], (x - nrm[2]) / nrm[3]])
+    vc = _conformal_root(x)
+    np.testing.assert_allclose(4 * vc / (3 + vc * vc), x, rtol=1e-14)
+    b1, b2, W3 = rng.normal(size=H), rng.normal(size=H), rng.normal(size=H)
+    A, B = rng.normal(size=(H, 2)), rng.normal(size=(H, H))
+    # layers 1 and 2 without weights: exact
+    b3 = 0.37
+    P = _mlp_pack(np.zeros((H, 2)), b1, np.zeros((H, H)), b2, W3, b3, nrm)
+    z = W3 @ np.tanh(b2) + b3
+    want = vc + (x - vc) / (1.0 + np.exp(-z))
+    np.testing.assert_allclose(O.mlp_forward(P, X), want, rtol=1e-13, atol=1e-15)
+    # zero biases, small weights: the linearised product W3 B A s
+    eps = 1e-3
+    P = _mlp_pack(eps * A, np.zeros(H), eps * B, np.zeros(H), W3, 0.0, nrm)
+    zl = eps * eps * (s @ A.T @ B.T @ W3)
+    got = 4.0 * (O.mlp_forward(P, X) - 0.5 * (vc + x)) / (x - vc)
+    np.testing.assert_allclose(got, zl, rtol=1e-4, atol=1e-12)
+    # layer 1 without weights: its output tanh(b1) through the linearised rest
+    P = _mlp_pack(np.zeros((H, 2)), b1, eps * B, np.zeros(H), W3, 0.0, nrm)
+    zb = eps * (W3 @ (B @ np.tanh(b1)))
+    got = 4.0 * (O.mlp_forward(P, X) - 0.5 * (vc + x)) / (x - vc)
+    np.testing.assert_allclose(got, np.full(n, zb), rtol=1e-4)
+
+
 def test_round_bf16_matches_library_conversion():
     import torch
     x = RNG.normal(size=2000) * 10.0 ** RNG.uniform(-10, 10, size=2000)
