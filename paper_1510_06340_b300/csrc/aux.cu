@@ -13,8 +13,9 @@ namespace hy {
 template <class R>
 __device__ __forceinline__ void eos_pc2(const Scheme &sc, R e, R &p, R &c2) {
     if (sc.eos_kind == EOS_CONFORMAL) {
-        p = R(sc.cs2) * e;
-        c2 = R(sc.cs2);
+        // the scheme's constants in precision R (no FP64 conversion per cell)
+        p = consts<R>(sc).cs2 * e;
+        c2 = consts<R>(sc).cs2;
     } else {
         eos_table<R>(sc, e, p, c2);
     }
@@ -25,7 +26,7 @@ template <class R>
 __device__ __forceinline__ void c2p_full(const Scheme &sc, R E, R Mx, R My, R Mz, R &e, R &vx,
                                          R &vy, R &vz, int &iters) {
     iters = 0;
-    const R delta = R(sc.delta);
+    const R delta = consts<R>(sc).delta;
     R M2 = Mx * Mx + My * My + Mz * Mz;
     if (!(E > consts<R>(sc).emin)) { e = R(0); vx = vy = vz = R(0); return; }   // vacuum (R18)
     const R cap = (R(1) - delta) * E;
@@ -35,7 +36,7 @@ __device__ __forceinline__ void c2p_full(const Scheme &sc, R E, R Mx, R My, R Mz
         M2 = cap * cap;
     }
     if (sc.eos_kind == EOS_CONFORMAL) {
-        const R cs2 = R(sc.cs2);
+        const R cs2 = consts<R>(sc).cs2;
         const R a = (R(1) + cs2) * E;
         R disc = a * a - R(4) * cs2 * M2;
         disc = disc < R(0) ? R(0) : disc;
@@ -238,6 +239,7 @@ __global__ void k_jet(const EventGeo *__restrict__ ev, R *__restrict__ U,
     struct JetBox {
         int lo[3], B[3];
         R amp, cx, cy, cz, inv2s2, cut2, nx, ny, nz;
+        R x0[3], h[3];   // grid origin and spacing in precision R
         int on;
     };
     __shared__ JetBox jb;
@@ -269,20 +271,26 @@ __global__ void k_jet(const EventGeo *__restrict__ ev, R *__restrict__ U,
             jb.inv2s2 = R(1.0 / (2.0 * sig * sig));
             jb.cut2 = R(81.0 * sig * sig);
             jb.nx = R(j[3]); jb.ny = R(j[4]); jb.nz = R(j[5]);
+            for (int d = 0; d < 3; ++d) {
+                jb.x0[d] = R(g.lo[d]);
+                jb.h[d] = R(g.h[d]);
+            }
         }
     }
     __syncthreads();
     if (!jb.on) return;
-    const int B0 = jb.B[0], B1 = jb.B[1];
-    const long long total = (long long)B0 * B1 * jb.B[2];
-    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < total;
-         k += (long long)gridDim.x * blockDim.x) {
-        const int x = jb.lo[0] + int(k % B0);
-        const int y = jb.lo[1] + int((k / B0) % B1);
-        const int z = jb.lo[2] + int(k / ((long long)B0 * B1));
-        const R px = R(g.lo[0]) + (R(x) + R(0.5)) * R(g.h[0]) - jb.cx;
-        const R py = R(g.lo[1]) + (R(y) + R(0.5)) * R(g.h[1]) - jb.cy;
-        const R pz = R(g.lo[2]) + (R(z) + R(0.5)) * R(g.h[2]) - jb.cz;
+    // the box lies in one event (nq cells < 2^31): 32-bit index arithmetic
+    const unsigned B0 = unsigned(jb.B[0]), B1 = unsigned(jb.B[1]);
+    const unsigned total = B0 * B1 * unsigned(jb.B[2]);
+    for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < total;
+         k += gridDim.x * blockDim.x) {
+        const unsigned q = k / B0;
+        const int x = jb.lo[0] + int(k - q * B0);
+        const int y = jb.lo[1] + int(q % B1);
+        const int z = jb.lo[2] + int(q / B1);
+        const R px = jb.x0[0] + (R(x) + R(0.5)) * jb.h[0] - jb.cx;
+        const R py = jb.x0[1] + (R(y) + R(0.5)) * jb.h[1] - jb.cy;
+        const R pz = jb.x0[2] + (R(z) + R(0.5)) * jb.h[2] - jb.cz;
         const R r2 = px * px + py * py + pz * pz;
         if (r2 > jb.cut2) continue;
         const R s = jb.amp * exp(-r2 * jb.inv2s2);
@@ -418,9 +426,11 @@ __global__ void k_hotspots(const EventGeo *__restrict__ ev, const WorkItem *__re
         };
         for (int k = threadIdx.x; k < w.count; k += blockDim.x) {
             const long long c = w.first + k;
-            const int x = int(c % nx);
-            const int y = int((c / nx) % ny);
-            const int z = int(c / ((long long)nx * ny));
+            // an event has fewer than 2^31 cells: 32-bit index arithmetic
+            const unsigned cu = unsigned(c), q = cu / unsigned(nx);
+            const int x = int(cu - q * unsigned(nx));
+            const int y = int(q % unsigned(ny));
+            const int z = int(q / unsigned(ny));
             const R px = R(g.lo[0] + (x + 0.5) * g.h[0]);
             const R py = R(g.lo[1] + (y + 0.5) * g.h[1]);
             const R pz = R(g.lo[2] + (z + 0.5) * g.h[2]);
@@ -470,7 +480,7 @@ __global__ void k_c2p_newton(Scheme sc, const R *__restrict__ U, long long n, in
     const R E = U[i], Mx = U[n + i], My = U[2 * n + i], Mz = U[3 * n + i];
     R M2 = Mx * Mx + My * My + Mz * Mz;
     if (!(E > R(0))) { vmag[i] = R(0); iters[i] = 0; return; }
-    const R cap = (R(1) - R(sc.delta)) * E;
+    const R cap = (R(1) - consts<R>(sc).delta) * E;
     if (M2 > cap * cap) M2 = cap * cap;
     const R M = dsqrt_(M2);
     R p;
@@ -501,7 +511,7 @@ __global__ void k_c2p_newton_pairs(Scheme sc, const R *__restrict__ U, long long
         const R mx = U[n + c], my = U[2 * n + c], mz = U[3 * n + c];
         M2[s] = mx * mx + my * my + mz * mz;
         skip[s] = !(E[s] > R(0));
-        const R cap = (R(1) - R(sc.delta)) * E[s];
+        const R cap = (R(1) - consts<R>(sc).delta) * E[s];
         if (M2[s] > cap * cap) M2[s] = cap * cap;
         M[s] = dsqrt_(M2[s]);
     }
