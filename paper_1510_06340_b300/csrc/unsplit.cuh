@@ -324,7 +324,7 @@ k_us_tile(const R *__restrict__ faces, const R *__restrict__ u0, const R *__rest
         report_flags(sc, w.event, ph.flags_);
         // per cell of the tile: dt L(U) = -D, D = sum_d dt/dx_d (F_d,i+1/2 -
         // F_d,i-1/2) with the axes in order, then the RK stage combination of
-        // Eq. 5-7 (as k_us_update)
+        // Eq. 5-7
         UsDiv de0, de1;
         de0.init(E[0]);
         de1.init(E[1]);
