@@ -942,7 +942,9 @@ struct Physics {
                 bool capped = false;
                 FL = flux_uncapped(ul, capped);
                 FR = flux_uncapped(ur, capped);
-                if (capped) { FL = flux(ul); FR = flux(ur); }
+                // the warp redoes the group together (a warp-uniform branch):
+                // lanes that met no cap or vacuum get the same bits again
+                if (__any_sync(0xffffffffu, capped)) { FL = flux(ul); FR = flux(ur); }
             } else {
                 flux2(ul, ur, FL, FR);
             }
@@ -974,7 +976,7 @@ struct Physics {
             } else {
                 F = musta_g<true>(UL, UR, lam, capped);
             }
-            if (!capped) return F;
+            if (!__any_sync(0xffffffffu, capped)) return F;   // warp-uniform, as in faces()
         }
         return musta_g<false>(UL, UR, lam, capped);
     }
