@@ -68,7 +68,7 @@ def flops_per_cell_sweep(rk=2, stages=2, limiter="minmod"):
 # the two stages of a step), from ncu captures of the current kernels (the
 # sweep and unsplit profile summaries under profiles/); None where no capture
 # of the current kernels exists
-SWEEP_TRAFFIC = {(256, "fp32", 2, 2, False): 595.9e6,
+SWEEP_TRAFFIC = {(256, "fp32", 2, 2, False): 595.2e6,
                  (256, "fp32", 2, 2, True): 5032.0e6}
 # the event batch (FP32, minmod, k = 2, RK2): DRAM bytes per cell and sweep
 # launch, the mean over one step's five sweeps of an ncu capture of 64 events
