@@ -776,10 +776,11 @@ struct Physics {
     // The conformal FP32/FP64 sweeps take the |M| cap (R9) per group of flux
     // evaluations instead of per evaluation: the group runs without it and
     // only records whether any state exceeded the cap (one predicate-or per
-    // evaluation); a lane that recorded one redoes the group with the capped
-    // flux; so does a lane that met a vacuum state (W <= wmin).  Where neither
-    // applies the two give the same bits, so the results are those of flux()
-    // throughout.  Counting runs keep flux().
+    // evaluation); where a lane of the warp recorded one, the warp redoes the
+    // group with the capped flux (a warp-uniform branch); so it does where a
+    // lane met a vacuum state (W <= wmin).  Where neither applies the two give
+    // the same bits, so the results are those of flux() throughout.  Counting
+    // runs keep flux().
     // The mixed sweeps group their FP64 redo the same way: a group is redone
     // through flux() where a state's FP32 recovery gives |v| > 0.99.
     static constexpr bool CAP_GROUPS = EOSK == EOS_CONFORMAL && !COUNT;
