@@ -69,13 +69,13 @@ def flops_per_cell_sweep(rk=2, stages=2, limiter="minmod"):
 # sweep and unsplit profile summaries under profiles/); None where no capture
 # of the current kernels exists
 SWEEP_TRAFFIC = {(256, "fp32", 2, 2, False): 595.2e6,
-                 (256, "fp32", 2, 2, True): 5032.0e6}
+                 (256, "fp32", 2, 2, True): 5043.2e6}
 # the event batch (FP32, minmod, k = 2, RK2): DRAM bytes per cell and sweep
 # launch, the mean over one step's five sweeps of an ncu capture of 64 events
 # of the batch recipe (1.10e8 cells, 3.3 GB held on the device), scaled by
 # cells to the full batch (the profile summary of the batch sweep under
 # profiles/); 32 B per cell is algorithmic
-BATCH_TRAFFIC_PER_CELL = 45.46
+BATCH_TRAFFIC_PER_CELL = 45.38
 
 
 def bytes_per_cell_stage_unsplit(elem):
